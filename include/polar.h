@@ -1,0 +1,172 @@
+/* polar.h -- C ABI of the GB300 library for the implicit theta-weighted step on the
+ * radius-angle-time mesh of the unit disk.
+ *
+ * The library advances  u_t + L u = f  on the unit disk in polar coordinates, with
+ * Dirichlet data on r = 1, by the adjustable Crank-Nicolson scheme of Eq. (2.5)
+ * (parabolic equation, Section 2.1) and of Section 3.2.1 (continuity equation).
+ * The paper's weight a multiplies the OLD time level; this interface takes the
+ * implicit weight  theta = 1 - a  (theta = 1/2 is Crank-Nicolson).  One step solves
+ *
+ *     (I/dt + theta L) U^{k+1} = (I/dt - (1-theta) L) U^k + theta F^{k+1} + (1-theta) F^k
+ *
+ * where F^k collects the source f(t_k) and the Dirichlet data g(t_k) of the ring
+ * r = 1 (Eqs. 2.9, 2.11, 2.12; Section 3.2.3).
+ *
+ * Vector layout at this interface (the unknown ordering of Eq. 2.12): N = m*n + 1
+ * doubles; element 0 is the origin, element 1 + j*m + (i-1) is the node
+ * (r_i, theta_j), i = 1..m, j = 0..n-1.  Radial lines are contiguous.
+ *
+ * Spatial operators (Section 3.2):
+ *  - POLAR_SCHEME_CONSERVATIVE: control-volume form.  Every face flux
+ *    (diffusion D grad u and first-order upwinded drift v u) is shared by the two
+ *    cells of the face, so the discrete mass balance is exact.  With v = 0 the ring
+ *    rows are those of Section 3.2.1 (Section 2.1 when D = 1) and the origin row is
+ *    the control-volume row of Section 3.2.2 (the Swarztrauber-Sweet row of
+ *    Section 2.1 when D = 1 and the angles are uniform).
+ *  - POLAR_SCHEME_PAPER: the printed stencils of Section 3.2.1 (scalar E at nodes,
+ *    forward differences) and the printed origin row of Section 3.2.2.
+ *
+ * Every function returns 0 (POLAR_OK) or a negative error code; nothing throws across
+ * the interface and polar_last_error() returns a message for the calling thread.
+ * All GPU work runs on the CUDA stream given in polar_mesh_desc; the library has no
+ * CPU fallback: without a usable CUDA device every call that needs one returns
+ * POLAR_ECUDA.
+ */
+#ifndef POLAR_H
+#define POLAR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  POLAR_OK = 0,
+  POLAR_EINVAL = -1,     /* bad argument; detected before any GPU work           */
+  POLAR_ENOMEM = -2,     /* device allocation failed                             */
+  POLAR_ECUDA = -3,      /* CUDA runtime error, or no device                     */
+  POLAR_ENOCONV = -4,    /* solver did not reach the tolerance; state unchanged  */
+  POLAR_ENONFINITE = -5, /* NaN/Inf in an input or in the solver; state unchanged */
+  POLAR_ESTATE = -7      /* call out of order (e.g. step before set_coeffs)      */
+};
+
+enum { POLAR_SCHEME_CONSERVATIVE = 0, POLAR_SCHEME_PAPER = 1 };
+enum { POLAR_FP64 = 0, POLAR_MIXED = 1 };   /* solver arithmetic                     */
+enum { POLAR_HOST = 0, POLAR_DEVICE = 1 };  /* where a caller's pointer lives         */
+
+typedef struct polar_ctx polar_ctx;
+
+/* Mesh of Sections 2.1 / 3.1.  The caller owns r and theta; they are copied. */
+typedef struct {
+  int32_t nr;            /* m >= 2 unknown rings r_1..r_m                              */
+  int32_t ntheta;        /* n >= 4 angles theta_0..theta_{n-1}                          */
+  const double* r;       /* host, m+2 values, r[0] = 0 < r[1] < ... < r[m+1] = 1        */
+  const double* theta;   /* host, n values, 0 <= theta[0] < ... < theta[n-1] < theta[0] + 2 pi */
+  int32_t scheme;        /* POLAR_SCHEME_*                                              */
+  int32_t precision;     /* POLAR_FP64 or POLAR_MIXED                                   */
+  void* stream;          /* cudaStream_t for all work (NULL = legacy default stream)    */
+} polar_mesh_desc;
+
+/* polar_mesh_create: validates the mesh (strictly increasing r with r[0] = 0 and
+ * r[m+1] = 1; strictly increasing theta spanning less than 2 pi; m >= 2; n >= 4)
+ * and allocates every device buffer of the context on the current device.
+ * Errors: POLAR_EINVAL (bad mesh, nothing allocated), POLAR_ENOMEM, POLAR_ECUDA.
+ * On success *out owns the buffers until polar_mesh_destroy. */
+int polar_mesh_create(const polar_mesh_desc* desc, polar_ctx** out);
+int polar_mesh_destroy(polar_ctx* ctx);
+
+/* Coefficients of the equation (Eq. 2.1 / Eq. 3.1) and its data, in the face
+ * layouts below; `memory` says whether ALL pointers are host or device pointers.
+ * Arrays are copied; the caller keeps ownership.
+ *   d_rface  (m+1)*n  D at radial faces (r_{i+1/2}, theta_j), i = 0..m, index j*(m+1)+i;
+ *                     NULL means D = d_const everywhere.
+ *   d_tface  m*n      D at angular faces (r_i, theta_{j+1/2}), i = 1..m, index j*m+(i-1),
+ *                     theta_{n-1/2} halfway between theta_{n-1} and theta_0 + 2 pi;
+ *                     NULL means D = d_const.
+ *   v_rface  (m+1)*n  radial drift velocity (mu E_r) at radial faces, or NULL (no drift)
+ *   v_tface  m*n      angular drift velocity (mu E_theta) at angular faces, or NULL
+ *   e_node   N        scalar E at nodes (PAPER scheme only), or NULL (E = 0)
+ *   b        N        reaction b >= 0 at nodes, or NULL (b = b_const)
+ *   d0                D at the origin (PAPER scheme only)
+ *   nsrc     Q in [0, 4] separable terms: f(t) = sum_q w_q(t) src[q], g(t) = sum_q w_q(t) bnd[q]
+ *   src[q]   N        node values of the q-th source field (origin first)
+ *   bnd[q]   n        values of the q-th Dirichlet field on r = 1 at theta_j
+ * Errors: POLAR_EINVAL (NULL where an array is required, nsrc out of range),
+ * POLAR_ENONFINITE (NaN or Inf in any array), POLAR_ECUDA. */
+typedef struct {
+  int32_t memory;
+  const double* d_rface;
+  const double* d_tface;
+  const double* v_rface;
+  const double* v_tface;
+  const double* e_node;
+  const double* b;
+  double d_const;
+  double b_const;
+  double d0;
+  int32_t nsrc;
+  const double* src[4];
+  const double* bnd[4];
+} polar_coeffs;
+int polar_set_coeffs(polar_ctx* ctx, const polar_coeffs* coeffs);
+
+/* State U (N values in the interface layout) and its time t.  set copies in,
+ * get copies out; `memory` says where u lives.  get before set -> POLAR_ESTATE. */
+int polar_set_state(polar_ctx* ctx, const double* u, double t, int32_t memory);
+int polar_get_state(polar_ctx* ctx, double* u, double* t, int32_t memory);
+
+/* Solver controls (NULL -> defaults).
+ *   tol         stop when max_i |r_i| / A_ii <= tol * max_i |U_i|, r = e - A U
+ *               (Jacobi-scaled residual of the implicit system); default 1e-14
+ *   max_iter    Krylov iterations per solve (FP64) or per inner solve (MIXED); default 4000
+ *   max_refine  outer refinement sweeps of the MIXED path; default 12
+ *   inner_tol   relative residual reduction of each FP32 inner solve; default 1e-5 */
+typedef struct {
+  double tol;
+  int32_t max_iter;
+  int32_t max_refine;
+  double inner_tol;
+} polar_solver_opts;
+
+typedef struct {
+  int32_t iters;         /* Krylov iterations (all inner solves for MIXED)            */
+  int32_t refinements;   /* outer FP64 residual evaluations (MIXED), 1 for FP64       */
+  int32_t status;        /* POLAR_OK or the error of this step                        */
+  int32_t pad;
+  double scaled_resid;   /* final max |r_i| / A_ii / max |U_i|                        */
+} polar_step_stats;
+
+/* One theta-step of length dt from the current state (Eq. 2.5 / Section 3.2.1):
+ * w_old[q] = w_q(t), w_new[q] = w_q(t + dt) weight the nsrc source/boundary fields.
+ * theta in (0, 1], dt > 0.  On success U and t advance; on failure they keep their
+ * values.  Errors: POLAR_EINVAL, POLAR_ESTATE (no coefficients or state),
+ * POLAR_ENOCONV, POLAR_ENONFINITE, POLAR_ECUDA.  stats may be NULL. */
+int polar_step(polar_ctx* ctx, double dt, double theta, const double* w_old,
+               const double* w_new, const polar_solver_opts* opts, polar_step_stats* stats);
+
+/* nsteps consecutive steps over the time levels t[0..nsteps] (t[0] must equal the
+ * current time to 1e-12 relative; t strictly increasing: variable dt_k of Section 3.1).
+ * w is (nsteps+1) x nsrc row-major: w[k*nsrc + q] = w_q(t[k]).  Stops at the first
+ * failing step, whose index is recorded in the stats (stats has nsteps entries or is
+ * NULL; entries after a failure have status POLAR_ESTATE). */
+int polar_advance(polar_ctx* ctx, int32_t nsteps, const double* t, double theta,
+                  const double* w, const polar_solver_opts* opts, polar_step_stats* stats);
+
+/* y = (alpha I + beta L) x for one vector x with homogeneous Dirichlet data
+ * (g = 0): the matrix-free operator every kernel of the step is built on.
+ * x and y hold N doubles in the interface layout, both on the host or both on the
+ * device as `memory` says.  Used to check the operator against an assembled matrix. */
+int polar_apply_operator(polar_ctx* ctx, double alpha, double beta, const double* x,
+                         double* y, int32_t memory);
+
+/* Number of CUDA kernels this context has launched since creation. */
+int64_t polar_kernel_launches(const polar_ctx* ctx);
+
+const char* polar_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* POLAR_H */

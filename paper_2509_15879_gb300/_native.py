@@ -1,0 +1,230 @@
+"""ctypes binding of libpolar.so: argument marshalling only.
+
+Every function carries the name of the C entry point it wraps (``include/polar.h``).
+Arrays are numpy float64 arrays (host memory) or CUDA tensors exposing ``data_ptr()``
+(device memory; torch supplies the memory, the library never allocates for them).
+The library has no CPU fallback: loading fails loudly if libpolar.so is missing.
+"""
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libpolar.so")
+
+POLAR_OK, POLAR_EINVAL, POLAR_ENOMEM, POLAR_ECUDA = 0, -1, -2, -3
+POLAR_ENOCONV, POLAR_ENONFINITE, POLAR_ESTATE = -4, -5, -7
+POLAR_SCHEME_CONSERVATIVE, POLAR_SCHEME_PAPER = 0, 1
+POLAR_FP64, POLAR_MIXED = 0, 1
+POLAR_HOST, POLAR_DEVICE = 0, 1
+
+_dp = C.POINTER(C.c_double)
+
+
+class polar_mesh_desc(C.Structure):
+    _fields_ = [("nr", C.c_int32), ("ntheta", C.c_int32), ("r", _dp), ("theta", _dp),
+                ("scheme", C.c_int32), ("precision", C.c_int32), ("stream", C.c_void_p)]
+
+
+class polar_coeffs(C.Structure):
+    _fields_ = [("memory", C.c_int32), ("d_rface", C.c_void_p), ("d_tface", C.c_void_p),
+                ("v_rface", C.c_void_p), ("v_tface", C.c_void_p), ("e_node", C.c_void_p),
+                ("b", C.c_void_p), ("d_const", C.c_double), ("b_const", C.c_double),
+                ("d0", C.c_double), ("nsrc", C.c_int32), ("src", C.c_void_p * 4),
+                ("bnd", C.c_void_p * 4)]
+
+
+class polar_solver_opts(C.Structure):
+    _fields_ = [("tol", C.c_double), ("max_iter", C.c_int32), ("max_refine", C.c_int32),
+                ("inner_tol", C.c_double)]
+
+
+class polar_step_stats(C.Structure):
+    _fields_ = [("iters", C.c_int32), ("refinements", C.c_int32), ("status", C.c_int32),
+                ("pad", C.c_int32), ("scaled_resid", C.c_double)]
+
+    def as_dict(self):
+        return dict(iters=self.iters, refinements=self.refinements, status=self.status,
+                    scaled_resid=self.scaled_resid)
+
+
+class PolarError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"polar error {code}: {msg}")
+        self.code = code
+
+
+_lib = None
+
+EXPORTS = {
+    "polar_mesh_create": (C.c_int, [C.POINTER(polar_mesh_desc), C.POINTER(C.c_void_p)]),
+    "polar_mesh_destroy": (C.c_int, [C.c_void_p]),
+    "polar_set_coeffs": (C.c_int, [C.c_void_p, C.POINTER(polar_coeffs)]),
+    "polar_set_state": (C.c_int, [C.c_void_p, C.c_void_p, C.c_double, C.c_int32]),
+    "polar_get_state": (C.c_int, [C.c_void_p, C.c_void_p, _dp, C.c_int32]),
+    "polar_step": (C.c_int, [C.c_void_p, C.c_double, C.c_double, _dp, _dp,
+                             C.POINTER(polar_solver_opts), C.POINTER(polar_step_stats)]),
+    "polar_advance": (C.c_int, [C.c_void_p, C.c_int32, _dp, C.c_double, _dp,
+                                C.POINTER(polar_solver_opts), C.POINTER(polar_step_stats)]),
+    "polar_apply_operator": (C.c_int, [C.c_void_p, C.c_double, C.c_double, C.c_void_p,
+                                       C.c_void_p, C.c_int32]),
+    "polar_kernel_launches": (C.c_int64, [C.c_void_p]),
+    "polar_last_error": (C.c_char_p, []),
+}
+
+
+def load(path: str = LIB_PATH):
+    """Loads libpolar.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(path):
+            raise ImportError(f"{path} is missing: build it with "
+                              "python -m paper_2509_15879_gb300.build")
+        lib = C.CDLL(path)
+        for name, (res, args) in EXPORTS.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+    return _lib
+
+
+def _check(rc):
+    if rc != POLAR_OK:
+        raise PolarError(rc, load().polar_last_error().decode())
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+class _Arr:
+    """Holds a pointer to caller data and keeps the owner alive."""
+
+    def __init__(self, a):
+        if a is None:
+            self.ptr, self.keep, self.device = None, None, None
+        elif hasattr(a, "data_ptr") and getattr(a, "is_cuda", False):
+            self.ptr, self.keep, self.device = a.data_ptr(), a, True
+        else:
+            arr = _f64(a)
+            self.ptr, self.keep, self.device = arr.ctypes.data, arr, False
+
+
+class Ctx:
+    """Handle of a polar_ctx; destroyed with the object or by polar_mesh_destroy."""
+
+    def __init__(self, handle, m, n):
+        self.handle, self.m, self.n = handle, m, n
+
+    @property
+    def N(self):
+        return self.m * self.n + 1
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.polar_mesh_destroy(self.handle)
+            self.handle = None
+
+
+def polar_mesh_create(r, theta, scheme=POLAR_SCHEME_CONSERVATIVE, precision=POLAR_FP64,
+                      stream=None) -> Ctx:
+    lib = load()
+    r, theta = _f64(r), _f64(theta)
+    d = polar_mesh_desc(len(r) - 2, len(theta), r.ctypes.data_as(_dp), theta.ctypes.data_as(_dp),
+                        scheme, precision, stream)
+    h = C.c_void_p()
+    _check(lib.polar_mesh_create(C.byref(d), C.byref(h)))
+    return Ctx(h, len(r) - 2, len(theta))
+
+
+def polar_mesh_destroy(ctx: Ctx):
+    if ctx.handle:
+        _check(load().polar_mesh_destroy(ctx.handle))
+        ctx.handle = None
+
+
+def polar_set_coeffs(ctx: Ctx, d_rface=None, d_tface=None, v_rface=None, v_tface=None,
+                     e_node=None, b=None, d_const=1.0, b_const=0.0, d0=1.0, src=(), bnd=()):
+    arrs = [_Arr(x) for x in (d_rface, d_tface, v_rface, v_tface, e_node, b)]
+    srcs = [_Arr(x) for x in src]
+    bnds = [_Arr(x) for x in bnd]
+    kinds = {a.device for a in arrs + srcs + bnds if a.ptr is not None}
+    if len(kinds) > 1:
+        raise ValueError("all coefficient arrays must live in the same memory")
+    mem = POLAR_DEVICE if kinds == {True} else POLAR_HOST
+    c = polar_coeffs()
+    c.memory = mem
+    c.d_rface, c.d_tface, c.v_rface, c.v_tface, c.e_node, c.b = [a.ptr for a in arrs]
+    c.d_const, c.b_const, c.d0 = float(d_const), float(b_const), float(d0)
+    c.nsrc = len(srcs)
+    for q in range(len(srcs)):
+        c.src[q] = srcs[q].ptr
+        c.bnd[q] = bnds[q].ptr
+    _check(load().polar_set_coeffs(ctx.handle, C.byref(c)))
+
+
+def polar_set_state(ctx: Ctx, u, t: float):
+    a = _Arr(u)
+    _check(load().polar_set_state(ctx.handle, a.ptr, float(t),
+                                  POLAR_DEVICE if a.device else POLAR_HOST))
+
+
+def polar_get_state(ctx: Ctx, out=None):
+    """Returns (u, t); u is a new numpy array unless ``out`` (host or device) is given."""
+    if out is None:
+        out = np.empty(ctx.N, dtype=np.float64)
+    a = _Arr(out)
+    t = C.c_double()
+    _check(load().polar_get_state(ctx.handle, a.ptr, C.byref(t),
+                                  POLAR_DEVICE if a.device else POLAR_HOST))
+    return out, t.value
+
+
+def _opts(opts):
+    if opts is None:
+        return None
+    o = polar_solver_opts(opts.get("tol", 0.0), opts.get("max_iter", 0),
+                          opts.get("max_refine", 0), opts.get("inner_tol", 0.0))
+    return C.byref(o)
+
+
+def polar_step(ctx: Ctx, dt, theta, w_old=(), w_new=(), opts=None):
+    wo, wn = _f64(w_old), _f64(w_new)
+    st = polar_step_stats()
+    rc = load().polar_step(ctx.handle, float(dt), float(theta), wo.ctypes.data_as(_dp),
+                           wn.ctypes.data_as(_dp), _opts(opts), C.byref(st))
+    _check(rc)
+    return st.as_dict()
+
+
+def polar_advance(ctx: Ctx, t, theta, w=None, opts=None, check=True):
+    t = _f64(t)
+    K = len(t) - 1
+    w = np.zeros((K + 1, 0)) if w is None else _f64(w)
+    stats = (polar_step_stats * max(K, 1))()
+    rc = load().polar_advance(ctx.handle, K, t.ctypes.data_as(_dp), float(theta),
+                              w.ctypes.data_as(_dp), _opts(opts), stats)
+    if check:
+        _check(rc)
+    return [stats[k].as_dict() for k in range(K)], rc
+
+
+def polar_apply_operator(ctx: Ctx, alpha, beta, x, out=None):
+    if out is None:
+        out = np.empty(ctx.N, dtype=np.float64)
+    ax, ay = _Arr(x), _Arr(out)
+    if ax.device != ay.device:
+        raise ValueError("x and y must live in the same memory")
+    _check(load().polar_apply_operator(ctx.handle, float(alpha), float(beta), ax.ptr, ay.ptr,
+                                       POLAR_DEVICE if ax.device else POLAR_HOST))
+    return out
+
+
+def polar_kernel_launches(ctx: Ctx) -> int:
+    return int(load().polar_kernel_launches(ctx.handle))
+
+
+def polar_last_error() -> str:
+    return load().polar_last_error().decode()

@@ -1,0 +1,89 @@
+"""GPU parity: the CUDA library against the FP64 CPU oracle on the same seeded inputs.
+
+Operator: y = alpha x + beta L x through polar_apply_operator against the oracle's
+assembled sparse L (relative 1e-13).  Steps: polar_advance against the oracle's sparse
+LU time stepping; FP64 path <= 1e-12 and mixed path <= 1e-9 in the relative max norm.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import polar_inputs as pi
+from polar_inputs import meshes
+from oracle import polar_oracle as po
+
+pytestmark = pytest.mark.gpu
+
+P = pytest.importorskip("paper_2509_15879_gb300")
+from paper_2509_15879_gb300 import driver  # noqa: E402
+
+
+def _rel(a, b):
+    return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
+
+
+def _small_continuity(m, n, K=4, seed=21, pe=6.0, theta_w=0.5):
+    return pi.continuity_problem(m, n, K, seed, theta_w=theta_w, pe_target=pe, d_amp=1.3,
+                                 delta=0.2)
+
+
+OPERATOR_CASES = [
+    ("parabolic_uniform", lambda: pi.config1()),
+    ("parabolic_graded_ragged", lambda: pi.config2(m=37, n=53, K=3)),
+    ("continuity_ragged", lambda: _small_continuity(45, 70)),
+    ("continuity_tiny", lambda: _small_continuity(2, 4)),
+    ("paper_parabolic", lambda: pi.paper_parabolic_e1(19)),
+    ("paper_continuity", lambda: pi.paper_continuity_e3(13)),
+]
+
+
+@pytest.mark.parametrize("name,make", OPERATOR_CASES)
+def test_operator_matches_assembled_matrix(name, make):
+    prob = make()
+    L, _ = po.operator(prob)
+    ctx = driver.create(prob, compact_d=False)
+    rng = np.random.default_rng(7)
+    x = rng.standard_normal(prob.N)
+    for alpha, beta in ((0.0, 1.0), (37.5, 0.5)):
+        y = P.polar_apply_operator(ctx, alpha, beta, x)
+        ref = alpha * x + beta * (L @ x)
+        scale = alpha * np.abs(x) + beta * (abs(L) @ np.abs(x))
+        assert np.all(np.abs(y - ref) <= 1e-13 * scale), name
+
+
+def _oracle_levels(prob, K):
+    out = []
+    po.run(prob, K, callback=lambda k, U: out.append(U.copy()))
+    return out
+
+
+@pytest.mark.parametrize("precision,tol", [(0, 1e-12), (1, 1e-9)])
+def test_config1_full_run(precision, tol):
+    """Uniform 32 x 64 mesh, Crank-Nicolson, dt = 0.01, 100 steps to T = 1."""
+    prob = pi.config1()
+    ref = po.run(prob)
+    ctx = driver.create(prob, precision)
+    stats = driver.advance(ctx, prob)
+    assert all(s["status"] == 0 for s in stats)
+    U, t = P.polar_get_state(ctx)
+    assert abs(t - 1.0) < 1e-15
+    assert _rel(U, ref) < tol
+
+
+@pytest.mark.parametrize("precision,tol", [(0, 1e-12), (1, 1e-9)])
+@pytest.mark.parametrize("name,make,K", [
+    ("C2_shape", lambda: pi.config2(m=64, n=128, K=30), 30),
+    ("continuity_drift", lambda: _small_continuity(40, 72, K=12), 12),
+    ("continuity_theta06", lambda: _small_continuity(33, 50, K=8, theta_w=0.6, pe=18.0), 8),
+    ("paper_e1", lambda: pi.paper_parabolic_e1(19), 10),
+    ("paper_e3", lambda: pi.paper_continuity_e3(19), 10),
+])
+def test_steps_match_oracle(name, make, K, precision, tol):
+    prob = make()
+    refs = _oracle_levels(prob, K)
+    ctx = driver.create(prob, precision)
+    for k in range(K):
+        driver.advance(ctx, prob, k, k + 1)
+        U, _ = P.polar_get_state(ctx)
+        assert _rel(U, refs[k]) < tol, (name, k, _rel(U, refs[k]))
