@@ -230,12 +230,25 @@ def system_matrix(L, dt, th):
     return (sp.identity(L.shape[0], format="csr") / dt + th * L).tocsc()
 
 
-def step(L, B, U, dt, th, f_old, g_old, f_new, g_new, lu=None):
-    """One theta-step (Eq. 2.11) solved with a sparse LU factorisation."""
+def residual_extended(A, x, e):
+    """e - A x accumulated in extended precision (numpy longdouble), rounded to FP64."""
+    A = A.tocsr()
+    prod = A.data.astype(np.longdouble) * x.astype(np.longdouble)[A.indices]
+    rows = np.add.reduceat(prod, A.indptr[:-1])
+    return (e.astype(np.longdouble) - rows).astype(np.float64)
+
+
+def step(L, B, U, dt, th, f_old, g_old, f_new, g_new, lu=None, A=None):
+    """One theta-step (Eq. 2.11): sparse LU solve followed by one step of iterative
+    refinement whose residual is accumulated in extended precision, so the result is
+    the discrete solution to rounding rather than to (condition number) x rounding."""
     e = rhs(L, B, U, dt, th, f_old, g_old, f_new, g_new)
+    if A is None:
+        A = system_matrix(L, dt, th)
     if lu is None:
-        lu = spla.splu(system_matrix(L, dt, th))
-    return lu.solve(e)
+        lu = spla.splu(A.tocsc())
+    x = lu.solve(e)
+    return x + lu.solve(residual_extended(A, x, e))
 
 
 def run(prob, nsteps=None, callback=None):
@@ -246,13 +259,14 @@ def run(prob, nsteps=None, callback=None):
     K = len(t) - 1 if nsteps is None else nsteps
     U = np.asarray(prob.u0, dtype=np.float64).copy()
     f_old, g_old = source(prob, t[0])
-    lu, lu_dt = None, None
+    lu, lu_dt, A = None, None, None
     for k in range(K):
         dt = t[k + 1] - t[k]
         if lu is None or abs(dt - lu_dt) > 1e-15 * dt:
-            lu, lu_dt = spla.splu(system_matrix(L, dt, prob.theta_w)), dt
+            A = system_matrix(L, dt, prob.theta_w)
+            lu, lu_dt = spla.splu(A), dt
         f_new, g_new = source(prob, t[k + 1])
-        U = step(L, B, U, dt, prob.theta_w, f_old, g_old, f_new, g_new, lu)
+        U = step(L, B, U, dt, prob.theta_w, f_old, g_old, f_new, g_new, lu, A)
         f_old, g_old = f_new, g_new
         if callback is not None:
             callback(k + 1, U)
