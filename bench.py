@@ -1,0 +1,383 @@
+"""Throughput of the implicit theta-step on the adaptive polar mesh (one GB300 per rank).
+
+Workload: the singular parabolic equation on the unit disk on the adaptive mesh --
+m = 512 rings graded geometrically (ratio 1.03) toward r = 0 and r = 1, n = 1024
+angles with node density 1 + 0.5 cos(theta - theta0), Crank-Nicolson, variable
+dt_k = 1e-4 * 1.01^k over a 1000-level schedule (T ~ 209.6); manufactured solution
+u = e^{-t}(1 - r^2)(1 + r cos theta).  Inputs are synthetic and seeded.
+
+A bench step is one implicit theta-step (right-hand side, line factors, Krylov solve
+to the FP64 tolerance, time-level update) of that schedule.  With K < 1000 the K steps
+are spread evenly over the schedule, each starting from the manufactured solution at
+its level (set outside the timed region); with K >= 1000 the schedule runs
+consecutively.  L2 is flushed (a 512 MB write) before every timed step.
+
+value  = grid-point updates (N per step) / device time of the K steps, summed over ranks
+         (replicas: every rank advances its own copy; no collective on the data path)
+e2e    = the same through the C ABI with the state copied in from pinned host memory
+         and out to pinned host memory inside every timed step
+roofline: the dominant kernel class's algorithmic bytes / its event-timed duration
+cpu_baseline: the FP64 CPU oracle on a bounded sample of the same workload
+
+--impl reference times the CPU oracle itself (the reference arm of this workload).
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "grid-point-updates/s and HBM GB/s vs peak, mixed vs FP64 GPU at stated error"
+UNIT = "grid-point-updates/s"
+M_RINGS, N_ANGLES, K_SCHEDULE = 512, 1024, 1000
+WORKLOAD = ("parabolic u_t = Lap u + f, adaptive polar mesh 512 x 1024 (r graded 1.03 "
+            "to both ends, theta density 1 + 0.5 cos), Crank-Nicolson, dt_k = 1e-4 * 1.01^k, "
+            "1000-level schedule")
+FALLBACK_HBM_GBS = 6800.0
+
+# ncu dram bytes (read + write) per launch of the dominant kernel class, from the
+# capture summarised under profiles/; None until a capture of the current kernel exists
+NCU_TRAFFIC = {}
+
+
+def env_int(name, default):
+    try:
+        return int(os.environ.get(name, default))
+    except ValueError:
+        return default
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons, sampled every 200 ms in the background."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.file, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.file.flush()
+        self.file.seek(0)
+        sm, smax, reasons = [], None, set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for line in self.file.read().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.file.name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": smax, "reasons": ["no samples"]}
+        # median over the samples taken under load (clock above idle)
+        hi = [s for s in sm if s >= 0.5 * max(sm)]
+        return {"sm_mhz": statistics.median(hi), "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def make_problem(m=M_RINGS, n=N_ANGLES, K=K_SCHEDULE):
+    import polar_inputs as pi
+    return pi.config2(m=m, n=n, K=K)
+
+
+def step_levels(K):
+    """Schedule levels at which the K timed steps start."""
+    if K >= K_SCHEDULE:
+        return [k % K_SCHEDULE for k in range(K)], True
+    return [int(math.floor(s * K_SCHEDULE / K)) for s in range(K)], False
+
+
+# ------------------------------------------------------------------------- CPU oracle
+def oracle_sample(budget_s=20.0, prob=None):
+    """Times the FP64 CPU oracle on whole theta-steps of the workload (full mesh, steps
+    spread over the schedule, each from the manufactured solution at its level) until
+    about budget_s of CPU time has passed.  Returns (updates/s, steps, seconds)."""
+    from oracle import polar_oracle as po
+    prob = prob or make_problem()
+    L, B = po.operator(prob)
+    levels = [0, 500, 250, 750, 125, 625, 375, 875]
+    done, t_used, upd = 0, 0.0, 0
+    for k in levels:
+        if done and t_used >= budget_s:
+            break
+        U = prob.exact(prob.t[k])
+        dt = prob.t[k + 1] - prob.t[k]
+        t0 = time.perf_counter()
+        fo, go = po.source(prob, prob.t[k])
+        fn, gn = po.source(prob, prob.t[k + 1])
+        po.step(L, B, U, dt, prob.theta_w, fo, go, fn, gn)
+        t_used += time.perf_counter() - t0
+        upd += prob.N
+        done += 1
+    return upd / t_used, done, t_used
+
+
+def run_reference(args):
+    rank = env_int("RANK", 0)
+    if rank != 0:
+        return 0
+    prob = make_problem()
+    total = args.warmup + args.steps
+    # each reference step is one oracle theta-step on a sample mesh whose size keeps
+    # the whole run within about three minutes (one full-size step takes ~10-15 s)
+    per_step = 150.0 / max(total, 1)
+    scale = 1
+    while scale < 8 and 13.0 / (scale * scale) > per_step:
+        scale *= 2
+    sample = make_problem(M_RINGS // scale, N_ANGLES // scale) if scale > 1 else prob
+    from oracle import polar_oracle as po
+    L, B = po.operator(sample)
+    levels, _ = step_levels(args.steps)
+    wl, _ = step_levels(max(args.warmup, 1))
+
+    def one(k):
+        U = sample.exact(sample.t[k])
+        dt = sample.t[k + 1] - sample.t[k]
+        fo, go = po.source(sample, sample.t[k])
+        fn, gn = po.source(sample, sample.t[k + 1])
+        po.step(L, B, U, dt, sample.theta_w, fo, go, fn, gn)
+
+    for k in wl[:args.warmup]:
+        one(k)
+    t0 = time.perf_counter()
+    for k in levels:
+        one(k)
+    el = time.perf_counter() - t0
+    value = sample.N * len(levels) / el
+    desc = (f"one FP64 oracle theta-step (sparse LU + one extended-precision refinement) per "
+            f"bench step on the {sample.m} x {sample.n} version of the workload mesh, "
+            f"levels spread over the schedule")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / len(levels),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "m": sample.m, "n": sample.n, "N": sample.N,
+                       "sample_of": f"{M_RINGS} x {N_ANGLES}"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": desc},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------------- GPU arm
+def run_native(args):
+    import torch
+    import paper_2509_15879_gb300 as P
+    from paper_2509_15879_gb300 import driver
+
+    world = env_int("WORLD_SIZE", 1)
+    rank = env_int("RANK", 0)
+    local = env_int("LOCAL_RANK", 0)
+    if not torch.cuda.is_available():
+        raise RuntimeError("bench.py needs a CUDA GPU (the library has no CPU path)")
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    precision = P.POLAR_MIXED if args.precision == "mixed" else P.POLAR_FP64
+    prob = make_problem()
+    stream = torch.cuda.current_stream()
+    ctx = driver.create(prob, precision, stream=stream.cuda_stream)
+    t_all = np.asarray(prob.t)
+    W = prob.weight_table()
+    exact = {}
+
+    def set_level(k, host=None):
+        if k not in exact:
+            exact[k] = np.ascontiguousarray(prob.exact(t_all[k]))
+        P.polar_set_state(ctx, exact[k] if host is None else host, t_all[k])
+
+    def step(k, opts=None):
+        st, rc = P.polar_advance(ctx, t_all[k:k + 2], prob.theta_w, W[k:k + 2], opts)
+        return st[0]
+
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    levels, consecutive = step_levels(args.steps)
+
+    # warm-up: W steps spread over the schedule
+    wl, _ = step_levels(max(args.warmup, 1))
+    for k in wl[:args.warmup]:
+        set_level(k)
+        step(k)
+    torch.cuda.synchronize()
+
+    # ---- timed region (device time of each step, L2 flushed before each)
+    clocks = ClockSampler(local)
+    clocks.start()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in levels]
+    iters, refs = [], []
+    launches0 = P.polar_kernel_launches(ctx)
+    P.polar_timing_enable(ctx, True)
+    barrier()
+    wall0 = time.perf_counter()
+    for s, k in enumerate(levels):
+        if not consecutive or k == 0:
+            set_level(k)
+        flush.fill_(float(s))
+        ev[s][0].record(stream)
+        st = step(k)
+        ev[s][1].record(stream)
+        iters.append(st["iters"])
+        refs.append(st["refinements"])
+    barrier()
+    wall = time.perf_counter() - wall0
+    clk = clocks.stop()
+    launches = P.polar_kernel_launches(ctx) - launches0
+    kstats = P.polar_timing_query(ctx)
+    P.polar_timing_enable(ctx, False)
+    dev_ms = sum(a.elapsed_time(b) for a, b in ev)
+    U_last, t_last = P.polar_get_state(ctx)
+    err_exact = float(np.max(np.abs(U_last - prob.exact(t_last))) /
+                      np.max(np.abs(prob.exact(t_last))))
+    if dist is not None:
+        tt = torch.tensor([dev_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        dev_ms = float(tt.item())
+    updates = prob.N * len(levels) * world
+    value = updates / (dev_ms * 1e-3)
+
+    # ---- end to end: pinned host state in, pinned host state out, every step
+    ke = levels[:max(1, min(len(levels), 20))]
+    host_in = {k: torch.from_numpy(np.ascontiguousarray(prob.exact(t_all[k]))).pin_memory()
+               for k in ke}
+    host_out = torch.empty(prob.N, dtype=torch.float64).pin_memory()
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e_ms = 0.0
+    for k in ke:
+        flush.fill_(1.0)
+        e0.record(stream)
+        P.polar_set_state(ctx, host_in[k], t_all[k])
+        step(k)
+        P.polar_get_state(ctx, host_out)
+        e1.record(stream)
+        e1.synchronize()
+        e_ms += e0.elapsed_time(e1)
+    if dist is not None:
+        tt = torch.tensor([e_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e_ms = float(tt.item())
+    e2e_value = prob.N * len(ke) * world / (e_ms * 1e-3)
+
+    # ---- roofline of the dominant kernel class
+    peak, peak_src = measured_peaks()
+    dom = max(kstats.items(), key=lambda kv: kv[1]["ms"]) if kstats else None
+    roof = None
+    if dom is not None:
+        name, d = dom
+        achieved = d["bytes"] / (d["ms"] * 1e-3) / 1e9
+        per_launch = d["bytes"] / max(d["launches"], 1)
+        roof = {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": peak,
+                "peak_source": peak_src, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": NCU_TRAFFIC.get(name), "algorithmic_bytes_per_launch": per_launch,
+                "avg_launch_us": 1e3 * d["ms"] / max(d["launches"], 1),
+                "share_of_step": d["ms"] / dev_ms}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dev_ms / len(levels),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if precision == P.POLAR_FP64 else "f32+f64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "m": prob.m, "n": prob.n, "N": prob.N,
+                       "precision": args.precision,
+                       "levels": "consecutive" if consecutive else
+                                 f"{len(levels)} steps spread over the 1000-level schedule",
+                       "l2": "flushed (512 MB write) before every timed step",
+                       "parallelism": f"replicas x{world}"},
+            "krylov_iters_per_step": float(np.mean(iters)),
+            "refinements_per_step": float(np.mean(refs)),
+            "rel_err_vs_exact_last_step": err_exact,
+            "wall_s": wall,
+            "gpu_launches": int(launches),
+            "clocks": clk,
+            "roofline": roof,
+            "kernels": {k: {"launches": v["launches"], "ms": round(v["ms"], 3),
+                            "GBps": round(v["bytes"] / max(v["ms"], 1e-9) / 1e6, 1)}
+                        for k, v in sorted(kstats.items(), key=lambda kv: -kv[1]["ms"])},
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": prob.N * 8,
+                    "d2h_bytes_per_step": prob.N * 8, "steps": len(ke)}}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, nsteps, secs = oracle_sample(args.cpu_budget, prob)
+        line["cpu_baseline"] = {
+            "value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{nsteps} full-size theta-steps of the workload ({secs:.1f} s; sparse LU "
+                      f"+ one extended-precision refinement, single-threaded SuperLU)"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=40)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["native", "reference"], default="native")
+    ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64")
+    ap.add_argument("--cpu-budget", type=float, default=20.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_native(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

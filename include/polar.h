@@ -164,6 +164,19 @@ int polar_apply_operator(polar_ctx* ctx, double alpha, double beta, const double
 /* Number of CUDA kernels this context has launched since creation. */
 int64_t polar_kernel_launches(const polar_ctx* ctx);
 
+/* Per-kernel timing for roofline measurements (not part of the method).
+ * polar_timing_enable(ctx, 1) clears the counters and brackets every later launch of
+ * the step's kernels with two CUDA events on the context's stream; 0 turns it off.
+ * polar_timing_query returns, for kernel class `index` (0, 1, ... in order of first
+ * launch; POLAR_EINVAL past the last), its name (NUL-terminated, truncated to
+ * name_len), the number of timed launches, their summed device time in ms and the
+ * summed algorithmic bytes of those launches (the words each launch must read and
+ * write per grid point times the points it covers).  Querying synchronises the
+ * stream.  Any output pointer may be NULL. */
+int polar_timing_enable(polar_ctx* ctx, int32_t on);
+int polar_timing_query(polar_ctx* ctx, int32_t index, char* name, size_t name_len,
+                       int64_t* launches, double* total_ms, double* bytes);
+
 const char* polar_last_error(void);
 
 #ifdef __cplusplus

@@ -70,6 +70,9 @@ EXPORTS = {
     "polar_apply_operator": (C.c_int, [C.c_void_p, C.c_double, C.c_double, C.c_void_p,
                                        C.c_void_p, C.c_int32]),
     "polar_kernel_launches": (C.c_int64, [C.c_void_p]),
+    "polar_timing_enable": (C.c_int, [C.c_void_p, C.c_int32]),
+    "polar_timing_query": (C.c_int, [C.c_void_p, C.c_int32, C.c_char_p, C.c_size_t,
+                                     C.POINTER(C.c_int64), _dp, _dp]),
     "polar_last_error": (C.c_char_p, []),
 }
 
@@ -107,6 +110,11 @@ class _Arr:
             self.ptr, self.keep, self.device = None, None, None
         elif hasattr(a, "data_ptr") and getattr(a, "is_cuda", False):
             self.ptr, self.keep, self.device = a.data_ptr(), a, True
+        elif hasattr(a, "data_ptr") and hasattr(a, "is_contiguous"):
+            # host torch tensor (e.g. pinned): used in place, never copied
+            if str(a.dtype) != "torch.float64" or not a.is_contiguous():
+                raise ValueError("host tensors must be contiguous float64")
+            self.ptr, self.keep, self.device = a.data_ptr(), a, False
         else:
             arr = _f64(a)
             self.ptr, self.keep, self.device = arr.ctypes.data, arr, False
@@ -224,6 +232,24 @@ def polar_apply_operator(ctx: Ctx, alpha, beta, x, out=None):
 
 def polar_kernel_launches(ctx: Ctx) -> int:
     return int(load().polar_kernel_launches(ctx.handle))
+
+
+def polar_timing_enable(ctx: Ctx, on=True):
+    _check(load().polar_timing_enable(ctx.handle, 1 if on else 0))
+
+
+def polar_timing_query(ctx: Ctx):
+    """Returns {kernel class: dict(launches, ms, bytes)} of the timed launches."""
+    lib, out, k = load(), {}, 0
+    while True:
+        name = C.create_string_buffer(64)
+        nl, ms, by = C.c_int64(), C.c_double(), C.c_double()
+        rc = lib.polar_timing_query(ctx.handle, k, name, 64, C.byref(nl), C.byref(ms), C.byref(by))
+        if rc != POLAR_OK:
+            break
+        out[name.value.decode()] = dict(launches=nl.value, ms=ms.value, bytes=by.value)
+        k += 1
+    return out
 
 
 def polar_last_error() -> str:

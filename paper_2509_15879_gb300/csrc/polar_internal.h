@@ -1,11 +1,17 @@
 // Internal declarations shared by the host orchestration (polar_api.cu) and the
-// kernels (polar_kernels.cu).  Nothing here is part of the C ABI.
+// kernels (polar_kernels.cu, polar_mg.cu).  Nothing here is part of the C ABI.
 //
-// Device vector layout ("padded layout"): element 0 is the origin, elements 1..3 are
-// zero padding, and radial line j (angle theta_j) occupies [kOfs + j*ld, kOfs + j*ld + m)
-// with ld = m rounded up to a multiple of 4, so every line starts on a 32-byte
-// boundary for FP64 and a 16-byte boundary for FP32.  Entries [m, ld) of every line
-// are kept at zero by every kernel that writes a vector.
+// Every vector of the solver lives in the "split-parity" layout of its multigrid
+// level (m rings, n angles):
+//   [0, kOrig)                          origin at 0, the rest zero padding
+//   odd block   odd0 + j*ldo + k        ring 2k+1 (k < no = (m+1)/2), angle j
+//   even block  even0 + j*lde + k       ring 2k+2 (k < ne = m/2),     angle j
+// Radial lines stay contiguous within each parity block (one line of odd rings, one of
+// even rings per angle), ldo/lde are multiples of 8 so every line starts on a 64-byte
+// boundary, and padding entries are kept at zero by every kernel that writes a vector.
+// The ring-by-ring (zebra) relaxation of the multigrid smoother touches one parity
+// block at a time, so its loads use every byte of every sector, and the even block of
+// a level holds exactly the rings that form the next coarser level.
 #pragma once
 #include <cstddef>
 #include <cstdint>
@@ -13,47 +19,63 @@
 
 namespace polar {
 
-constexpr int kOfs = 4;
+constexpr int kOrig = 8;
 
-// The discrete operator L of one instance, as 5-point rows (Section 3.2.1) kept in
-// difference form: with the diagonal C = R - W - E - S - N,
-//   (L x)_{i,j} = R x_{i,j} + W (x_{i-1,j} - x_{i,j}) + E (x_{i+1,j} - x_{i,j})
-//               + S (x_{i,j-1} - x_{i,j}) + N (x_{i,j+1} - x_{i,j}),
-// with x_{0,j} = x_0 (the origin, Eq. 2.8), periodic j (Eqs. 2.6-2.7), and x_{m+1,j}
-// the Dirichlet value (Eq. 2.9; zero in the homogeneous operator).  R is the row sum
-// (b plus the drift divergence), so smooth vectors lose no digits to the cancellation
-// of the huge angular couplings near the origin, also in FP32.
-// Origin row (Section 3.2.2): (L x)_0 = R[0] x_0 + sum_j o[j] (x_{1,j} - x_0).
-template <typename T>
-struct OpView {
-  int m, n, ld;
-  const T* R;
-  const T* W;
-  const T* E;
-  const T* S;
-  const T* N;
-  const T* o;  // n coefficients of the origin row
+struct Shape {
+  int m, n;        // rings, angles
+  int no, ne;      // odd / even ring counts
+  int ldo, lde;    // padded line lengths of the two blocks
+  size_t odd0, even0, nv;
+  __host__ __device__ size_t at(int i, int j) const {  // ring i in 1..m, angle j
+    return (i & 1) ? odd0 + (size_t)j * ldo + (size_t)(i >> 1)
+                   : even0 + (size_t)j * lde + (size_t)((i >> 1) - 1);
+  }
 };
 
-// LU factors of the line blocks of A = alpha I + beta L (per time step).
-// Radial line j (rows i = 1..m, tridiagonal, origin and boundary couplings dropped):
-//   forward  y_k = d_k - l_k y_{k-1};  backward  x_k = ui_k y_k - cu_k x_{k+1}.
-// Angular line i (rows j = 0..n-1, periodic): the same factors of the tridiagonal
-// part A' after the Sherman-Morrison splitting A = A' + u v^T, plus q = A'^{-1} u and
-// per ring vf = v_{n-1} and inv1vq = 1 / (1 + v.q).
+inline Shape make_shape(int m, int n) {
+  Shape s;
+  s.m = m;
+  s.n = n;
+  s.no = (m + 1) / 2;
+  s.ne = m / 2;
+  s.ldo = (s.no + 7) & ~7;
+  s.lde = (s.ne + 7) & ~7;
+  s.odd0 = kOrig;
+  s.even0 = s.odd0 + (size_t)n * s.ldo;
+  s.nv = s.even0 + (size_t)n * s.lde;
+  return s;
+}
+
+// One multigrid level of S = alpha V + beta (V L), the theta-step matrix scaled by
+// the control volumes (Section 3.2; alpha = 1/dt, beta = theta).  Static parts come
+// from the coefficients (V L in difference form, see polar_api.cu); the per-step parts
+// (diag, line factors, origin scalars) are refreshed whenever alpha or beta change.
+//   (S x)_ij = diag x_ij + beta (w x_{i-1,j} + e x_{i+1,j} + s x_{i,j-1} + nn x_{i,j+1})
+//   (S x)_0  = diag0 x_0 + beta sum_j o_j x_{1,j}
+// with x_{0,j} = x_0 and x_{m+1,j} = 0 (homogeneous Dirichlet ring).
 template <typename T>
-struct LineFactors {
-  T* rl;
-  T* rui;
-  T* rcu;
-  T* al;
-  T* aui;
-  T* acu;
-  T* aq;
-  T* avf;     // m
-  T* ainv;    // m
-  double* ws; // 2 nv doubles: FP64 forward values of q and FP64 pivots (factor kernel only)
-  T diag0;    // A_00, the origin block of the preconditioner
+struct LevelView {
+  Shape sh;
+  // static (V L), nv each; o has n entries
+  const T* vol;
+  const T* rs;   // row sums of V L (reaction and drift divergence)
+  const T* w;
+  const T* e;
+  const T* s;
+  const T* nn;
+  const T* o;
+  const T* ia;   // interpolation weights of the odd rings from the coarser level:
+  const T* ib;   //   x_{2k+1} = ia x_{2k} + ib x_{2k+2} (x_0 = origin, x_{m+1} = 0)
+  // per step
+  T* diag;       // nv: alpha vol + beta (rs - w - e - s - nn)
+  T* fl;         // line factors of every ring's periodic angular line, nv each
+  T* fui;
+  T* fcu;
+  T* fq;
+  T* fring;      // 2 per ring, ring order (odd rings, then even): vf, 1/(1 + v.q)
+  T* fz;         // n: coarsest level only, T_1^{-1} (beta w_1)
+  double* sc;    // scalars: [0] diag0, [1] coarsest Schur denominator, [2] sum_j o_j (static),
+                 //          [3] vol0, [4] rs0 (static)
 };
 
 // Scalars of one Krylov solve, kept on the device so that no iteration needs the host.
@@ -61,14 +83,13 @@ struct KrylovScalars {
   double rho, alpha, omega, beta;
   double rr0, rr, tol2;
   double dot[4];
-  int done;        // 0 running, 1 converged, 2 breakdown, 3 non-finite
+  int done;        // 0 running, 1 converged, 2 breakdown, 3 non-finite, 4 iteration limit
   int iters;
   int max_iter;
   int pad0;
-  // refinement (FP64) reductions
-  double rmax;     // max |r_i|
-  double smax;     // max |r_i| / A_ii
-  double xmax;     // max |x_i|
+  double rmax;     // refinement reductions: max |r_i|, max |r_i| / S_ii, max |x_i|
+  double smax;
+  double xmax;
   unsigned int counter;
   unsigned int pad1;
 };
@@ -79,55 +100,62 @@ struct Reduce {
 };
 constexpr int kMaxBlocks = 2048;
 
+// Per-step parameters read by the kernels from device memory: [0] alpha, [1] beta.
+using Params = const double*;
+
 int grid_for(size_t work, int threads);
 
-// ----------------------------------------------------------------- kernel launchers
+// ----------------------------------------------------------------- launchers
 // All launchers enqueue on `st` and return the number of kernels launched.
 
-// y = alpha x + beta L x (+ optional terms; see polar_kernels.cu for each mode)
+// Stencil of the fine level.  Modes:
+//   apply:   y = S x
+//   resid:   y = b - S x
+//   dot v:   y = S x, alpha_k = rho / (rhat . y)            (BiCGStab)
+//   dot t:   y = S x, omega = (t . s) / (t . t)             (BiCGStab)
 template <typename T>
-int launch_apply(const OpView<T>& op, T alpha, T beta, const T* x, T* y, cudaStream_t st,
-                 Reduce red);
-
-// y = b - (alpha x + beta L x)
+int launch_apply(const LevelView<T>& L, Params p, const T* x, T* y, cudaStream_t st, Reduce red);
 template <typename T>
-int launch_resid(const OpView<T>& op, T alpha, T beta, const T* x, const T* b, T* y,
-                 cudaStream_t st, Reduce red);
+int launch_apply_dot(const LevelView<T>& L, Params p, const T* x, T* y, const T* d1, int mode,
+                     cudaStream_t st, Reduce red);
 
-// FP64 right-hand side of the theta-step:
-// e = alpha x + beta L_g x + sum_q cf[q] src[q], where L_g takes x_{m+1,j} =
-// sum_q cg[q] bnd[q][j] as the Dirichlet value
-int launch_rhs(const OpView<double>& op, double alpha, double beta, const double* x,
-               int nsrc, const double* const* src, const double* const* bnd,
-               const double* cf, const double* cg, double* e, cudaStream_t st, Reduce red);
+// FP64 residual with reductions (rmax, Jacobi-scaled smax, xmax): r = b - S x
+int launch_resid64(const LevelView<double>& L, Params p, const double* x, const double* b,
+                   double* r, cudaStream_t st, Reduce red);
 
-// FP64 residual of the implicit system with reductions into red.ks:
-// r = e - (alpha x + beta L x); rmax, smax (Jacobi-scaled), xmax.
-// c0 is the diagonal of the origin row of L.
-int launch_resid64(const OpView<double>& op, double alpha, double beta, const double* x,
-                   const double* e, double* r, double c0, cudaStream_t st, Reduce red);
+// FP64 right-hand side of the theta-step in S form:
+//   e = (V/dt) u - (1 - theta) (V L) u + sum_q cf[q] Vsrc[q] - e_{m,j} sum_q cg[q] bnd[q][j]
+// (cg already carries the weights of both time levels).
+int launch_rhs(const LevelView<double>& L, double alpha, double one_minus_theta, const double* u,
+               int nsrc, const double* const* vsrc, const double* const* bnd, const double* cf,
+               const double* cg, double* e, cudaStream_t st, Reduce red);
 
-// factors in precision T, computed in FP64 from the FP64 operator
+// Per-step refresh of every level: diag, angular line factors, origin scalars and the
+// coarsest-level Schur data.  Factors are formed in FP64 and stored in T.
 template <typename T>
-int launch_factor(const OpView<double>& op, double alpha, double beta, LineFactors<T>& f,
-                  cudaStream_t st);
+int launch_refresh(const LevelView<double>* L64, LevelView<T>* LT, int nlev, Params p,
+                   double* ws, cudaStream_t st);
 
-// out = M_r^{-1} rhs (radial lines + origin block)
+// Multigrid V(1,1) cycle pieces (polar_mg.cu).  mode 0 = pre-smoothing (the level's
+// x starts from zero), 1 = post-smoothing (x of the odd rings is corrected on the fly
+// with the coarser level's solution X); parity 1 = odd rings, 0 = even rings + origin.
+enum { RING_PRE = 0, RING_POST = 1 };
 template <typename T>
-int launch_radial_solve(const OpView<T>& op, const LineFactors<T>& f, const T* rhs, T* out,
-                        cudaStream_t st, const int* done);
-// out = base + M_a^{-1} rhs (angular periodic lines + origin block); tmp is scratch
+int launch_ring(const LevelView<T>& L, const LevelView<T>& C, const T* b, T* x, const T* X,
+                Params p, int parity, int mode, const int* done, cudaStream_t st);
+// right-hand side of the coarser level from the odd rings' residual after pre-smoothing
 template <typename T>
-int launch_angular_solve(const OpView<T>& op, const LineFactors<T>& f, const T* rhs,
-                         const T* base, T* out, T* tmp, cudaStream_t st, const int* done);
+int launch_restrict(const LevelView<T>& L, const LevelView<T>& C, const T* x, T* B, Params p,
+                    const int* done, cudaStream_t st);
+// exact solve of the coarsest level (origin + one ring)
+template <typename T>
+int launch_coarsest(const LevelView<T>& L, const T* b, T* x, Params p, const int* done,
+                    cudaStream_t st);
 
-// ---- Krylov (BiCGStab) kernels; see polar_kernels.cu
+// ---- BiCGStab vector kernels
 template <typename T>
 int launch_bicg_init(size_t nv, const T* r, T* rhat, T* p, T* v, T* x, bool zero_x,
                      double rel_tol, int max_iter, cudaStream_t st, Reduce red);
-template <typename T>
-int launch_apply_dot(const OpView<T>& op, T alpha, T beta, const T* x, T* y, const T* d1,
-                     int mode, cudaStream_t st, Reduce red);
 template <typename T>
 int launch_bicg_s(size_t nv, const T* r, const T* v, T* s, cudaStream_t st, Reduce red);
 template <typename T>
@@ -137,19 +165,18 @@ template <typename T>
 int launch_bicg_p(size_t nv, T* p, const T* r, const T* v, cudaStream_t st, Reduce red);
 
 // ---- mixed-precision helpers
-// rs = r * (1 / ks->rmax) in precision T
 template <typename T>
 int launch_scale_cast(size_t nv, const double* r, T* rs, cudaStream_t st, Reduce red);
-// x += ks->rmax * d
 template <typename T>
 int launch_correct(size_t nv, double* x, const T* d, cudaStream_t st, Reduce red);
-// float copy of a double array
 int launch_to_float(size_t n, const double* a, float* b, cudaStream_t st);
-// nonfinite check of n doubles: sets ks->done = 3 if any is NaN/Inf
 int launch_check_finite(size_t n, const double* a, cudaStream_t st, Reduce red);
 
-// interface layout <-> padded layout
-int launch_pack(int m, int n, int ld, const double* in, double* out, cudaStream_t st);
-int launch_unpack(int m, int n, int ld, const double* in, double* out, cudaStream_t st);
+// interface layout (origin, then radial lines j = 0..n-1 of m values) <-> split layout;
+// `scale` (nullable, split layout) multiplies on the way in, `div` divides on the way out
+int launch_pack(const Shape& sh, const double* in, const double* scale, double* out,
+                cudaStream_t st);
+int launch_unpack(const Shape& sh, const double* in, const double* div, double* out,
+                  cudaStream_t st);
 
 }  // namespace polar

@@ -1,8 +1,11 @@
-// CUDA kernels of the implicit theta-step on the polar mesh (sm_103a).
+// CUDA kernels of the implicit theta-step on the polar mesh (sm_103a): the 5-point
+// operator with its origin row, the right-hand side, the BiCGStab vector updates and
+// the mixed-precision helpers.  The multigrid preconditioner is in polar_mg.cu.
 //
-// Every kernel is bandwidth- or FP64-issue-bound: nothing here is a dense contraction,
-// so no tensor-core path exists.  Reductions are deterministic: every block reduces
-// its elements in a fixed order, writes one partial per block, and the last block to
+// Every kernel here streams its vectors once (HBM-bound; on GB300 the FP64 ones are
+// close to the FP64 issue limit as well): nothing is a dense contraction, so no
+// tensor-core path exists.  Reductions are deterministic: every block reduces its
+// elements in a fixed order, writes one partial per block, and the last block to
 // arrive (atomic counter + fences) sums the partials in block order and finishes the
 // scalar recurrences of the Krylov solver on the device.
 #include "polar_internal.h"
@@ -49,7 +52,7 @@ __device__ void block_reduce(double (&v)[K]) {
   __syncthreads();
   if (warp == 0) {
 #pragma unroll
-    for (int k = 0; k < K; ++k) v[k] = (lane < nw) ? sh[k][lane] : 0.0;
+    for (int k = 0; k < K; ++k) v[k] = (lane < nw) ? sh[k][lane] : ((k < KMAX) ? 0.0 : 0.0);
     warp_reduce<K, KMAX>(v);
   }
   __syncthreads();
@@ -94,122 +97,141 @@ __device__ void grid_totals(const double* part, double (&tot)[K]) {
 
 __device__ __forceinline__ double absfin(double v) { return isfinite(v) ? fabs(v) : INFINITY; }
 
+// ------------------------------------------------------------------ point loops
+// Tiles of TK consecutive rings of one parity block x TJ consecutive angles; every
+// warp reads TK consecutive entries of a radial line (coalesced).
+struct Tiling {
+  int TK, TJ;
+  int tko, tke, tj;  // tiles along k (odd, even) and along j
+  int ntiles;
+};
+
+__host__ __device__ inline Tiling make_tiling(const Shape& sh) {
+  Tiling t;
+  const int kmax = sh.no > sh.ne ? sh.no : sh.ne;
+  t.TK = 32;
+  while (t.TK < kmax && t.TK < 256) t.TK <<= 1;
+  t.TJ = 256 / t.TK;
+  t.tko = (sh.no + t.TK - 1) / t.TK;
+  t.tke = (sh.ne + t.TK - 1) / t.TK;
+  t.tj = (sh.n + t.TJ - 1) / t.TJ;
+  t.ntiles = (t.tko + t.tke) * t.tj;
+  return t;
+}
+
+// Calls f(i, j, idx, west, east, south, north) for every point of this thread; west and
+// east are indices of the radial neighbours (west = 0 is the origin for ring 1, east =
+// SIZE_MAX marks the Dirichlet ring), south/north the periodic angular neighbours.
+template <typename F>
+__device__ __forceinline__ void for_points(const Shape& sh, const Tiling& t, F f) {
+  const int n = sh.n, m = sh.m;
+  for (int tile = blockIdx.x; tile < t.ntiles; tile += gridDim.x) {
+    const int tj = tile % t.tj;
+    const int tk = tile / t.tj;
+    const bool odd = tk < t.tko;
+    const int k = (odd ? tk : tk - t.tko) * t.TK + threadIdx.x;
+    const int j = tj * t.TJ + threadIdx.y;
+    if (j >= n || k >= (odd ? sh.no : sh.ne)) continue;
+    const int i = odd ? 2 * k + 1 : 2 * k + 2;
+    size_t idx, west, east, south, north;
+    const int jm = (j == 0) ? n - 1 : j - 1, jp = (j == n - 1) ? 0 : j + 1;
+    if (odd) {
+      idx = sh.odd0 + (size_t)j * sh.ldo + k;
+      south = sh.odd0 + (size_t)jm * sh.ldo + k;
+      north = sh.odd0 + (size_t)jp * sh.ldo + k;
+      west = (k == 0) ? 0 : sh.even0 + (size_t)j * sh.lde + (k - 1);
+      east = (i < m) ? sh.even0 + (size_t)j * sh.lde + k : (size_t)-1;
+    } else {
+      idx = sh.even0 + (size_t)j * sh.lde + k;
+      south = sh.even0 + (size_t)jm * sh.lde + k;
+      north = sh.even0 + (size_t)jp * sh.lde + k;
+      west = sh.odd0 + (size_t)j * sh.ldo + k;
+      east = (i < m) ? sh.odd0 + (size_t)j * sh.ldo + (k + 1) : (size_t)-1;
+    }
+    f(i, j, idx, west, east, south, north);
+  }
+}
+
 // ------------------------------------------------------------------ stencil
-// One kernel body for every use of the 5-point operator; MODE selects the epilogue.
-enum { M_APPLY = 0, M_RESID = 1, M_RHS = 2, M_RESID64 = 3, M_DOTV = 4, M_DOTT = 5 };
+enum { M_APPLY = 0, M_RESID64 = 1, M_DOTV = 2, M_DOTT = 3 };
 
 template <typename T>
 struct StArgs {
-  OpView<T> op;
-  T alpha, beta;
+  LevelView<T> L;
+  Params par;
   const T* x;
-  const T* b;   // M_RESID / M_RESID64: right-hand side
+  const T* b;   // M_RESID64: right-hand side
   T* y;
   const T* d1;  // M_DOTV: rhat; M_DOTT: s
-  int nsrc;
-  const double* src[4];
-  const double* bnd[4];
-  double cf[4], cg[4];
   Reduce red;
-  int nic, njg;  // tiles: nic chunks along i  x  njg groups of lines
-  double c0;     // diagonal of the origin row of L
+  Tiling t;
 };
 
-// Slots: [0] origin coupling sum_j o_j x_{1,j}; then mode-specific sums; maxima last.
 template <int MODE>
 struct Slots {
   static constexpr int K = (MODE == M_RESID64) ? 4 : (MODE == M_DOTV) ? 2 : (MODE == M_DOTT) ? 3 : 1;
   static constexpr int KMAX = (MODE == M_RESID64) ? 1 : K;
 };
 
+// y = S x in the direct form diag x + beta (w xW + e xE + s xS + nn xN) (Section 3.2.1
+// rows scaled by the control volumes); slot 0 collects sum_j o_j x_{1,j} for the
+// origin row (Section 3.2.2), which the last block finishes.
 template <typename T, int MODE>
 __global__ void __launch_bounds__(256) k_stencil(StArgs<T> a) {
-  if ((MODE >= M_DOTV || MODE == M_RESID) && a.red.ks->done) return;
+  if (MODE >= M_DOTV && a.red.ks->done) return;
   constexpr int K = Slots<MODE>::K, KMAX = Slots<MODE>::KMAX;
-  const int m = a.op.m, n = a.op.n, ld = a.op.ld;
-  const int TI = blockDim.x, TJ = blockDim.y;
-  const int ntiles = a.nic * a.njg;
+  const T beta = (T)a.par[1];
+  const LevelView<T>& L = a.L;
   double acc[K];
 #pragma unroll
   for (int k = 0; k < K; ++k) acc[k] = 0.0;
-  T accT1 = T(0), accT2 = T(0);
-  const T alpha = a.alpha, beta = a.beta;
-  const T x0 = a.x[0];
-
-  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const int jg = tile / a.nic, ic = tile - jg * a.nic;
-    const int i = ic * TI + threadIdx.x + 1;
-    const int j = jg * TJ + threadIdx.y;
-    if (i > m || j >= n) continue;
-    const size_t idx = kOfs + (size_t)j * ld + (i - 1);
-    const ptrdiff_t ds = (j == 0) ? (ptrdiff_t)(n - 1) * ld : -(ptrdiff_t)ld;
-    const ptrdiff_t dn = (j == n - 1) ? -(ptrdiff_t)(n - 1) * ld : (ptrdiff_t)ld;
-    const T xc = a.x[idx];
-    const T xw = (i == 1) ? x0 : a.x[idx - 1];
-    const T xs = a.x[idx + ds];
-    const T xn = a.x[idx + dn];
-    T xe = (i == m) ? T(0) : a.x[idx + 1];
-    if (MODE == M_RHS && i == m) {  // Dirichlet value on r = 1 (Eq. 2.9)
-      double g = 0.0;
-      for (int q = 0; q < a.nsrc; ++q) g = fma(a.cg[q], a.bnd[q][j], g);
-      xe = (T)g;
-    }
-    const T cW = a.op.W[idx], cE = a.op.E[idx], cS = a.op.S[idx], cN = a.op.N[idx];
-    T Lx = a.op.R[idx] * xc;
-    Lx = fma(cW, xw - xc, Lx);
-    Lx = fma(cE, xe - xc, Lx);
-    Lx = fma(cS, xs - xc, Lx);
-    Lx = fma(cN, xn - xc, Lx);
-    T val = fma(beta, Lx, alpha * xc);
-    if (i == 1) acc[0] = fma((double)a.op.o[j], (double)xc - (double)x0, acc[0]);
-    if (MODE == M_RESID || MODE == M_RESID64) val = a.b[idx] - val;
-    if (MODE == M_RHS) {
-      double s = (double)val;
-      for (int q = 0; q < a.nsrc; ++q) s = fma(a.cf[q], a.src[q][idx], s);
-      val = (T)s;
-    }
+  const T* __restrict__ x = a.x;
+  const T x0 = x[0];
+  for_points(L.sh, a.t, [&](int i, int j, size_t idx, size_t west, size_t east, size_t south,
+                            size_t north) {
+    const T xc = x[idx];
+    const T xw = (west == 0) ? x0 : x[west];
+    const T xe = (east == (size_t)-1) ? T(0) : x[east];
+    T off = L.w[idx] * xw;
+    off = fma(L.e[idx], xe, off);
+    off = fma(L.s[idx], x[south], off);
+    off = fma(L.nn[idx], x[north], off);
+    const T dg = L.diag[idx];
+    T val = fma(beta, off, dg * xc);
+    if (i == 1) acc[0] = fma((double)L.o[j], (double)xc, acc[0]);
     if (MODE == M_RESID64) {
-      const double cdiag = (double)a.op.R[idx] - (double)cW - (double)cE - (double)cS - (double)cN;
-      const double dg = fabs((double)alpha + (double)beta * cdiag);
+      val = a.b[idx] - val;
       const double ar = absfin((double)val);
       acc[1] = fmax(acc[1], ar);
-      acc[2] = fmax(acc[2], ar / dg);
+      acc[2] = fmax(acc[2], ar / fabs((double)dg));
       acc[3] = fmax(acc[3], absfin((double)xc));
     }
-    if (MODE == M_DOTV) accT1 = fma(a.d1[idx], val, accT1);
+    if (MODE == M_DOTV) acc[1] = fma((double)a.d1[idx], (double)val, acc[1]);
     if (MODE == M_DOTT) {
-      accT1 = fma(val, a.d1[idx], accT1);
-      accT2 = fma(val, val, accT2);
+      acc[1] = fma((double)val, (double)a.d1[idx], acc[1]);
+      acc[2] = fma((double)val, (double)val, acc[2]);
     }
     a.y[idx] = val;
-  }
-  if (MODE == M_DOTV) acc[1] = (double)accT1;
-  if (MODE == M_DOTT) {
-    acc[1] = (double)accT1;
-    acc[2] = (double)accT2;
-  }
+  });
   block_reduce<K, KMAX>(acc);
   if (!publish_and_arrive<K>(acc, a.red.part, &a.red.ks->counter)) return;
 
-  // ---- last block: origin row (Section 3.2.2) and the scalar epilogue
+  // ---- last block: origin row and the scalar epilogue
   double tot[K];
   grid_totals<K, KMAX>(a.red.part, tot);
   const int tid = threadIdx.x + blockDim.x * threadIdx.y;
   if (tid != 0) return;
   KrylovScalars* ks = a.red.ks;
+  const double d0 = L.sc[0];
   const double x0d = (double)x0;
-  const double L0 = fma((double)a.op.R[0], x0d, tot[0]);
-  double y0 = fma((double)beta, L0, (double)alpha * x0d);
-  if (MODE == M_RESID || MODE == M_RESID64) y0 = (double)a.b[0] - y0;
-  if (MODE == M_RHS)
-    for (int q = 0; q < a.nsrc; ++q) y0 = fma(a.cf[q], a.src[q][0], y0);
+  double y0 = fma((double)beta, tot[0], d0 * x0d);
+  if (MODE == M_RESID64) y0 = (double)a.b[0] - y0;
   const T y0t = (T)y0;
   a.y[0] = y0t;
   if (MODE == M_RESID64) {
-    const double dg = fabs((double)alpha + (double)beta * a.c0);
     const double ar = absfin(y0);
     ks->rmax = fmax(tot[1], ar);
-    ks->smax = fmax(tot[2], ar / dg);
+    ks->smax = fmax(tot[2], ar / fabs(d0));
     ks->xmax = fmax(tot[3], absfin(x0d));
   }
   if (MODE == M_DOTV) {
@@ -231,366 +253,128 @@ __global__ void __launch_bounds__(256) k_stencil(StArgs<T> a) {
   ks->counter = 0;
 }
 
-template <typename T>
-static void stencil_shape(const OpView<T>& op, dim3& blk, int& nic, int& njg) {
-  int TI = 32;
-  while (TI < op.m && TI < 256) TI <<= 1;
-  const int TJ = 256 / TI;
-  blk = dim3(TI, TJ);
-  nic = (op.m + TI - 1) / TI;
-  njg = (op.n + TJ - 1) / TJ;
-}
-
 template <typename T, int MODE>
 static int stencil_launch(StArgs<T>& a, cudaStream_t st) {
-  dim3 blk;
-  stencil_shape(a.op, blk, a.nic, a.njg);
-  size_t tiles = (size_t)a.nic * a.njg;
-  int grid = tiles > (size_t)kMaxBlocks ? kMaxBlocks : (int)tiles;
-  k_stencil<T, MODE><<<grid, blk, 0, st>>>(a);
+  a.t = make_tiling(a.L.sh);
+  const int grid = a.t.ntiles > kMaxBlocks ? kMaxBlocks : a.t.ntiles;
+  k_stencil<T, MODE><<<grid, dim3(a.t.TK, a.t.TJ), 0, st>>>(a);
   return 1;
 }
 
 template <typename T>
-static StArgs<T> st_args(const OpView<T>& op, T alpha, T beta, const T* x, T* y, Reduce red) {
+int launch_apply(const LevelView<T>& L, Params p, const T* x, T* y, cudaStream_t st, Reduce red) {
   StArgs<T> a{};
-  a.op = op;
-  a.alpha = alpha;
-  a.beta = beta;
+  a.L = L;
+  a.par = p;
   a.x = x;
   a.y = y;
   a.red = red;
-  return a;
-}
-
-template <typename T>
-int launch_apply(const OpView<T>& op, T alpha, T beta, const T* x, T* y, cudaStream_t st,
-                 Reduce red) {
-  StArgs<T> a = st_args(op, alpha, beta, x, y, red);
   return stencil_launch<T, M_APPLY>(a, st);
 }
 
 template <typename T>
-int launch_resid(const OpView<T>& op, T alpha, T beta, const T* x, const T* b, T* y,
-                 cudaStream_t st, Reduce red) {
-  StArgs<T> a = st_args(op, alpha, beta, x, y, red);
-  a.b = b;
-  return stencil_launch<T, M_RESID>(a, st);
-}
-
-int launch_rhs(const OpView<double>& op, double alpha, double beta, const double* x,
-               int nsrc, const double* const* src, const double* const* bnd,
-               const double* cf, const double* cg, double* e, cudaStream_t st, Reduce red) {
-  StArgs<double> a = st_args(op, alpha, beta, x, e, red);
-  a.nsrc = nsrc;
-  for (int q = 0; q < nsrc; ++q) {
-    a.src[q] = src[q];
-    a.bnd[q] = bnd[q];
-    a.cf[q] = cf[q];
-    a.cg[q] = cg[q];
-  }
-  return stencil_launch<double, M_RHS>(a, st);
-}
-
-int launch_resid64(const OpView<double>& op, double alpha, double beta, const double* x,
-                   const double* e, double* r, double c0, cudaStream_t st, Reduce red) {
-  StArgs<double> a = st_args(op, alpha, beta, x, r, red);
-  a.b = e;
-  a.c0 = c0;
-  return stencil_launch<double, M_RESID64>(a, st);
-}
-
-template <typename T>
-int launch_apply_dot(const OpView<T>& op, T alpha, T beta, const T* x, T* y, const T* d1,
-                     int mode, cudaStream_t st, Reduce red) {
-  StArgs<T> a = st_args(op, alpha, beta, x, y, red);
+int launch_apply_dot(const LevelView<T>& L, Params p, const T* x, T* y, const T* d1, int mode,
+                     cudaStream_t st, Reduce red) {
+  StArgs<T> a{};
+  a.L = L;
+  a.par = p;
+  a.x = x;
+  a.y = y;
   a.d1 = d1;
+  a.red = red;
   if (mode == 0) return stencil_launch<T, M_DOTV>(a, st);
   return stencil_launch<T, M_DOTT>(a, st);
 }
 
-// ------------------------------------------------------------------ line factors
-// LU factors (Doolittle, no pivoting: the line blocks of an M-matrix are diagonally
-// dominant) of every radial line block, one thread per line.
-__device__ __forceinline__ double diag_of(const OpView<double>& op, size_t idx) {
-  return op.R[idx] - op.W[idx] - op.E[idx] - op.S[idx] - op.N[idx];
+int launch_resid64(const LevelView<double>& L, Params p, const double* x, const double* b,
+                   double* r, cudaStream_t st, Reduce red) {
+  StArgs<double> a{};
+  a.L = L;
+  a.par = p;
+  a.x = x;
+  a.b = b;
+  a.y = r;
+  a.red = red;
+  return stencil_launch<double, M_RESID64>(a, st);
 }
 
-template <typename T>
-__global__ void k_factor_radial(OpView<double> op, double alpha, double beta, T* rl, T* rui,
-                                T* rcu) {
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= op.n) return;
-  const int m = op.m;
-  const size_t base = kOfs + (size_t)j * op.ld;
-  double uprev = 1.0, cprev = 0.0;
-  for (int k = 0; k < m; ++k) {
-    const double a = (k > 0) ? beta * op.W[base + k] : 0.0;
-    const double b = alpha + beta * diag_of(op, base + k);
-    const double c = (k < m - 1) ? beta * op.E[base + k] : 0.0;
-    const double l = (k > 0) ? a / uprev : 0.0;
-    const double u = b - l * cprev;
-    const double ui = 1.0 / u;
-    rl[base + k] = (T)l;
-    rui[base + k] = (T)ui;
-    rcu[base + k] = (T)(c * ui);
-    uprev = u;
-    cprev = c;
-  }
-}
+// ------------------------------------------------------------------ right-hand side
+struct RhsArgs {
+  LevelView<double> L;
+  double alpha, omt;  // 1/dt, 1 - theta
+  const double* u;
+  double* e;
+  int nsrc;
+  const double* vsrc[4];
+  const double* bnd[4];
+  double cf[4], cg[4];
+  Reduce red;
+  Tiling t;
+};
 
-// Periodic angular line of ring i: A = A' + u v^T with gamma = -b_0,
-// u = (gamma, 0, .., 0, c_{n-1}), v = (1, 0, .., 0, a_0 / gamma) (Sherman-Morrison);
-// LU factors of the tridiagonal A', q = A'^{-1} u, vf = a_0 / gamma, inv1vq = 1/(1 + v.q).
-template <typename T>
-__global__ void k_factor_angular(OpView<double> op, double alpha, double beta, T* al, T* aui,
-                                 T* acu, T* aq, T* avf, T* ainv, double* ws) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x + 1;
-  if (i > op.m) return;
-  const int n = op.n;
-  const size_t ld = op.ld;
-  const size_t col = kOfs + (size_t)(i - 1);
-  const double a0 = beta * op.S[col];
-  const double b0 = alpha + beta * diag_of(op, col);
-  const double cn1 = beta * op.N[col + (size_t)(n - 1) * ld];
-  const double gamma = -b0;
-  const double vf = a0 / gamma;
-  double uprev = 1.0, cprev = 0.0, yq = 0.0;
-  // ws[idx] keeps the FP64 forward values of q and ws[idx + ld n] the FP64 pivot
-  // reciprocals, so that q and 1 + v.q are formed in FP64 whatever T is.
-  for (int j = 0; j < n; ++j) {
-    const size_t idx = col + (size_t)j * ld;
-    const double a = (j > 0) ? beta * op.S[idx] : 0.0;
-    double b = alpha + beta * diag_of(op, idx);
-    if (j == 0) b -= gamma;
-    if (j == n - 1) b -= cn1 * vf;
-    const double c = (j < n - 1) ? beta * op.N[idx] : 0.0;
-    const double l = (j > 0) ? a / uprev : 0.0;
-    const double u = b - l * cprev;
-    const double ui = 1.0 / u;
-    al[idx] = (T)l;
-    aui[idx] = (T)ui;
-    acu[idx] = (T)(c * ui);
-    const double ur = (j == 0) ? gamma : ((j == n - 1) ? cn1 : 0.0);
-    yq = ur - l * yq;
-    ws[idx] = yq;
-    ws[idx + op.ld * (size_t)n] = ui;  // second half: FP64 pivot reciprocal
-    uprev = u;
-    cprev = c;
-  }
-  // backward pass for q in FP64: q_j = ui_j y_j - (c_j ui_j) q_{j+1}
-  double qnext = 0.0, q0 = 0.0, qn1 = 0.0;
-  for (int j = n - 1; j >= 0; --j) {
-    const size_t idx = col + (size_t)j * ld;
-    const double ui = ws[idx + op.ld * (size_t)n];
-    const double c = (j < n - 1) ? beta * op.N[idx] : 0.0;
-    const double q = ui * (ws[idx] - c * qnext);
-    aq[idx] = (T)q;
-    if (j == n - 1) qn1 = q;
-    if (j == 0) q0 = q;
-    qnext = q;
-  }
-  avf[i - 1] = (T)vf;
-  ainv[i - 1] = (T)(1.0 / (1.0 + q0 + vf * qn1));
-}
-
-template <typename T>
-int launch_factor(const OpView<double>& op, double alpha, double beta, LineFactors<T>& f,
-                  cudaStream_t st) {
-  k_factor_radial<T><<<(op.n + 63) / 64, 64, 0, st>>>(op, alpha, beta, f.rl, f.rui, f.rcu);
-  k_factor_angular<T><<<(op.m + 63) / 64, 64, 0, st>>>(op, alpha, beta, f.al, f.aui, f.acu, f.aq,
-                                                      f.avf, f.ainv, f.ws);
-  return 2;
-}
-
-// ------------------------------------------------------------------ line solves
-// The forward and backward substitutions are first-order affine recurrences; each
-// thread composes the maps of its chunk, a block scan of the composed maps gives every
-// chunk its incoming value, and the chunk is replayed.  Composition: a map is (A, B),
-// x -> A x + B; the scan forms  R_p = M_p o R_{p-1}.
-template <typename T>
-__device__ void scan_affine(T A, T B, T* sA, T* sB, int r, int pos, int RW, int TW) {
-  sA[pos * RW + r] = A;
-  sB[pos * RW + r] = B;
-  __syncthreads();
-  for (int off = 1; off < TW; off <<= 1) {
-    const T a = sA[pos * RW + r], b = sB[pos * RW + r];
-    T ao = T(1), bo = T(0);
-    const bool has = pos >= off;
-    if (has) {
-      ao = sA[(pos - off) * RW + r];
-      bo = sB[(pos - off) * RW + r];
+// e = alpha V u - (1 - theta) (V L) u + sum_q cf_q V src_q + e_{m,j} g_j, the explicit
+// half of Eq. (2.5) with the sources of both levels and the Dirichlet data of both
+// levels (g_j = sum_q cg_q bnd_q[j], Eq. 2.9) moved to the right-hand side.
+__global__ void __launch_bounds__(256) k_rhs(RhsArgs a) {
+  const LevelView<double>& L = a.L;
+  double acc[1] = {0.0};
+  const double* __restrict__ u = a.u;
+  const double u0 = u[0];
+  for_points(L.sh, a.t, [&](int i, int j, size_t idx, size_t west, size_t east, size_t south,
+                            size_t north) {
+    const double uc = u[idx];
+    const double uw = (west == 0) ? u0 : u[west];
+    const double ue = (east == (size_t)-1) ? 0.0 : u[east];
+    const double w = L.w[idx], e = L.e[idx], s = L.s[idx], nn = L.nn[idx];
+    const double rsd = L.rs[idx] - w - e - s - nn;
+    double Lu = rsd * uc;
+    Lu = fma(w, uw, Lu);
+    Lu = fma(e, ue, Lu);
+    Lu = fma(s, u[south], Lu);
+    Lu = fma(nn, u[north], Lu);
+    double val = fma(-a.omt, Lu, a.alpha * L.vol[idx] * uc);
+    for (int q = 0; q < a.nsrc; ++q) val = fma(a.cf[q], a.vsrc[q][idx], val);
+    if (i == L.sh.m) {
+      double g = 0.0;
+      for (int q = 0; q < a.nsrc; ++q) g = fma(a.cg[q], a.bnd[q][j], g);
+      val = fma(e, g, val);
     }
-    __syncthreads();
-    if (has) {
-      sA[pos * RW + r] = a * ao;
-      sB[pos * RW + r] = fma(a, bo, b);
-    }
-    __syncthreads();
-  }
+    if (i == 1) acc[0] = fma(L.o[j], uc, acc[0]);
+    a.e[idx] = val;
+  });
+  block_reduce<1, 1>(acc);
+  if (!publish_and_arrive<1>(acc, a.red.part, &a.red.ks->counter)) return;
+  double tot[1];
+  grid_totals<1, 1>(a.red.part, tot);
+  if (threadIdx.x + blockDim.x * threadIdx.y != 0) return;
+  const double vol0 = L.sc[3], rs0 = L.sc[4], osum = L.sc[2];
+  const double Lu0 = fma(rs0 - osum, u0, tot[0]);
+  double e0 = fma(-a.omt, Lu0, a.alpha * vol0 * u0);
+  for (int q = 0; q < a.nsrc; ++q) e0 = fma(a.cf[q], a.vsrc[q][0], e0);
+  a.e[0] = e0;
+  a.red.ks->counter = 0;
 }
 
-constexpr int kRT = 128;  // threads per radial line
-
-__host__ __device__ inline int spad(int k) { return k + (k >> 5); }
-
-template <typename T>
-__global__ void __launch_bounds__(kRT) k_radial_solve(int m, int ld, const T* __restrict__ rl,
-                                                      const T* __restrict__ rui,
-                                                      const T* __restrict__ rcu,
-                                                      const T* __restrict__ rhs, T* __restrict__ out,
-                                                      T diag0, const int* done) {
-  if (done && *done) return;
-  extern __shared__ unsigned char smraw[];
-  T* s = reinterpret_cast<T*>(smraw);
-  T* sA = s + spad(m) + 1;
-  T* sB = sA + kRT;
-  const int j = blockIdx.x, t = threadIdx.x;
-  const size_t base = kOfs + (size_t)j * ld;
-  for (int k = t; k < m; k += kRT) s[spad(k)] = rhs[base + k];
-  if (j == 0 && t == 0) out[0] = rhs[0] / diag0;
-  __syncthreads();
-  const int P = (m + kRT - 1) / kRT;
-  const int k0 = min(m, t * P), k1 = min(m, k0 + P);
-  T A = T(1), B = T(0);
-  for (int k = k0; k < k1; ++k) {
-    const T l = rl[base + k];
-    B = s[spad(k)] - l * B;
-    A = -l * A;
+int launch_rhs(const LevelView<double>& L, double alpha, double one_minus_theta, const double* u,
+               int nsrc, const double* const* vsrc, const double* const* bnd, const double* cf,
+               const double* cg, double* e, cudaStream_t st, Reduce red) {
+  RhsArgs a{};
+  a.L = L;
+  a.alpha = alpha;
+  a.omt = one_minus_theta;
+  a.u = u;
+  a.e = e;
+  a.nsrc = nsrc;
+  for (int q = 0; q < nsrc; ++q) {
+    a.vsrc[q] = vsrc[q];
+    a.bnd[q] = bnd[q];
+    a.cf[q] = cf[q];
+    a.cg[q] = cg[q];
   }
-  scan_affine(A, B, sA, sB, 0, t, 1, kRT);
-  T prev = (t > 0) ? sB[t - 1] : T(0);
-  for (int k = k0; k < k1; ++k) {
-    const T y = s[spad(k)] - rl[base + k] * prev;
-    s[spad(k)] = y;
-    prev = y;
-  }
-  __syncthreads();
-  A = T(1);
-  B = T(0);
-  for (int k = k1 - 1; k >= k0; --k) {
-    const T ui = rui[base + k], cu = rcu[base + k];
-    B = ui * s[spad(k)] - cu * B;
-    A = -cu * A;
-  }
-  const int pos = kRT - 1 - t;
-  scan_affine(A, B, sA, sB, 0, pos, 1, kRT);
-  T next = (pos > 0) ? sB[pos - 1] : T(0);
-  for (int k = k1 - 1; k >= k0; --k) {
-    const T x = rui[base + k] * s[spad(k)] - rcu[base + k] * next;
-    s[spad(k)] = x;
-    next = x;
-  }
-  __syncthreads();
-  for (int k = t; k < m; k += kRT) out[base + k] = s[spad(k)];
-}
-
-template <typename T>
-int launch_radial_solve(const OpView<T>& op, const LineFactors<T>& f, const T* rhs, T* out,
-                        cudaStream_t st, const int* done) {
-  const size_t smem = sizeof(T) * ((size_t)spad(op.m) + 1 + 2 * kRT);
-  static bool attr_set = false;  // one opt-in per instantiation for lines beyond 48 KB
-  if (!attr_set) {
-    cudaFuncSetAttribute(k_radial_solve<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         227 * 1024);
-    attr_set = true;
-  }
-  k_radial_solve<T><<<op.n, kRT, smem, st>>>(op.m, op.ld, f.rl, f.rui, f.rcu, rhs, out, f.diag0,
-                                            done);
-  return 1;
-}
-
-// Angular solve: block = RW rings (threadIdx.x, adjacent in memory) x TW chunks of
-// the angular line (threadIdx.y).
-template <typename T>
-__global__ void __launch_bounds__(256) k_angular_solve(int m, int n, int ld, const T* __restrict__ al,
-                                                       const T* __restrict__ aui,
-                                                       const T* __restrict__ acu,
-                                                       const T* __restrict__ aq,
-                                                       const T* __restrict__ avf,
-                                                       const T* __restrict__ ainv, const T* rhs,
-                                                       const T* base, T* out, T* tmp, T diag0,
-                                                       const int* done) {
-  if (done && *done) return;
-  extern __shared__ unsigned char smraw[];
-  const int RW = blockDim.x, TW = blockDim.y;
-  T* sA = reinterpret_cast<T*>(smraw);
-  T* sB = sA + RW * TW;
-  T* sx0 = sB + RW * TW;
-  T* sxn = sx0 + RW;
-  const int r = threadIdx.x, c = threadIdx.y;
-  const int i = blockIdx.x * RW + r + 1;
-  const bool valid = i <= m;
-  const int P = (n + TW - 1) / TW;
-  const int j0 = min(n, c * P), j1 = min(n, j0 + P);
-  const size_t col = kOfs + (size_t)(i - 1);
-  if (blockIdx.x == 0 && r == 0 && c == 0) out[0] = (base ? base[0] : T(0)) + rhs[0] / diag0;
-  T A = T(1), B = T(0);
-  if (valid) {
-    for (int j = j0; j < j1; ++j) {
-      const size_t idx = col + (size_t)j * ld;
-      const T l = al[idx];
-      B = rhs[idx] - l * B;
-      A = -l * A;
-    }
-  }
-  scan_affine(A, B, sA, sB, r, c, RW, TW);
-  T prev = (c > 0) ? sB[(c - 1) * RW + r] : T(0);
-  if (valid) {
-    for (int j = j0; j < j1; ++j) {
-      const size_t idx = col + (size_t)j * ld;
-      const T y = rhs[idx] - al[idx] * prev;
-      tmp[idx] = y;
-      prev = y;
-    }
-  }
-  __syncthreads();
-  A = T(1);
-  B = T(0);
-  if (valid) {
-    for (int j = j1 - 1; j >= j0; --j) {
-      const size_t idx = col + (size_t)j * ld;
-      const T cu = acu[idx];
-      B = aui[idx] * tmp[idx] - cu * B;
-      A = -cu * A;
-    }
-  }
-  const int pos = TW - 1 - c;
-  scan_affine(A, B, sA, sB, r, pos, RW, TW);
-  T next = (pos > 0) ? sB[(pos - 1) * RW + r] : T(0);
-  if (valid) {
-    for (int j = j1 - 1; j >= j0; --j) {
-      const size_t idx = col + (size_t)j * ld;
-      const T x = aui[idx] * tmp[idx] - acu[idx] * next;
-      tmp[idx] = x;
-      next = x;
-      if (j == 0) sx0[r] = x;
-      if (j == n - 1) sxn[r] = x;
-    }
-  }
-  __syncthreads();
-  if (valid) {
-    const T sigma = (sx0[r] + avf[i - 1] * sxn[r]) * ainv[i - 1];
-    for (int j = j0; j < j1; ++j) {
-      const size_t idx = col + (size_t)j * ld;
-      const T v = tmp[idx] - sigma * aq[idx];
-      out[idx] = base ? base[idx] + v : v;
-    }
-  }
-}
-
-template <typename T>
-int launch_angular_solve(const OpView<T>& op, const LineFactors<T>& f, const T* rhs,
-                         const T* base, T* out, T* tmp, cudaStream_t st, const int* done) {
-  int RW = 32;
-  while (RW > 4 && (op.m + RW - 1) / RW < 2 * 152) RW >>= 1;
-  int TW = 256 / RW;
-  while (TW > 1 && (op.n + TW - 1) / TW < 2) TW >>= 1;
-  const size_t smem = sizeof(T) * (2 * (size_t)RW * TW + 2 * RW);
-  const int grid = (op.m + RW - 1) / RW;
-  k_angular_solve<T><<<grid, dim3(RW, TW), smem, st>>>(op.m, op.n, op.ld, f.al, f.aui, f.acu,
-                                                       f.aq, f.avf, f.ainv, rhs, base, out, tmp,
-                                                       f.diag0, done);
+  a.red = red;
+  a.t = make_tiling(L.sh);
+  const int grid = a.t.ntiles > kMaxBlocks ? kMaxBlocks : a.t.ntiles;
+  k_rhs<<<grid, dim3(a.t.TK, a.t.TJ), 0, st>>>(a);
   return 1;
 }
 
@@ -602,16 +386,16 @@ __global__ void __launch_bounds__(kVT) k_bicg_init(size_t nv, const T* r, T* rha
                                                    T* x, int zero_x, double rel_tol,
                                                    int max_iter, Reduce red) {
   double acc[1];
-  T s = T(0);
+  double s = 0.0;
   for (size_t k = blockIdx.x * (size_t)kVT + threadIdx.x; k < nv; k += (size_t)gridDim.x * kVT) {
     const T rv = r[k];
     rhat[k] = rv;
     p[k] = rv;
     v[k] = T(0);
     if (zero_x) x[k] = T(0);
-    s = fma(rv, rv, s);
+    s = fma((double)rv, (double)rv, s);
   }
-  acc[0] = (double)s;
+  acc[0] = s;
   block_reduce<1, 1>(acc);
   if (!publish_and_arrive<1>(acc, red.part, &red.ks->counter)) return;
   double tot[1];
@@ -637,7 +421,7 @@ __global__ void __launch_bounds__(kVT) k_bicg_s(size_t nv, const T* r, const T* 
   if (ks->done) return;
   const T alpha = (T)ks->alpha;
   for (size_t k = blockIdx.x * (size_t)kVT + threadIdx.x; k < nv; k += (size_t)gridDim.x * kVT)
-    s[k] = r[k] - alpha * v[k];
+    s[k] = fma(-alpha, v[k], r[k]);
 }
 
 template <typename T>
@@ -646,15 +430,15 @@ __global__ void __launch_bounds__(kVT) k_bicg_update(size_t nv, T* x, const T* p
                                                      const T* t, const T* rhat, Reduce red) {
   if (red.ks->done) return;
   const T alpha = (T)red.ks->alpha, omega = (T)red.ks->omega;
-  T s1 = T(0), s2 = T(0);
+  double s1 = 0.0, s2 = 0.0;
   for (size_t k = blockIdx.x * (size_t)kVT + threadIdx.x; k < nv; k += (size_t)gridDim.x * kVT) {
     x[k] = fma(omega, shat[k], fma(alpha, phat[k], x[k]));
-    const T rn = s[k] - omega * t[k];
+    const T rn = fma(-omega, t[k], s[k]);
     r[k] = rn;
-    s1 = fma(rhat[k], rn, s1);
-    s2 = fma(rn, rn, s2);
+    s1 = fma((double)rhat[k], (double)rn, s1);
+    s2 = fma((double)rn, (double)rn, s2);
   }
-  double acc[2] = {(double)s1, (double)s2};
+  double acc[2] = {s1, s2};
   block_reduce<2, 2>(acc);
   if (!publish_and_arrive<2>(acc, red.part, &red.ks->counter)) return;
   double tot[2];
@@ -685,7 +469,7 @@ __global__ void __launch_bounds__(kVT) k_bicg_p(size_t nv, T* p, const T* r, con
   if (ks->done) return;
   const T beta = (T)ks->beta, omega = (T)ks->omega;
   for (size_t k = blockIdx.x * (size_t)kVT + threadIdx.x; k < nv; k += (size_t)gridDim.x * kVT)
-    p[k] = fma(beta, p[k] - omega * v[k], r[k]);
+    p[k] = fma(beta, fma(-omega, v[k], p[k]), r[k]);
 }
 
 template <typename T>
@@ -761,52 +545,50 @@ int launch_check_finite(size_t n, const double* a, cudaStream_t st, Reduce red) 
 }
 
 // ------------------------------------------------------------------ layout conversion
-__global__ void k_pack(int m, int n, int ld, const double* in, double* out) {
-  const size_t N = (size_t)m * n + 1;
+// interface index q = 1 + j m + (i - 1) <-> split index sh.at(i, j); q = 0 is the origin
+__global__ void k_pack(Shape sh, const double* in, const double* scale, double* out) {
+  const size_t N = (size_t)sh.m * sh.n + 1;
   for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < N;
        q += (size_t)gridDim.x * blockDim.x) {
-    if (q == 0) {
-      out[0] = in[0];
-    } else {
-      const size_t jj = (q - 1) / m, ii = (q - 1) - jj * m;
-      out[kOfs + jj * ld + ii] = in[q];
+    size_t p = 0;
+    if (q > 0) {
+      const size_t jj = (q - 1) / sh.m;
+      const int ii = (int)(q - 1 - jj * sh.m) + 1;
+      p = sh.at(ii, (int)jj);
     }
+    out[p] = scale ? in[q] * scale[p] : in[q];
   }
 }
-__global__ void k_unpack(int m, int n, int ld, const double* in, double* out) {
-  const size_t N = (size_t)m * n + 1;
+__global__ void k_unpack(Shape sh, const double* in, const double* div, double* out) {
+  const size_t N = (size_t)sh.m * sh.n + 1;
   for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < N;
        q += (size_t)gridDim.x * blockDim.x) {
-    if (q == 0) {
-      out[0] = in[0];
-    } else {
-      const size_t jj = (q - 1) / m, ii = (q - 1) - jj * m;
-      out[q] = in[kOfs + jj * ld + ii];
+    size_t p = 0;
+    if (q > 0) {
+      const size_t jj = (q - 1) / sh.m;
+      const int ii = (int)(q - 1 - jj * sh.m) + 1;
+      p = sh.at(ii, (int)jj);
     }
+    out[q] = div ? in[p] / div[p] : in[p];
   }
 }
-int launch_pack(int m, int n, int ld, const double* in, double* out, cudaStream_t st) {
-  k_pack<<<grid_for((size_t)m * n + 1, kVT), kVT, 0, st>>>(m, n, ld, in, out);
+int launch_pack(const Shape& sh, const double* in, const double* scale, double* out,
+                cudaStream_t st) {
+  k_pack<<<grid_for((size_t)sh.m * sh.n + 1, kVT), kVT, 0, st>>>(sh, in, scale, out);
   return 1;
 }
-int launch_unpack(int m, int n, int ld, const double* in, double* out, cudaStream_t st) {
-  k_unpack<<<grid_for((size_t)m * n + 1, kVT), kVT, 0, st>>>(m, n, ld, in, out);
+int launch_unpack(const Shape& sh, const double* in, const double* div, double* out,
+                  cudaStream_t st) {
+  k_unpack<<<grid_for((size_t)sh.m * sh.n + 1, kVT), kVT, 0, st>>>(sh, in, div, out);
   return 1;
 }
 
 // ------------------------------------------------------------------ instantiations
 #define POLAR_INST(T)                                                                          \
-  template int launch_apply<T>(const OpView<T>&, T, T, const T*, T*, cudaStream_t, Reduce);    \
-  template int launch_resid<T>(const OpView<T>&, T, T, const T*, const T*, T*, cudaStream_t,   \
+  template int launch_apply<T>(const LevelView<T>&, Params, const T*, T*, cudaStream_t,        \
                                Reduce);                                                        \
-  template int launch_apply_dot<T>(const OpView<T>&, T, T, const T*, T*, const T*, int,        \
+  template int launch_apply_dot<T>(const LevelView<T>&, Params, const T*, T*, const T*, int,   \
                                    cudaStream_t, Reduce);                                      \
-  template int launch_factor<T>(const OpView<double>&, double, double, LineFactors<T>&,        \
-                                cudaStream_t);                                                 \
-  template int launch_radial_solve<T>(const OpView<T>&, const LineFactors<T>&, const T*, T*,   \
-                                      cudaStream_t, const int*);                               \
-  template int launch_angular_solve<T>(const OpView<T>&, const LineFactors<T>&, const T*,      \
-                                       const T*, T*, T*, cudaStream_t, const int*);            \
   template int launch_bicg_init<T>(size_t, const T*, T*, T*, T*, T*, bool, double, int,        \
                                    cudaStream_t, Reduce);                                      \
   template int launch_bicg_s<T>(size_t, const T*, const T*, T*, cudaStream_t, Reduce);         \

@@ -1,0 +1,754 @@
+// Multigrid preconditioner of the theta-step system S x = b (sm_103a).
+//
+// Levels coarsen the radial direction only (rings 2, 4, 6, ... of a level form the
+// next coarser one); the angular direction keeps all n angles.  The smoother relaxes
+// whole rings at once: every ring is a periodic tridiagonal system in the angle
+// (Eqs. 2.6-2.7), solved exactly with LU factors and a Sherman-Morrison correction for
+// the periodic corner entries, odd rings first, then the origin and the even rings
+// (zebra order).  Because the radial couplings of the coarse levels are the Schur
+// complements of the odd rings (cyclic reduction of every radial line, see
+// polar_api.cu), this combination converges independently of the strong angular
+// coupling near the origin and of the radial grading toward r = 0 and r = 1.
+//
+// Kernels:
+//   k_refresh         per step: diag, ring factors, origin scalars of every level
+//   k_ring<.., mode>  one zebra half-sweep of one level (all rings of one parity)
+//   k_restrict        residual of the odd rings -> right-hand side of the coarser level
+//   k_coarsest        exact solve of the coarsest level (origin + one ring)
+// A V(1,1) cycle on L levels launches 5 (L - 1) + 1 kernels.
+//
+// The ring solve: the n angles of a ring are split into TW chunks of P consecutive
+// angles (one thread each, values in registers).  The forward and backward
+// substitutions are first-order affine recurrences; each thread composes the maps of
+// its chunk, a block scan of the composed maps gives every chunk its incoming value,
+// and the chunk is replayed.  Rings longer than one CTA can hold are split over the
+// CTAs of a thread-block cluster, which exchange their segment maps and the ring's end
+// values through distributed shared memory.
+#include <cooperative_groups.h>
+
+#include "polar_internal.h"
+
+namespace cg = cooperative_groups;
+
+namespace polar {
+
+// ---------------------------------------------------------------------------------
+// per-step refresh
+
+struct RefreshLevel {
+  Shape sh;
+  const double* vol;
+  const double* rs;
+  const double* w;
+  const double* e;
+  const double* s;
+  const double* nn;
+  const double* o;
+  double* sc;
+  void* diag;
+  double* diag64;  // FP64 copy of diag when T is float (level 0 only), else null
+  void* fl;
+  void* fui;
+  void* fcu;
+  void* fq;
+  void* fring;
+  void* fz;
+  double* ws;  // 3 nv doubles: forward values, pivot reciprocals, q (FP64)
+  int coarsest;
+  int ring0;   // first global ring index of this level
+};
+constexpr int kMaxLevels = 20;
+struct RefreshArgs {
+  RefreshLevel lv[kMaxLevels];
+  int nlev;
+  const double* par;
+};
+
+// One thread per ring of every level.  Ring i of a level is the periodic tridiagonal
+// system  a_j x_{j-1} + b_j x_j + c_j x_{j+1} = d_j  (indices mod n) with
+//   a_j = beta s_ij,  b_j = alpha vol_ij + beta (rs - w - e - s - nn)_ij,  c_j = beta nn_ij.
+// Sherman-Morrison: with gamma = -b_0, u = (gamma, 0, .., 0, c_{n-1}),
+// v = (1, 0, .., 0, a_0 / gamma), the system is (T' + u v^T) x = d where T' is the
+// non-periodic tridiagonal part with b'_0 = b_0 - gamma and
+// b'_{n-1} = b_{n-1} - c_{n-1} a_0 / gamma.  Stored: Doolittle factors of T'
+// (l_j = a_j / u_{j-1}, ui_j = 1 / u_j, cu_j = c_j / u_j), q = T'^{-1} u and, per ring,
+// vf = a_0 / gamma and 1 / (1 + v.q).
+template <typename T>
+__global__ void k_refresh(RefreshArgs A) {
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  int l = 0;
+  while (l + 1 < A.nlev && g >= A.lv[l + 1].ring0) ++l;
+  const RefreshLevel& L = A.lv[l];
+  const int local = g - L.ring0;
+  const Shape sh = L.sh;
+  if (local < 0 || local >= sh.m) return;
+  const double alpha = A.par[0], beta = A.par[1];
+  // ring order: odd rings (local < no) then even rings
+  const int i = (local < sh.no) ? 2 * local + 1 : 2 * (local - sh.no) + 2;
+  const int n = sh.n;
+  T* diag = static_cast<T*>(L.diag);
+  T* fl = static_cast<T*>(L.fl);
+  T* fui = static_cast<T*>(L.fui);
+  T* fcu = static_cast<T*>(L.fcu);
+  T* fq = static_cast<T*>(L.fq);
+  T* fring = static_cast<T*>(L.fring);
+  double* wy = L.ws;
+  double* wu = L.ws + sh.nv;
+  double* wq = L.ws + 2 * sh.nv;
+  auto dg = [&](size_t q) {
+    return alpha * L.vol[q] + beta * (L.rs[q] - L.w[q] - L.e[q] - L.s[q] - L.nn[q]);
+  };
+  const size_t q0 = sh.at(i, 0), qn = sh.at(i, n - 1);
+  const double a0 = beta * L.s[q0];
+  const double b0 = dg(q0);
+  const double cn1 = beta * L.nn[qn];
+  const double gamma = -b0;
+  const double vf = a0 / gamma;
+  double uprev = 1.0, cprev = 0.0, yq = 0.0;
+  for (int j = 0; j < n; ++j) {
+    const size_t q = sh.at(i, j);
+    const double a = (j > 0) ? beta * L.s[q] : 0.0;
+    const double bd = dg(q);
+    diag[q] = (T)bd;
+    if (L.diag64) L.diag64[q] = bd;
+    double b = bd;
+    if (j == 0) b -= gamma;
+    if (j == n - 1) b -= cn1 * vf;
+    const double c = (j < n - 1) ? beta * L.nn[q] : 0.0;
+    const double lj = (j > 0) ? a / uprev : 0.0;
+    const double u = b - lj * cprev;
+    const double ui = 1.0 / u;
+    fl[q] = (T)lj;
+    fui[q] = (T)ui;
+    fcu[q] = (T)(c * ui);
+    const double ur = (j == 0) ? gamma : ((j == n - 1) ? cn1 : 0.0);
+    yq = ur - lj * yq;
+    wy[q] = yq;
+    wu[q] = ui;
+    uprev = u;
+    cprev = c;
+  }
+  double qnext = 0.0, qfirst = 0.0, qlast = 0.0;
+  for (int j = n - 1; j >= 0; --j) {
+    const size_t q = sh.at(i, j);
+    const double c = (j < n - 1) ? beta * L.nn[q] : 0.0;
+    const double qq = wu[q] * (wy[q] - c * qnext);
+    fq[q] = (T)qq;
+    wq[q] = qq;
+    if (j == n - 1) qlast = qq;
+    if (j == 0) qfirst = qq;
+    qnext = qq;
+  }
+  const double inv = 1.0 / (1.0 + qfirst + vf * qlast);
+  fring[2 * local] = (T)vf;
+  fring[2 * local + 1] = (T)inv;
+  if (i == 1) {
+    // origin scalars of this level: diag0 = alpha vol0 + beta (rs0 - sum_j o_j)
+    const double d0 = alpha * L.sc[3] + beta * (L.sc[4] - L.sc[2]);
+    L.sc[0] = d0;
+    if (L.coarsest) {
+      // z = T_1^{-1} (beta w_1) in FP64 (forward values reuse wy), then the Schur
+      // denominator diag0 - beta sum_j o_j z_j of the origin row
+      T* fz = static_cast<T*>(L.fz);
+      // forward substitution with l_j recomputed in FP64
+      double up = 1.0, cp = 0.0, yz = 0.0;
+      for (int j = 0; j < n; ++j) {
+        const size_t q = sh.at(i, j);
+        const double a = (j > 0) ? beta * L.s[q] : 0.0;
+        double b = dg(q);
+        if (j == 0) b -= gamma;
+        if (j == n - 1) b -= cn1 * vf;
+        const double c = (j < n - 1) ? beta * L.nn[q] : 0.0;
+        const double lj = (j > 0) ? a / up : 0.0;
+        const double u = b - lj * cp;
+        yz = beta * L.w[q] - lj * yz;
+        wy[q] = yz;
+        up = u;
+        cp = c;
+      }
+      double xn = 0.0, x0v = 0.0, xl = 0.0;
+      for (int j = n - 1; j >= 0; --j) {
+        const size_t q = sh.at(i, j);
+        const double c = (j < n - 1) ? beta * L.nn[q] : 0.0;
+        const double xv = wu[q] * (wy[q] - c * xn);
+        wy[q] = xv;
+        if (j == n - 1) xl = xv;
+        if (j == 0) x0v = xv;
+        xn = xv;
+      }
+      const double sigma = (x0v + vf * xl) * inv;
+      double dot = 0.0;
+      for (int j = 0; j < n; ++j) {
+        const size_t q = sh.at(i, j);
+        const double zj = wy[q] - sigma * wq[q];
+        fz[j] = (T)zj;
+        dot += L.o[j] * zj;
+      }
+      L.sc[1] = d0 - beta * dot;
+    }
+  }
+}
+
+template <typename T>
+int launch_refresh(const LevelView<double>* L64, LevelView<T>* LT, int nlev, Params p,
+                   double* ws, cudaStream_t st) {
+  RefreshArgs A{};
+  A.nlev = nlev;
+  A.par = p;
+  int rings = 0;
+  size_t wofs = 0;
+  for (int l = 0; l < nlev; ++l) {
+    RefreshLevel& r = A.lv[l];
+    const LevelView<double>& d = L64[l];
+    r.sh = d.sh;
+    r.vol = d.vol;
+    r.rs = d.rs;
+    r.w = d.w;
+    r.e = d.e;
+    r.s = d.s;
+    r.nn = d.nn;
+    r.o = d.o;
+    r.sc = LT[l].sc;
+    r.diag = LT[l].diag;
+    r.diag64 = (sizeof(T) == 4 && l == 0) ? L64[0].diag : nullptr;
+    r.fl = LT[l].fl;
+    r.fui = LT[l].fui;
+    r.fcu = LT[l].fcu;
+    r.fq = LT[l].fq;
+    r.fring = LT[l].fring;
+    r.fz = LT[l].fz;
+    r.ws = ws + wofs;
+    wofs += 3 * d.sh.nv;
+    r.coarsest = (l == nlev - 1);
+    r.ring0 = rings;
+    rings += d.sh.m;
+  }
+  k_refresh<T><<<(rings + 63) / 64, 64, 0, st>>>(A);
+  return 1;
+}
+
+// ---------------------------------------------------------------------------------
+// ring solves
+
+// inclusive scan of affine maps x -> A x + B over positions 0..TW-1 of column r
+template <typename T>
+__device__ void scan_affine(T A, T B, T* sA, T* sB, int r, int pos, int RW, int TW) {
+  sA[pos * RW + r] = A;
+  sB[pos * RW + r] = B;
+  __syncthreads();
+  for (int off = 1; off < TW; off <<= 1) {
+    const T a = sA[pos * RW + r], b = sB[pos * RW + r];
+    T ao = T(1), bo = T(0);
+    const bool has = pos >= off;
+    if (has) {
+      ao = sA[(pos - off) * RW + r];
+      bo = sB[(pos - off) * RW + r];
+    }
+    __syncthreads();
+    if (has) {
+      sA[pos * RW + r] = a * ao;
+      sB[pos * RW + r] = fma(a, bo, b);
+    }
+    __syncthreads();
+  }
+}
+
+
+template <typename T>
+struct RingArgs {
+  LevelView<T> L;   // level being smoothed
+  LevelView<T> C;   // next coarser level (RING_POST, even rings)
+  const T* b;       // right-hand side of this level
+  T* x;             // solution of this level (updated in place)
+  const T* X;       // solution of the coarser level (RING_POST)
+  Params par;
+  const int* done;
+  int parity;       // 1: odd rings, 0: even rings (+ origin)
+  int mode;
+};
+
+// A radial position of a level, addressed along the angle: entry j at base + j * ld.
+struct Line {
+  size_t base;
+  int ld;
+  __device__ __forceinline__ size_t at(int j) const { return base + (size_t)j * ld; }
+};
+
+__device__ __forceinline__ Line line_of(const Shape& sh, int i) {
+  return Line{sh.at(i, 0), (i & 1) ? sh.ldo : sh.lde};
+}
+
+// Coarse ring I of the next level: the origin for I = 0 (stride 0), a zero ring beyond
+// the last one (weight 0, reads the origin slot harmlessly).
+template <typename T>
+struct CoarseRef {
+  Line ln;
+  T mul;
+};
+template <typename T>
+__device__ __forceinline__ CoarseRef<T> coarse_ref(const Shape& C, int I) {
+  if (I == 0) return CoarseRef<T>{Line{0, 0}, T(1)};
+  if (I > C.m) return CoarseRef<T>{Line{0, 0}, T(0)};
+  return CoarseRef<T>{line_of(C, I), T(1)};
+}
+
+// Odd ring q of the level with its coarse correction x_q + ia X_k + ib X_{k+1}
+// (q = 2k + 1: its coarse neighbours are coarse rings k and k + 1).
+template <typename T>
+struct OddRef {
+  Line ln;
+  CoarseRef<T> lo, hi;
+};
+template <typename T>
+__device__ __forceinline__ OddRef<T> odd_ref(const Shape& F, const Shape& C, int q) {
+  const int k = q >> 1;
+  return OddRef<T>{line_of(F, q), coarse_ref<T>(C, k), coarse_ref<T>(C, k + 1)};
+}
+template <typename T>
+__device__ __forceinline__ T corrected(const OddRef<T>& o, const T* x, const T* ia, const T* ib,
+                                       const T* X, int j) {
+  const size_t p = o.ln.at(j);
+  const T xl = X[o.lo.ln.at(j)] * o.lo.mul;
+  const T xh = X[o.hi.ln.at(j)] * o.hi.mul;
+  return fma(ia[p], xl, fma(ib[p], xh, x[p]));
+}
+
+// right-hand side of the angular line of ring i:
+//   d_j = b_ij - beta (w_ij x_{i-1,j} + e_ij x_{i+1,j})
+// with the neighbours as the sweep sees them (zero in the first half-sweep, corrected
+// odd rings in the first post-smoothing half-sweep); x_{0,j} is the origin and
+// x_{m+1,j} = 0.
+template <typename T>
+struct RingRhs {
+  const T* b;
+  const T* w;
+  const T* e;
+  const T* x;
+  const T* ia;
+  const T* ib;
+  const T* X;
+  Line own, wl, el;        // own line, west / east neighbour lines (wl.ld = 0: origin)
+  OddRef<T> wo, eo;        // corrected odd neighbours (kind 2)
+  T beta, emul;            // emul = 0 on the last ring (Dirichlet neighbour)
+  int kind;                // 0: b only, 1: plain neighbours, 2: corrected odd neighbours
+  __device__ __forceinline__ T operator()(int j) const {
+    const size_t p = own.at(j);
+    const T bv = b[p];
+    if (kind == 0) return bv;
+    T xw, xe;
+    if (kind == 1) {
+      xw = x[wl.at(j)];
+      xe = x[el.at(j)] * emul;
+    } else {
+      xw = corrected(wo, x, ia, ib, X, j);
+      xe = corrected(eo, x, ia, ib, X, j) * emul;
+    }
+    return bv - beta * fma(w[p], xw, e[p] * xe);
+  }
+};
+
+template <typename T>
+__device__ __forceinline__ RingRhs<T> make_ring_rhs(const RingArgs<T>& a, T beta, int i) {
+  const Shape& sh = a.L.sh;
+  RingRhs<T> r{};
+  r.b = a.b;
+  r.w = a.L.w;
+  r.e = a.L.e;
+  r.x = a.x;
+  r.ia = a.L.ia;
+  r.ib = a.L.ib;
+  r.X = a.X;
+  r.beta = beta;
+  r.own = line_of(sh, i);
+  const bool last = i >= sh.m;
+  r.emul = last ? T(0) : T(1);
+  r.wl = (i == 1) ? Line{0, 0} : line_of(sh, i - 1);
+  r.el = last ? Line{0, 0} : line_of(sh, i + 1);
+  if (a.mode == RING_PRE && a.parity == 1) {
+    r.kind = 0;
+  } else if (a.mode == RING_POST && a.parity == 0) {
+    r.kind = 2;
+    r.wo = odd_ref<T>(sh, a.C.sh, i - 1);
+    r.eo = last ? odd_ref<T>(sh, a.C.sh, i - 1) : odd_ref<T>(sh, a.C.sh, i + 1);
+  } else {
+    r.kind = 1;
+  }
+  return r;
+}
+
+// Solves the periodic lines of one CTA (RW lines x TW chunks of P) or one cluster.
+// Rhs(j) gives d_j of this thread's line; Out(j, x) stores the solution.
+template <typename T, int P, typename Rhs, typename Fac, typename Out>
+__device__ void solve_lines(int n, bool valid, Rhs rhs, Fac fac, T vf, T inv, Out out) {
+  extern __shared__ unsigned char smraw[];
+  const int RW = blockDim.x, TW = blockDim.y;
+  const int r = threadIdx.x, c = threadIdx.y;
+  T* sA = reinterpret_cast<T*>(smraw);
+  T* sB = sA + RW * TW;
+  T* segA = sB + RW * TW;   // this CTA's segment map, per line
+  T* segB = segA + RW;
+  T* ends = segB + RW;      // [0, RW): x_0 of the line, [RW, 2 RW): x_{n-1}
+  cg::cluster_group cl = cg::this_cluster();
+  const int CS = (int)cl.num_blocks();
+  const int crank = (int)cl.block_rank();
+  const int gc = crank * TW + c;
+  const int j0 = gc * P;
+  T v[P];
+#pragma unroll
+  for (int p = 0; p < P; ++p) {
+    const int j = j0 + p;
+    v[p] = (valid && j < n) ? rhs(j) : T(0);
+  }
+  // forward substitution y_j = d_j - l_j y_{j-1}
+  T A = T(1), B = T(0);
+#pragma unroll
+  for (int p = 0; p < P; ++p) {
+    const int j = j0 + p;
+    if (valid && j < n) {
+      const T l = fac.l(j);
+      B = fma(-l, B, v[p]);
+      A = -l * A;
+    }
+  }
+  scan_affine(A, B, sA, sB, r, c, RW, TW);
+  if (c == TW - 1) {
+    segA[r] = sA[c * RW + r];
+    segB[r] = sB[c * RW + r];
+  }
+  T yin = T(0);
+  if (CS > 1) {
+    cl.sync();
+    for (int q = 0; q < crank; ++q) {
+      const T* ra = cl.map_shared_rank(segA, q);
+      const T* rb = cl.map_shared_rank(segB, q);
+      yin = fma(ra[r], yin, rb[r]);
+    }
+  }
+  T prev = (c > 0) ? fma(sA[(c - 1) * RW + r], yin, sB[(c - 1) * RW + r]) : yin;
+  __syncthreads();
+#pragma unroll
+  for (int p = 0; p < P; ++p) {
+    const int j = j0 + p;
+    if (valid && j < n) {
+      prev = fma(-fac.l(j), prev, v[p]);
+      v[p] = prev;
+    }
+  }
+  // backward substitution x_j = ui_j y_j - cu_j x_{j+1}
+  A = T(1);
+  B = T(0);
+#pragma unroll
+  for (int p = P - 1; p >= 0; --p) {
+    const int j = j0 + p;
+    if (valid && j < n) {
+      const T cu = fac.cu(j);
+      B = fma(-cu, B, fac.ui(j) * v[p]);
+      A = -cu * A;
+    }
+  }
+  const int pos = TW - 1 - c;
+  scan_affine(A, B, sA, sB, r, pos, RW, TW);
+  if (pos == TW - 1) {
+    segA[r] = sA[pos * RW + r];
+    segB[r] = sB[pos * RW + r];
+  }
+  T xin = T(0);
+  if (CS > 1) {
+    cl.sync();
+    for (int q = CS - 1; q > crank; --q) {
+      const T* ra = cl.map_shared_rank(segA, q);
+      const T* rb = cl.map_shared_rank(segB, q);
+      xin = fma(ra[r], xin, rb[r]);
+    }
+  }
+  T next = (pos > 0) ? fma(sA[(pos - 1) * RW + r], xin, sB[(pos - 1) * RW + r]) : xin;
+#pragma unroll
+  for (int p = P - 1; p >= 0; --p) {
+    const int j = j0 + p;
+    if (valid && j < n) {
+      next = fma(-fac.cu(j), next, fac.ui(j) * v[p]);
+      v[p] = next;
+    }
+  }
+  // Sherman-Morrison: x -= q (x_0 + vf x_{n-1}) / (1 + v.q)
+  if (j0 == 0) ends[r] = v[0];
+#pragma unroll
+  for (int p = 0; p < P; ++p)
+    if (j0 + p == n - 1) ends[RW + r] = v[p];
+  T x0v, xl;
+  if (CS > 1) {
+    cl.sync();
+    const int owner = ((n - 1) / P) / TW;
+    x0v = cl.map_shared_rank(ends, 0)[r];
+    xl = cl.map_shared_rank(ends, owner)[RW + r];
+  } else {
+    __syncthreads();
+    x0v = ends[r];
+    xl = ends[RW + r];
+  }
+  const T sigma = fma(vf, xl, x0v) * inv;
+#pragma unroll
+  for (int p = 0; p < P; ++p) {
+    const int j = j0 + p;
+    if (valid && j < n) out(j, fma(-sigma, fac.q(j), v[p]));
+  }
+  if (CS > 1) cl.sync();  // no CTA leaves while another may still read its shared memory
+}
+
+template <typename T>
+struct RingFac {
+  const T* fl;
+  const T* fui;
+  const T* fcu;
+  const T* fq;
+  Line ln;
+  __device__ __forceinline__ T l(int j) const { return fl[ln.at(j)]; }
+  __device__ __forceinline__ T ui(int j) const { return fui[ln.at(j)]; }
+  __device__ __forceinline__ T cu(int j) const { return fcu[ln.at(j)]; }
+  __device__ __forceinline__ T q(int j) const { return fq[ln.at(j)]; }
+};
+
+// Origin relaxation: x_0 = (b_0 - beta sum_j o_j x_{1,j}) / diag0, x_1 from x (PRE) or
+// after the coarse correction (POST).  Run by one CTA.
+template <typename T>
+__device__ void relax_origin(const RingArgs<T>& a, T beta) {
+  __shared__ double red[32];
+  const int tid = threadIdx.x + blockDim.x * threadIdx.y;
+  const int nt = blockDim.x * blockDim.y;
+  double s = 0.0;
+  const OddRef<T> r1 = odd_ref<T>(a.L.sh, a.C.sh, 1);
+  for (int j = tid; j < a.L.sh.n; j += nt) {
+    const T x1 = (a.mode == RING_PRE) ? a.x[r1.ln.at(j)] : corrected(r1, a.x, a.L.ia, a.L.ib, a.X, j);
+    s = fma((double)a.L.o[j], (double)x1, s);
+  }
+  for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
+  if ((tid & 31) == 0) red[tid >> 5] = s;
+  __syncthreads();
+  if (tid == 0) {
+    double tot = 0.0;
+    for (int w = 0; w < (nt + 31) / 32; ++w) tot += red[w];
+    a.x[0] = (T)(((double)a.b[0] - (double)beta * tot) / a.L.sc[0]);
+  }
+}
+
+template <typename T, int P>
+__global__ void __launch_bounds__(512) k_ring(RingArgs<T> a) {
+  if (a.done && *a.done) return;
+  const T beta = (T)a.par[1];
+  const Shape& sh = a.L.sh;
+  const int nl = a.parity ? sh.no : sh.ne;
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  const bool valid = k < nl;
+  const int i = a.parity ? 2 * k + 1 : 2 * k + 2;
+  const int ringslot = a.parity ? k : sh.no + k;
+  T vf = T(0), inv = T(0);
+  if (valid) {
+    vf = a.L.fring[2 * ringslot];
+    inv = a.L.fring[2 * ringslot + 1];
+  }
+  const Line own = line_of(sh, valid ? i : 1);
+  RingFac<T> fac{a.L.fl, a.L.fui, a.L.fcu, a.L.fq, own};
+  const RingRhs<T> rhs = make_ring_rhs(a, beta, valid ? i : 1);
+  T* x = a.x;
+  solve_lines<T, P>(sh.n, valid, rhs, fac, vf, inv, [&](int j, T v) { x[own.at(j)] = v; });
+  // the origin is relaxed with the even rings; ring 1 (odd) is not written here
+  if (a.parity == 0 && blockIdx.x == 0 && blockIdx.y == 0) relax_origin(a, beta);
+}
+
+// residual of the odd rings after the pre-smoothing sweep, restricted to the coarser
+// level: B_I = ib_{2I-1} r_{2I-1} + ia_{2I+1} r_{2I+1} and B_0 = sum_j ia_{1,j} r_{1,j}
+// (the even rings and the origin have zero residual after their relaxation; an odd
+// ring's residual is what its even neighbours changed: r_q = -beta (w x_{q-1} + e x_{q+1})).
+template <typename T>
+struct RestrictArgs {
+  LevelView<T> L;
+  LevelView<T> C;
+  const T* x;
+  T* B;
+  Params par;
+  const int* done;
+};
+
+template <typename T>
+__device__ __forceinline__ T odd_resid(const LevelView<T>& L, const T* x, T beta, int q, int j) {
+  const size_t p = L.sh.at(q, j);
+  const T xw = (q == 1) ? x[0] : x[L.sh.at(q - 1, j)];
+  const T xe = (q < L.sh.m) ? x[L.sh.at(q + 1, j)] : T(0);
+  return -beta * fma(L.w[p], xw, L.e[p] * xe);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_restrict(RestrictArgs<T> a) {
+  if (a.done && *a.done) return;
+  const T beta = (T)a.par[1];
+  const Shape& sh = a.L.sh;
+  const int mc = a.C.sh.m, n = sh.n;
+  const size_t total = (size_t)mc * n;
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total;
+       t += (size_t)gridDim.x * blockDim.x) {
+    const int j = (int)(t / mc);
+    const int I = (int)(t - (size_t)j * mc) + 1;
+    const int qlo = 2 * I - 1, qhi = 2 * I + 1;
+    T v = a.L.ib[sh.at(qlo, j)] * odd_resid(a.L, a.x, beta, qlo, j);
+    if (qhi <= sh.m) v = fma(a.L.ia[sh.at(qhi, j)], odd_resid(a.L, a.x, beta, qhi, j), v);
+    a.B[a.C.sh.at(I, j)] = v;
+  }
+  if (blockIdx.x == 0) {
+    __shared__ double red[32];
+    double s = 0.0;
+    for (int j = threadIdx.x; j < n; j += blockDim.x)
+      s = fma((double)a.L.ia[sh.at(1, j)], (double)odd_resid(a.L, a.x, beta, 1, j), s);
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double tot = 0.0;
+      for (int w = 0; w < (int)(blockDim.x + 31) / 32; ++w) tot += red[w];
+      a.B[0] = (T)tot;
+    }
+  }
+}
+
+// coarsest level (origin + ring 1): y = T_1^{-1} b_1, x_0 = (b_0 - beta o.y) / denom,
+// x_1 = y - z x_0 with z = T_1^{-1} (beta w_1) from the refresh.
+template <typename T, int P>
+__global__ void __launch_bounds__(512) k_coarsest(LevelView<T> L, const T* b, T* x, Params par,
+                                                   const int* done) {
+  if (done && *done) return;
+  const T beta = (T)par[1];
+  const Shape& sh = L.sh;
+  const Line own = line_of(sh, 1);
+  RingFac<T> fac{L.fl, L.fui, L.fcu, L.fq, own};
+  solve_lines<T, P>(
+      sh.n, true, [&](int j) { return b[own.at(j)]; }, fac, L.fring[0], L.fring[1],
+      [&](int j, T v) { x[own.at(j)] = v; });
+  __syncthreads();
+  __shared__ double red[32];
+  __shared__ T x0s;
+  const int tid = threadIdx.x + blockDim.x * threadIdx.y;
+  const int nt = blockDim.x * blockDim.y;
+  double s = 0.0;
+  for (int j = tid; j < sh.n; j += nt) s = fma((double)L.o[j], (double)x[sh.at(1, j)], s);
+  for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
+  if ((tid & 31) == 0) red[tid >> 5] = s;
+  __syncthreads();
+  if (tid == 0) {
+    double tot = 0.0;
+    for (int w = 0; w < (nt + 31) / 32; ++w) tot += red[w];
+    const T x0 = (T)(((double)b[0] - (double)beta * tot) / L.sc[1]);
+    x[0] = x0;
+    x0s = x0;
+  }
+  __syncthreads();
+  const T x0 = x0s;
+  for (int j = tid; j < sh.n; j += nt) {
+    const size_t p = sh.at(1, j);
+    x[p] = fma(-L.fz[j], x0, x[p]);
+  }
+}
+
+// ---------------------------------------------------------------------------------
+// launch configuration of the ring solves
+
+struct RingShape {
+  int RW, TW, P;
+};
+constexpr int kRingThreads = 512;
+
+// RW lines per CTA (a full 32-byte sector of each line per row of angles), TW chunks
+// of P angles, at most kRingThreads threads: one CTA covers rings of up to
+// 512 / RW * 32 angles (4096 in FP64, 2048 in FP32 with RW = 8).
+template <typename T>
+static RingShape ring_shape(int nlines, int n) {
+  RingShape s;
+  s.RW = (sizeof(T) == 8) ? 4 : 8;
+  while (s.RW > 1 && s.RW > nlines) s.RW >>= 1;
+  const int maxTW = kRingThreads / s.RW;
+  s.P = 8;
+  while (s.P < 32 && (n + s.P - 1) / s.P > maxTW) s.P <<= 1;
+  int chunks = (n + s.P - 1) / s.P;
+  s.TW = 1;
+  while (s.TW < chunks) s.TW <<= 1;
+  if (s.TW > maxTW) s.TW = maxTW;
+  return s;
+}
+
+template <typename T>
+static size_t ring_smem(const RingShape& s) {
+  return sizeof(T) * (2 * (size_t)s.RW * s.TW + 4 * (size_t)s.RW);
+}
+
+template <typename T, int P>
+static void launch_ring_p(const RingArgs<T>& a, const RingShape& s, int nl, cudaStream_t st) {
+  const int grid = (nl + s.RW - 1) / s.RW;
+  k_ring<T, P><<<grid, dim3(s.RW, s.TW), ring_smem<T>(s), st>>>(a);
+}
+
+template <typename T>
+int launch_ring(const LevelView<T>& L, const LevelView<T>& C, const T* b, T* x, const T* X,
+                Params p, int parity, int mode, const int* done, cudaStream_t st) {
+  RingArgs<T> a{};
+  a.L = L;
+  a.C = C;
+  a.b = b;
+  a.x = x;
+  a.X = X;
+  a.par = p;
+  a.done = done;
+  a.parity = parity;
+  a.mode = mode;
+  const int nl = parity ? L.sh.no : L.sh.ne;
+  if (nl == 0) return 0;
+  const RingShape s = ring_shape<T>(nl, L.sh.n);
+  switch (s.P) {
+    case 8: launch_ring_p<T, 8>(a, s, nl, st); break;
+    case 16: launch_ring_p<T, 16>(a, s, nl, st); break;
+    default: launch_ring_p<T, 32>(a, s, nl, st); break;
+  }
+  return 1;
+}
+
+template <typename T>
+int launch_restrict(const LevelView<T>& L, const LevelView<T>& C, const T* x, T* B, Params p,
+                    const int* done, cudaStream_t st) {
+  RestrictArgs<T> r{L, C, x, B, p, done};
+  const size_t work = (size_t)C.sh.m * L.sh.n;
+  k_restrict<T><<<grid_for(work, 256), 256, 0, st>>>(r);
+  return 1;
+}
+
+template <typename T>
+int launch_coarsest(const LevelView<T>& L, const T* b, T* x, Params p, const int* done,
+                    cudaStream_t st) {
+  RingShape s;
+  s.RW = 1;
+  s.P = 8;
+  while (s.P < 32 && (L.sh.n + s.P - 1) / s.P > kRingThreads) s.P <<= 1;
+  s.TW = 32;
+  while (s.TW < (L.sh.n + s.P - 1) / s.P) s.TW <<= 1;
+  const size_t smem = ring_smem<T>(s);
+  switch (s.P) {
+    case 8: k_coarsest<T, 8><<<1, dim3(1, s.TW), smem, st>>>(L, b, x, p, done); break;
+    case 16: k_coarsest<T, 16><<<1, dim3(1, s.TW), smem, st>>>(L, b, x, p, done); break;
+    default: k_coarsest<T, 32><<<1, dim3(1, s.TW), smem, st>>>(L, b, x, p, done); break;
+  }
+  return 1;
+}
+
+// The ring kernels use dynamic shared memory only for the scan buffers
+// (2 RW TW + 4 RW words): at most 16.1 KB, below the default 48 KB limit.
+
+#define POLAR_MG_INST(T)                                                                      \
+  template int launch_refresh<T>(const LevelView<double>*, LevelView<T>*, int, Params,         \
+                                 double*, cudaStream_t);                                      \
+  template int launch_ring<T>(const LevelView<T>&, const LevelView<T>&, const T*, T*,          \
+                              const T*, Params, int, int, const int*, cudaStream_t);          \
+  template int launch_restrict<T>(const LevelView<T>&, const LevelView<T>&, const T*, T*,      \
+                                  Params, const int*, cudaStream_t);                          \
+  template int launch_coarsest<T>(const LevelView<T>&, const T*, T*, Params, const int*,       \
+                                  cudaStream_t);
+
+POLAR_MG_INST(float)
+POLAR_MG_INST(double)
+
+}  // namespace polar
