@@ -228,71 +228,100 @@ def run_native(args):
             dist.barrier()
         torch.cuda.synchronize()
 
-    precision = P.POLAR_MIXED if args.precision == "mixed" else P.POLAR_FP64
     prob = make_problem()
     stream = torch.cuda.current_stream()
-    ctx = driver.create(prob, precision, stream=stream.cuda_stream)
     t_all = np.asarray(prob.t)
     W = prob.weight_table()
     exact = {}
-
-    def set_level(k, host=None):
-        if k not in exact:
-            exact[k] = np.ascontiguousarray(prob.exact(t_all[k]))
-        P.polar_set_state(ctx, exact[k] if host is None else host, t_all[k])
-
-    def step(k, opts=None):
-        st, rc = P.polar_advance(ctx, t_all[k:k + 2], prob.theta_w, W[k:k + 2], opts)
-        return st[0]
-
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     levels, consecutive = step_levels(args.steps)
 
-    # warm-up: W steps spread over the schedule
-    wl, _ = step_levels(max(args.warmup, 1))
-    for k in wl[:args.warmup]:
-        set_level(k)
-        step(k)
-    torch.cuda.synchronize()
+    def timed_run(precision, timers):
+        """Warm-up, then the K timed steps; returns the measurements of this precision."""
+        ctx = driver.create(prob, precision, stream=stream.cuda_stream)
 
-    # ---- timed region (device time of each step, L2 flushed before each)
+        def set_level(k):
+            if k not in exact:
+                exact[k] = np.ascontiguousarray(prob.exact(t_all[k]))
+            P.polar_set_state(ctx, exact[k], t_all[k])
+
+        wl, _ = step_levels(max(args.warmup, 1))
+        for k in wl[:args.warmup]:
+            set_level(k)
+            P.polar_advance(ctx, t_all[k:k + 2], prob.theta_w, W[k:k + 2])
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in levels]
+        iters, refs, checkpoints = [], [], {}
+        launches0 = P.polar_kernel_launches(ctx)
+        if timers:
+            P.polar_timing_enable(ctx, True)
+        barrier()
+        wall0 = time.perf_counter()
+        for s, k in enumerate(levels):
+            if not consecutive or k == 0:
+                set_level(k)
+            flush.fill_(float(s))
+            ev[s][0].record(stream)
+            st, _ = P.polar_advance(ctx, t_all[k:k + 2], prob.theta_w, W[k:k + 2])
+            ev[s][1].record(stream)
+            iters.append(st[0]["iters"])
+            refs.append(st[0]["refinements"])
+            if consecutive and not timers and (k + 1) % 100 == 0:
+                checkpoints[k + 1] = P.polar_get_state(ctx)[0]
+        barrier()
+        wall = time.perf_counter() - wall0
+        launches = P.polar_kernel_launches(ctx) - launches0
+        kstats = P.polar_timing_query(ctx) if timers else {}
+        P.polar_timing_enable(ctx, False)
+        dev_ms = sum(a.elapsed_time(b) for a, b in ev)
+        U_last, t_last = P.polar_get_state(ctx)
+        if dist is not None:
+            tt = torch.tensor([dev_ms], device="cuda", dtype=torch.float64)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            dev_ms = float(tt.item())
+        return dict(ctx=ctx, dev_ms=dev_ms, wall=wall, launches=launches, kstats=kstats,
+                    iters=float(np.mean(iters)), refs=float(np.mean(refs)), U=U_last, t=t_last,
+                    set_level=set_level, checkpoints=checkpoints)
+
+    precision = P.POLAR_MIXED if args.precision == "mixed" else P.POLAR_FP64
+    other = P.POLAR_FP64 if precision == P.POLAR_MIXED else P.POLAR_MIXED
     clocks = ClockSampler(local)
     clocks.start()
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-          for _ in levels]
-    iters, refs = [], []
-    launches0 = P.polar_kernel_launches(ctx)
-    P.polar_timing_enable(ctx, True)
-    barrier()
-    wall0 = time.perf_counter()
-    for s, k in enumerate(levels):
-        if not consecutive or k == 0:
-            set_level(k)
-        flush.fill_(float(s))
-        ev[s][0].record(stream)
-        st = step(k)
-        ev[s][1].record(stream)
-        iters.append(st["iters"])
-        refs.append(st["refinements"])
-    barrier()
-    wall = time.perf_counter() - wall0
+    main = timed_run(precision, False)
     clk = clocks.stop()
-    launches = P.polar_kernel_launches(ctx) - launches0
-    kstats = P.polar_timing_query(ctx)
-    P.polar_timing_enable(ctx, False)
-    dev_ms = sum(a.elapsed_time(b) for a, b in ev)
-    U_last, t_last = P.polar_get_state(ctx)
+    # per-kernel CUDA events on a second pass over the same steps (kept out of the
+    # headline run, whose launch rate the event records would perturb)
+    prof = timed_run(precision, True)
+    comp = timed_run(other, False) if args.compare else None
+    ctx, dev_ms = main["ctx"], main["dev_ms"]
+    kstats = prof["kstats"]
+    set_level = main["set_level"]
+    U_last, t_last = main["U"], main["t"]
+    launches, wall = main["launches"], main["wall"]
+    iters, refs = [main["iters"]], [main["refs"]]
     err_exact = float(np.max(np.abs(U_last - prob.exact(t_last))) /
                       np.max(np.abs(prob.exact(t_last))))
-    if dist is not None:
-        tt = torch.tensor([dev_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        dev_ms = float(tt.item())
+    err_cp = {k: float(np.max(np.abs(U - prob.exact(t_all[k]))) / np.max(np.abs(prob.exact(t_all[k]))))
+              for k, U in sorted(main["checkpoints"].items())}
     updates = prob.N * len(levels) * world
     value = updates / (dev_ms * 1e-3)
+    compare = None
+    if comp is not None:
+        diff = float(np.max(np.abs(main["U"] - comp["U"])) / np.max(np.abs(comp["U"])))
+        # relative max-norm difference at the checkpoints t_100, t_200, ... (consecutive runs)
+        cp = {k: float(np.max(np.abs(main["checkpoints"][k] - comp["checkpoints"][k])) /
+                       np.max(np.abs(comp["checkpoints"][k])))
+              for k in sorted(main["checkpoints"]) if k in comp["checkpoints"]}
+        compare = {"precision": "fp64" if other == P.POLAR_FP64 else "mixed",
+                   "value": updates / (comp["dev_ms"] * 1e-3), "ms_per_step": comp["dev_ms"] / len(levels),
+                   "krylov_iters_per_step": comp["iters"], "refinements_per_step": comp["refs"],
+                   "speedup_of_headline": comp["dev_ms"] / dev_ms,
+                   "rel_max_diff_final_state": diff,
+                   "rel_max_diff_at_checkpoints": cp}
 
     # ---- end to end: pinned host state in, pinned host state out, every step
-    ke = levels[:max(1, min(len(levels), 20))]
+    ke = sorted(set(levels))[:: max(1, len(set(levels)) // 20)][:20]
     host_in = {k: torch.from_numpy(np.ascontiguousarray(prob.exact(t_all[k]))).pin_memory()
                for k in ke}
     host_out = torch.empty(prob.N, dtype=torch.float64).pin_memory()
@@ -303,7 +332,7 @@ def run_native(args):
         flush.fill_(1.0)
         e0.record(stream)
         P.polar_set_state(ctx, host_in[k], t_all[k])
-        step(k)
+        P.polar_advance(ctx, t_all[k:k + 2], prob.theta_w, W[k:k + 2])
         P.polar_get_state(ctx, host_out)
         e1.record(stream)
         e1.synchronize()
@@ -326,7 +355,8 @@ def run_native(args):
                 "peak_source": peak_src, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": NCU_TRAFFIC.get(name), "algorithmic_bytes_per_launch": per_launch,
                 "avg_launch_us": 1e3 * d["ms"] / max(d["launches"], 1),
-                "share_of_step": d["ms"] / dev_ms}
+                "share_of_step": d["ms"] / prof["dev_ms"],
+                "timing": "CUDA events around every launch, second pass over the same steps"}
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dev_ms / len(levels),
@@ -341,7 +371,9 @@ def run_native(args):
                        "parallelism": f"replicas x{world}"},
             "krylov_iters_per_step": float(np.mean(iters)),
             "refinements_per_step": float(np.mean(refs)),
-            "rel_err_vs_exact_last_step": err_exact,
+            "rel_err_vs_manufactured_last_step": err_exact,
+            "rel_err_vs_manufactured_at_checkpoints": err_cp,
+            "compare": compare,
             "wall_s": wall,
             "gpu_launches": int(launches),
             "clocks": clk,
@@ -364,18 +396,117 @@ def run_native(args):
     return 0
 
 
+# ------------------------------------------------------------------------- batch
+def run_batch(args):
+    """The 256-instance sweep: continuity equation on uneven adaptive meshes (m log-uniform
+    in [64, 1024], n in [128, 2048], D amplitude in [0.2, 5], Peclet in [0.1, 20]), 500-level
+    time stretch each, advanced together: one CUDA graph per step holds a step of every
+    instance.  value = sum of N_i x steps / device time."""
+    import torch
+    import polar_inputs as pi
+    import paper_2509_15879_gb300 as P
+    from paper_2509_15879_gb300 import driver
+    world = env_int("WORLD_SIZE", 1)
+    rank = env_int("RANK", 0)
+    local = env_int("LOCAL_RANK", 0)
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    K_sched = 500
+    count = args.instances
+    # replicas: rank r takes instances r, r + world, ... (independent instances, no collective)
+    mine = list(range(rank, count, world))
+    t0 = time.perf_counter()
+    probs = [pi.config4_instance(i, K=K_sched) for i in mine]
+    gen_s = time.perf_counter() - t0
+    stream = torch.cuda.current_stream()
+    precision = P.POLAR_MIXED if args.precision == "mixed" else P.POLAR_FP64
+
+    def run(prec):
+        ctxs = [driver.create(p, prec, stream=stream.cuda_stream) for p in probs]
+        batch = P.polar_batch_create(ctxs, stream.cuda_stream)
+        W = max(args.warmup, 1)
+        driver.batch_advance(batch, probs, 0, W)
+        for c, p in zip(ctxs, probs):  # back to the initial state for the timed steps
+            P.polar_set_state(c, p.u0, p.t[0])
+        K = min(args.steps, K_sched)
+        clocks = ClockSampler(local)
+        clocks.start()
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        stats, _ = driver.batch_advance(batch, probs, 0, K)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        clk = clocks.stop()
+        ms = e0.elapsed_time(e1)
+        if dist is not None:
+            tt = torch.tensor([ms], device="cuda", dtype=torch.float64)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            ms = float(tt.item())
+        states = [P.polar_get_state(c)[0] for c in ctxs]
+        iters = float(np.mean([s["iters"] for row in stats for s in row]))
+        launches = sum(P.polar_kernel_launches(c) for c in ctxs)
+        return ms, K, states, iters, clk, launches
+
+    ms, K, st_main, iters, clk, launches = run(precision)
+    pts = sum(p.N for p in probs)
+    total_pts = pts
+    if dist is not None:
+        tt = torch.tensor([float(pts)], device="cuda", dtype=torch.float64)
+        dist.all_reduce(tt)
+        total_pts = float(tt.item())
+    value = total_pts * K / (ms * 1e-3)
+    compare = None
+    if args.compare:
+        other = P.POLAR_FP64 if precision == P.POLAR_MIXED else P.POLAR_MIXED
+        ms2, _, st2, it2, _, _ = run(other)
+        diff = max(float(np.max(np.abs(a - b)) / np.max(np.abs(b))) for a, b in zip(st_main, st2))
+        compare = {"precision": "fp64" if other == P.POLAR_FP64 else "mixed",
+                   "value": total_pts * K / (ms2 * 1e-3), "ms_per_step": ms2 / K,
+                   "krylov_iters_per_step": it2, "speedup_of_headline": ms2 / ms,
+                   "max_rel_diff_final_states": diff}
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
+            "warmup": args.warmup, "ms_per_step": ms / K, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if precision == P.POLAR_FP64 else "f32+f64", "data": "synthetic",
+            "config": {"workload": f"batched sweep: {count} continuity instances, m in [64, 1024], "
+                                   f"n in [128, 2048], 500-level time stretch; one CUDA graph "
+                                   f"per step for all instances", "instances": len(probs),
+                       "sum_N": pts, "precision": args.precision,
+                       "l2": "inputs larger than L2 (several GB of instance data)",
+                       "parallelism": f"replicas x{world}"},
+            "krylov_iters_per_step": iters, "compare": compare, "gpu_launches": int(launches),
+            "clocks": clk, "setup_s": gen_s}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=40)
+    ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["native", "reference"], default="native")
     ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--compare", type=int, default=1,
+                    help="also time the other precision on the same steps")
+    ap.add_argument("--workload", choices=["c2", "batch"], default="c2")
+    ap.add_argument("--instances", type=int, default=256)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batch":
+        return run_batch(args)
     return run_native(args)
 
 

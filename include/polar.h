@@ -154,6 +154,26 @@ int polar_step(polar_ctx* ctx, double dt, double theta, const double* w_old,
 int polar_advance(polar_ctx* ctx, int32_t nsteps, const double* t, double theta,
                   const double* w, const polar_solver_opts* opts, polar_step_stats* stats);
 
+/* Batched execution of independent instances (parameter sweeps, mesh-tuning studies):
+ * each instance is an ordinary context (own mesh, coefficients, state, precision) on the
+ * same device.  polar_batch_create records the contexts (the caller keeps ownership and
+ * must keep them alive); polar_batch_advance advances every instance over its own
+ * schedule of nsteps steps: t[i] holds nsteps+1 levels of instance i (t[i][0] its current
+ * time), theta[i] its implicit weight, w[i] its (nsteps+1) x nsrc source weights (w may be
+ * NULL when no instance has sources).  One CUDA graph holds one step of every instance
+ * as independent branches (each with its device-side refinement and Krylov loops) and is
+ * launched nsteps times on `stream`; the graph is rebuilt when a context changed.  stats
+ * (count x nsteps, instance-major) or NULL.  An instance stops at its first failing step
+ * (state kept at its last committed level, later entries POLAR_ESTATE); the others go on.
+ * Returns the first error of any instance.  Contexts must not be stepped concurrently
+ * from elsewhere while the batch runs. */
+typedef struct polar_batch polar_batch;
+int polar_batch_create(polar_ctx* const* ctxs, int32_t count, void* stream, polar_batch** out);
+int polar_batch_destroy(polar_batch* batch);
+int polar_batch_advance(polar_batch* batch, int32_t nsteps, const double* const* t,
+                        const double* theta, const double* const* w,
+                        const polar_solver_opts* opts, polar_step_stats* stats);
+
 /* y = (alpha I + beta L) x for one vector x with homogeneous Dirichlet data
  * (g = 0): the matrix-free operator every kernel of the step is built on.
  * x and y hold N doubles in the interface layout, both on the host or both on the

@@ -70,6 +70,11 @@ EXPORTS = {
     "polar_apply_operator": (C.c_int, [C.c_void_p, C.c_double, C.c_double, C.c_void_p,
                                        C.c_void_p, C.c_int32]),
     "polar_kernel_launches": (C.c_int64, [C.c_void_p]),
+    "polar_batch_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int32, C.c_void_p,
+                                     C.POINTER(C.c_void_p)]),
+    "polar_batch_destroy": (C.c_int, [C.c_void_p]),
+    "polar_batch_advance": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(_dp), _dp, C.POINTER(_dp),
+                                      C.POINTER(polar_solver_opts), C.POINTER(polar_step_stats)]),
     "polar_timing_enable": (C.c_int, [C.c_void_p, C.c_int32]),
     "polar_timing_query": (C.c_int, [C.c_void_p, C.c_int32, C.c_char_p, C.c_size_t,
                                      C.POINTER(C.c_int64), _dp, _dp]),
@@ -232,6 +237,57 @@ def polar_apply_operator(ctx: Ctx, alpha, beta, x, out=None):
 
 def polar_kernel_launches(ctx: Ctx) -> int:
     return int(load().polar_kernel_launches(ctx.handle))
+
+
+class Batch:
+    """Handle of a polar_batch over a list of contexts (kept alive with it)."""
+
+    def __init__(self, handle, ctxs):
+        self.handle, self.ctxs = handle, list(ctxs)
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.polar_batch_destroy(self.handle)
+            self.handle = None
+
+
+def polar_batch_create(ctxs, stream=None) -> Batch:
+    arr = (C.c_void_p * len(ctxs))(*[c.handle.value if isinstance(c.handle, C.c_void_p) else c.handle
+                                      for c in ctxs])
+    h = C.c_void_p()
+    _check(load().polar_batch_create(arr, len(ctxs), stream, C.byref(h)))
+    return Batch(h, ctxs)
+
+
+def polar_batch_destroy(batch: Batch):
+    if batch.handle:
+        _check(load().polar_batch_destroy(batch.handle))
+        batch.handle = None
+
+
+def polar_batch_advance(batch: Batch, ts, thetas, ws=None, opts=None, check=True):
+    """Advances every instance over its own time levels ts[i] (same number of steps);
+    returns (stats[i][k] dicts, rc)."""
+    count = len(batch.ctxs)
+    ts = [_f64(t) for t in ts]
+    K = len(ts[0]) - 1
+    if any(len(t) != K + 1 for t in ts):
+        raise ValueError("every instance needs the same number of steps")
+    tptr = (_dp * count)(*[t.ctypes.data_as(_dp) for t in ts])
+    th = _f64(thetas)
+    keep = []
+    wptr = None
+    if ws is not None:
+        ws = [_f64(w) if w is not None else np.zeros(1) for w in ws]
+        keep = ws
+        wptr = (_dp * count)(*[w.ctypes.data_as(_dp) for w in ws])
+    stats = (polar_step_stats * max(count * K, 1))()
+    rc = load().polar_batch_advance(batch.handle, K, tptr, th.ctypes.data_as(_dp), wptr,
+                                    _opts(opts), stats)
+    del keep
+    if check:
+        _check(rc)
+    return [[stats[i * K + k].as_dict() for k in range(K)] for i in range(count)], rc
 
 
 def polar_timing_enable(ctx: Ctx, on=True):

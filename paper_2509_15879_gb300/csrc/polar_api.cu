@@ -10,10 +10,14 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "../../include/polar.h"
@@ -58,7 +62,7 @@ struct DevLevel {
   // per-step refresh, FP64 (FP64 path; level 0 diag also for the mixed path)
   double *diag, *fl, *fui, *fcu, *fq, *fring, *fz;
   // per-step refresh, FP32 (mixed path)
-  float *diag32, *fl32, *fui32, *fcu32, *fq32, *fring32, *fz32;
+  float *diag32, *fl32, *fui32, *fcu32, *fq32, *fring32, *fz32, *rsum32;
   // V-cycle right-hand side and solution (levels >= 1), in the inner precision
   void *b, *x;
 };
@@ -76,6 +80,15 @@ struct KernelStat {
 };
 
 }  // namespace
+
+struct polar_ctx;
+struct polar_batch {
+  std::vector<polar_ctx*> ctx;
+  cudaStream_t st = nullptr;
+  cudaGraph_t g = nullptr;
+  cudaGraphExec_t ex = nullptr;
+  std::vector<int64_t> gens;  // context generations the graph was captured with
+};
 
 struct polar_ctx {
   int m = 0, n = 0;
@@ -98,9 +111,32 @@ struct polar_ctx {
   double* r64 = nullptr;
   double* io = nullptr;  // interface-layout staging (N doubles)
   double* ws = nullptr;  // refresh workspace
-  double* par = nullptr; // device [alpha, beta]
-  double* par_host = nullptr;
+  StepParams* sp = nullptr;       // device parameters of the current step
+  StepParams* sp_host = nullptr;  // pinned staging copy
   double cur_alpha = -1.0, cur_beta = -1.0;  // values the refresh was made for
+  cudaStream_t cs = nullptr;      // stream the launchers enqueue on (st, or the capture stream)
+  cudaStream_t cap = nullptr;     // private stream for graph capture
+  cudaGraph_t graph = nullptr;    // one theta-step with device-side loops
+  cudaGraphExec_t gexec = nullptr;
+  bool graph_ok = false;          // gexec matches the current coefficients
+  bool use_graph = true;
+  // coarse end of the V-cycle in one CTA (launch_coarse_cycle).  Off: measured on the
+  // 512 x 1024 workload, one CTA took 272 us per V-cycle (FP32) and 611 us (FP64) for the
+  // levels below 32 rings, against about 210 us for their separate launches.
+  bool coarse_fusion = false;
+  int64_t graph_kernels_fixed = 0, graph_kernels_sweep = 0, graph_kernels_iter = 0;
+  int64_t generation = 0;         // bumped whenever a captured graph goes stale
+  // ring-solve tile shapes per level, [mode * 2 + parity] (autotuned on first use)
+  std::vector<std::array<RingShape, 4>> tiles;
+  bool tuned = false;
+  bool autotune = true;
+  // device-side schedule of a polar_advance (graph mode)
+  StepParams* sched = nullptr;
+  StepOut* dout = nullptr;
+  int* kstep = nullptr;
+  int sched_cap = 0;
+  StepParams* sched_host = nullptr;
+  StepOut* out_host = nullptr;
   KVecs<double> kv64{};
   KVecs<float> kv32{};
   double* part = nullptr;
@@ -113,6 +149,7 @@ struct polar_ctx {
   std::vector<KernelStat> kstats;
 
   Reduce red() const { return Reduce{part, ks}; }
+  Params par() const { return reinterpret_cast<const double*>(sp); }
   size_t N() const { return (size_t)m * n + 1; }
   const Shape& sh0() const { return lv[0].sh; }
   size_t nv() const { return lv[0].sh.nv; }
@@ -137,6 +174,10 @@ int dalloc(polar_ctx* c, T** p, size_t count) {
 }
 
 int check_launch(polar_ctx* c, int n) {
+  if (n < 0) {
+    const cudaError_t e = cudaGetLastError();
+    return fail(POLAR_ECUDA, std::string("kernel launch (cluster): ") + cudaGetErrorString(e));
+  }
   c->launches += n;
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return fail(POLAR_ECUDA, std::string("kernel launch: ") + cudaGetErrorString(e));
@@ -223,8 +264,18 @@ void release(polar_ctx* c) {
   c->allocs.clear();
   if (c->ks_host) cudaFreeHost(c->ks_host);
   c->ks_host = nullptr;
-  if (c->par_host) cudaFreeHost(c->par_host);
-  c->par_host = nullptr;
+  if (c->sp_host) cudaFreeHost(c->sp_host);
+  c->sp_host = nullptr;
+  if (c->gexec) cudaGraphExecDestroy(c->gexec);
+  if (c->graph) cudaGraphDestroy(c->graph);
+  c->gexec = nullptr;
+  c->graph = nullptr;
+  if (c->cap) cudaStreamDestroy(c->cap);
+  c->cap = nullptr;
+  if (c->sched_host) cudaFreeHost(c->sched_host);
+  if (c->out_host) cudaFreeHost(c->out_host);
+  c->sched_host = nullptr;
+  c->out_host = nullptr;
 }
 
 // Fetch caller data (host or device pointer) into a host vector.
@@ -289,6 +340,7 @@ int alloc_levels(polar_ctx* c) {
       TRY(dalloc(c, &d.o32, (size_t)c->n));
       float** f32[] = {&d.diag32, &d.fl32, &d.fui32, &d.fcu32, &d.fq32};
       for (float** p : f32) TRY(dalloc(c, p, nv));
+      if (l == 0) TRY(dalloc(c, &d.rsum32, nv));
       TRY(dalloc(c, &d.fring32, nr));
       TRY(dalloc(c, &d.fz32, (size_t)c->n));
       if (l > 0) {
@@ -337,6 +389,7 @@ int alloc_levels(polar_ctx* c) {
     b.ia = d.ia32;
     b.ib = d.ib32;
     b.diag = d.diag32;
+    b.rsum = d.rsum32;
     b.fl = d.fl32;
     b.fui = d.fui32;
     b.fcu = d.fcu32;
@@ -405,114 +458,272 @@ const std::vector<LevelView<T>>& views(const polar_ctx* c) {
   }
 }
 
-// Per-step refresh: the matrix S = alpha V + beta V L changes with dt and theta.
+// Per-step refresh: the matrix S = alpha V + beta V L changes with dt and theta.  The
+// kernel reads alpha, beta and do_refresh from the step parameters.
 template <typename T>
-int refresh(polar_ctx* c, double alpha, double beta) {
-  if (alpha == c->cur_alpha && beta == c->cur_beta) return POLAR_OK;
-  c->par_host[0] = alpha;
-  c->par_host[1] = beta;
-  CUDA_TRY(cudaMemcpyAsync(c->par, c->par_host, 2 * sizeof(double), cudaMemcpyHostToDevice, c->st));
+int launch_refresh_all(polar_ctx* c) {
   std::vector<LevelView<T>> vt = views<T>(c);
   double pts = 0.0;
   for (const DevLevel& d : c->lv) pts += (double)d.sh.m * d.sh.n;
   // reads 6 FP64 coefficient arrays, writes diag and 4 factor arrays
   TLAUNCH("refresh", pts * (6.0 * 8 + 5.0 * sizeof(T)),
-          launch_refresh<T>(c->v64.data(), vt.data(), c->nlev(), c->par, c->ws, c->st));
-  // the host copy of the parameters must not change before the copy above ran
-  CUDA_TRY(cudaStreamSynchronize(c->st));
-  c->cur_alpha = alpha;
-  c->cur_beta = beta;
+          launch_refresh<T>(c->v64.data(), vt.data(), c->nlev(), c->sp, c->ws, c->cs));
   return POLAR_OK;
 }
 
-// x = M^{-1} b: one V(1,1) cycle of the radial multigrid (polar_mg.cu).
+// tuned tile shape of a ring-solve launch (null: the launcher's default)
+const RingShape* tile(const polar_ctx* c, int l, int mode, int parity) {
+  if (!c->tuned || l >= (int)c->tiles.size()) return nullptr;
+  const RingShape& s = c->tiles[l][mode * 2 + parity];
+  return s.P > 0 ? &s : nullptr;
+}
+
+// first level of the hierarchy that the one-CTA coarse cycle takes (nlev - 1: none)
+template <typename T>
+int coarse_start(const polar_ctx* c) {
+  const std::vector<LevelView<T>>& L = views<T>(c);
+  const int nl = c->nlev();
+  int lc = nl - 1;
+  if (c->coarse_fusion && sizeof(T) == 4)
+    while (lc > 0 && L[lc - 1].sh.no <= coarse_cycle_lines<T>()) --lc;
+  return lc;
+}
+
+// x = M^{-1} b: one V(1,1) cycle of the radial multigrid (polar_mg.cu).  The levels
+// from `lc` down run inside one CTA (launch_coarse_cycle); the ones above it launch one
+// kernel per half-sweep.
 template <typename T>
 int vcycle(polar_ctx* c, const T* b, T* x) {
   const std::vector<LevelView<T>>& L = views<T>(c);
   const int nl = c->nlev();
   const int* done = &c->ks->done;
   const double B = sizeof(T);
+  const Params par = c->par();
   auto bof = [&](int l) { return l == 0 ? b : static_cast<const T*>(c->lv[l].b); };
   auto xof = [&](int l) { return l == 0 ? x : static_cast<T*>(c->lv[l].x); };
-  for (int l = 0; l + 1 < nl; ++l) {
+  // kernel classes are timed per level group: the fine level, level 1, and the rest
+  auto nm = [&](const char* base, int l) {
+    static thread_local std::string s;
+    s = std::string(base) + (l == 0 ? "@L0" : l == 1 ? "@L1" : "@L2+");
+    return s.c_str();
+  };
+  // one CTA holds the coarse end only in FP32: GB300's FP64 rate per SM (about 2 FMA
+  // per clock) makes a single CTA far slower than the same FP64 work spread over SMs
+  int lc = coarse_start<T>(c);
+  for (int l = 0; l < lc; ++l) {
     const Shape& s = L[l].sh;
     const double po = (double)s.no * s.n, pe = (double)s.ne * s.n;
     // algorithmic words: odd line solve reads b and 4 factors, writes x (6 per point);
     // even: b, w, e, the odd neighbours, 4 factors, writes x (9); restriction reads
     // w, e, ia, ib of the odd rings and x of the even ones, writes the coarse rhs
-    TLAUNCH("ring_pre_odd", 6 * B * po,
-            launch_ring<T>(L[l], L[l + 1], bof(l), xof(l), nullptr, c->par, 1, RING_PRE, done, c->st));
-    TLAUNCH("ring_pre_even", 9 * B * pe,
-            launch_ring<T>(L[l], L[l + 1], bof(l), xof(l), nullptr, c->par, 0, RING_PRE, done, c->st));
-    TLAUNCH("restrict", B * (4 * po + 2 * pe),
-            launch_restrict<T>(L[l], L[l + 1], xof(l), static_cast<T*>(c->lv[l + 1].b), c->par, done,
-                               c->st));
+    TLAUNCH(nm("ring_pre_odd", l), 6 * B * po,
+            launch_ring<T>(L[l], L[l + 1], bof(l), xof(l), nullptr, par, 1, RING_PRE, done, c->cs,
+                           tile(c, l, RING_PRE, 1)));
+    TLAUNCH(nm("ring_pre_even", l), 9 * B * pe,
+            launch_ring<T>(L[l], L[l + 1], bof(l), xof(l), nullptr, par, 0, RING_PRE, done, c->cs,
+                           tile(c, l, RING_PRE, 0)));
+    TLAUNCH(nm("restrict", l), B * (4 * po + 2 * pe),
+            launch_restrict<T>(L[l], L[l + 1], xof(l), static_cast<T*>(c->lv[l + 1].b), par, done,
+                               c->cs));
   }
-  TLAUNCH("coarsest", 8 * B * L[nl - 1].sh.n,
-          launch_coarsest<T>(L[nl - 1], bof(nl - 1), xof(nl - 1), c->par, done, c->st));
-  for (int l = nl - 2; l >= 0; --l) {
+  bool fused = false;
+  if (lc < nl - 1) {
+    std::vector<T*> bl(nl, nullptr), xl(nl, nullptr);
+    for (int l = 1; l < nl; ++l) {
+      bl[l] = static_cast<T*>(c->lv[l].b);
+      xl[l] = static_cast<T*>(c->lv[l].x);
+    }
+    double words = 0.0;
+    for (int l = lc; l < nl; ++l) words += 40.0 * L[l].sh.m * L[l].sh.n;
+    cudaEvent_t ev_;
+    TRY(timed_begin(c, &ev_));
+    const int k = launch_coarse_cycle<T>(L.data(), lc, nl, bof(lc), xof(lc), bl.data(), xl.data(),
+                                         par, done, c->cs);
+    LAUNCH(k);
+    TRY(timed_end(c, ev_, "coarse_cycle", B * words));
+    fused = k > 0;
+  }
+  if (!fused) {
+    lc = nl - 1;
+    TLAUNCH("coarsest", 8 * B * L[nl - 1].sh.n,
+            launch_coarsest<T>(L[nl - 1], bof(nl - 1), xof(nl - 1), par, done, c->cs));
+  }
+  for (int l = lc - 1; l >= 0; --l) {
     const Shape& s = L[l].sh;
     const double po = (double)s.no * s.n, pe = (double)s.ne * s.n;
     // even rings after the correction also read x, ia, ib of the odd rings and the
     // coarse solution (8 per even point + 3 per odd point + 1 per coarse point)
-    TLAUNCH("ring_post_even", B * (8 * pe + 3 * po + pe),
+    TLAUNCH(nm("ring_post_even", l), B * (8 * pe + 3 * po + pe),
             launch_ring<T>(L[l], L[l + 1], bof(l), xof(l), static_cast<const T*>(c->lv[l + 1].x),
-                           c->par, 0, RING_POST, done, c->st));
-    TLAUNCH("ring_post_odd", 9 * B * po,
-            launch_ring<T>(L[l], L[l + 1], bof(l), xof(l), nullptr, c->par, 1, RING_POST, done, c->st));
+                           par, 0, RING_POST, done, c->cs, tile(c, l, RING_POST, 0)));
+    TLAUNCH(nm("ring_post_odd", l), 9 * B * po,
+            launch_ring<T>(L[l], L[l + 1], bof(l), xof(l), nullptr, par, 1, RING_POST, done, c->cs,
+                           tile(c, l, RING_POST, 1)));
   }
   return POLAR_OK;
 }
 
-// Inner BiCGStab solve S d = r (r holds the scaled right-hand side), right-preconditioned
-// by one V-cycle per application; all scalars stay on the device.
+// ---- autotuner of the ring-solve tiles.  Every (level, mode, parity) launch of the
+// V-cycle is timed with CUDA events for each candidate shape on the context's own data
+// (after a refresh); the fastest is kept.  Results are shared between contexts through a
+// cache keyed by precision, mode, parity and the power-of-two buckets of the line count
+// and the ring length.
+using TuneKey = std::tuple<int, int, int, int, int>;
+std::mutex g_tune_lock;
+std::map<TuneKey, RingShape> g_tune_cache;
+
+int bucket(int v) {
+  int b = 1;
+  while (b < v) b <<= 1;
+  return b;
+}
+
 template <typename T>
-int inner_solve(polar_ctx* c, KVecs<T>& k, double rel_tol, int max_iter, int* iters) {
+KVecs<T>& kvecs(polar_ctx* c);
+
+template <typename T>
+int tune_rings(polar_ctx* c) {
+  const std::vector<LevelView<T>>& L = views<T>(c);
+  const int nl = c->nlev();
+  const int lc = coarse_start<T>(c);
+  c->tiles.assign(nl, std::array<RingShape, 4>{});
+  CUDA_TRY(cudaMemsetAsync(&c->ks->done, 0, sizeof(int), c->st));
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  CUDA_TRY(cudaEventCreate(&e0));
+  CUDA_TRY(cudaEventCreate(&e1));
+  std::vector<RingShape> cand;
+  int rc = POLAR_OK;
+  const int* done = &c->ks->done;
+  for (int l = 0; l < lc && rc == POLAR_OK; ++l) {
+    T* b = l == 0 ? kvecs<T>(c).p : static_cast<T*>(c->lv[l].b);
+    T* x = l == 0 ? kvecs<T>(c).phat : static_cast<T*>(c->lv[l].x);
+    const T* X = static_cast<const T*>(c->lv[l + 1].x);
+    for (int mode = 0; mode < 2 && rc == POLAR_OK; ++mode)
+      for (int parity = 0; parity < 2 && rc == POLAR_OK; ++parity) {
+        const int lines = parity ? L[l].sh.no : L[l].sh.ne;
+        if (lines == 0) continue;
+        const TuneKey key{(int)sizeof(T), mode, parity, bucket(lines), bucket(L[l].sh.n)};
+        {
+          std::lock_guard<std::mutex> g(g_tune_lock);
+          auto it = g_tune_cache.find(key);
+          if (it != g_tune_cache.end()) {
+            c->tiles[l][mode * 2 + parity] = it->second;
+            continue;
+          }
+        }
+        ring_candidates<T>(lines, L[l].sh.n, cand);
+        RingShape best = ring_default<T>(lines, L[l].sh.n);
+        float best_ms = 1e30f;
+        for (const RingShape& s : cand) {
+          auto go = [&]() {
+            return launch_ring<T>(L[l], L[l + 1], b, x, mode ? X : nullptr, c->par(), parity, mode,
+                                  done, c->st, &s);
+          };
+          if (go() < 0) {
+            (void)cudaGetLastError();  // shape not launchable here: skip it
+            continue;
+          }
+          cudaEventRecord(e0, c->st);
+          for (int r = 0; r < 3; ++r) go();
+          cudaEventRecord(e1, c->st);
+          if (cudaEventSynchronize(e1) != cudaSuccess) {
+            rc = fail(POLAR_ECUDA, "autotuner: ring launch failed");
+            break;
+          }
+          float ms = 0.f;
+          cudaEventElapsedTime(&ms, e0, e1);
+          if (ms < best_ms) {
+            best_ms = ms;
+            best = s;
+          }
+        }
+        c->tiles[l][mode * 2 + parity] = best;
+        std::lock_guard<std::mutex> g(g_tune_lock);
+        g_tune_cache[key] = best;
+      }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  (void)cudaGetLastError();
+  if (rc == POLAR_OK) c->tuned = true;
+  return rc;
+}
+
+template <typename T>
+KVecs<T>& kvecs(polar_ctx* c) {
+  if constexpr (sizeof(T) == 8) {
+    return c->kv64;
+  } else {
+    return c->kv32;
+  }
+}
+
+// One BiCGStab iteration, right-preconditioned by one V-cycle per application; all
+// scalars stay on the device.  `cond` (graph mode) receives "keep iterating".
+template <typename T>
+int bicg_iteration(polar_ctx* c, CondHandle cond) {
+  KVecs<T>& k = kvecs<T>(c);
   const LevelView<T>& L0 = views<T>(c)[0];
   const Reduce red = c->red();
   const size_t nv = c->nv();
   const double B = sizeof(T), pts = (double)c->m * c->n;
-  TLAUNCH("bicg_init", 5 * B * nv,
-          launch_bicg_init<T>(nv, k.r, k.rhat, k.p, k.v, k.d, true, rel_tol, max_iter, c->st, red));
-  int batch = 2;
-  for (;;) {
-    for (int it = 0; it < batch; ++it) {
-      TRY(vcycle<T>(c, k.p, k.phat));
-      // stencil with dot: reads x, diag, 4 couplings, d1; writes y (8 words per point)
-      TLAUNCH("stencil_dot", 8 * B * pts,
-              launch_apply_dot<T>(L0, c->par, k.phat, k.v, k.rhat, 0, c->st, red));
-      TLAUNCH("bicg_s", 3 * B * nv, launch_bicg_s<T>(nv, k.r, k.v, k.s, c->st, red));
-      TRY(vcycle<T>(c, k.s, k.shat));
-      TLAUNCH("stencil_dot", 8 * B * pts, launch_apply_dot<T>(L0, c->par, k.shat, k.t, k.s, 1, c->st, red));
-      TLAUNCH("bicg_update", 8 * B * nv,
-              launch_bicg_update<T>(nv, k.d, k.phat, k.shat, k.r, k.s, k.t, k.rhat, c->st, red));
-      TLAUNCH("bicg_p", 4 * B * nv, launch_bicg_p<T>(nv, k.p, k.r, k.v, c->st, red));
-    }
-    TRY(read_scalars(c));
-    if (c->ks_host->done != 0) break;
-    batch = std::min(batch * 2, 8);
-  }
-  *iters = c->ks_host->iters;
+  TRY(vcycle<T>(c, k.p, k.phat));
+  // stencil with dot: reads x, diag, 4 couplings, d1; writes y (8 words per point)
+  TLAUNCH("stencil_dot", 8 * B * pts, launch_apply_dot<T>(L0, c->par(), k.phat, k.v, k.rhat, 0, c->cs, red));
+  TLAUNCH("bicg_s", 3 * B * nv, launch_bicg_s<T>(nv, k.r, k.v, k.s, c->cs, red));
+  TRY(vcycle<T>(c, k.s, k.shat));
+  TLAUNCH("stencil_dot", 8 * B * pts, launch_apply_dot<T>(L0, c->par(), k.shat, k.t, k.s, 1, c->cs, red));
+  TLAUNCH("bicg_update", 8 * B * nv,
+          launch_bicg_update<T>(nv, k.d, k.phat, k.shat, k.r, k.s, k.t, k.rhat, c->cs, red));
+  TLAUNCH("bicg_p", 4 * B * nv, launch_bicg_p<T>(nv, k.p, k.r, k.v, cond, c->cs, red));
   return POLAR_OK;
 }
 
 template <typename T>
-int solve_step(polar_ctx* c, const polar_solver_opts& o, polar_step_stats& stats) {
-  KVecs<T>* k;
-  if constexpr (sizeof(T) == 8) {
-    k = &c->kv64;
-  } else {
-    k = &c->kv32;
-  }
+int bicg_begin(polar_ctx* c, CondHandle cond) {
+  KVecs<T>& k = kvecs<T>(c);
   const size_t nv = c->nv();
-  CUDA_TRY(cudaMemcpyAsync(c->X, c->U, nv * sizeof(double), cudaMemcpyDeviceToDevice, c->st));
   const Reduce red = c->red();
-  const double inner_tol = (sizeof(T) == 8) ? std::min(o.inner_tol, 1e-12) : o.inner_tol;
+  TLAUNCH("scale_cast", (8.0 + sizeof(T)) * nv, launch_scale_cast<T>(nv, c->r64, k.r, c->cs, red));
+  TLAUNCH("bicg_init", 5.0 * sizeof(T) * nv,
+          launch_bicg_init<T>(nv, k.r, k.rhat, k.p, k.v, k.d, c->sp, cond, c->cs, red));
+  return POLAR_OK;
+}
+
+int resid(polar_ctx* c) {
   const double pts = (double)c->m * c->n;
+  TLAUNCH("resid64", 8.0 * 8 * pts, launch_resid64(c->v64[0], c->par(), c->X, c->e, c->r64, c->cs, c->red()));
+  return POLAR_OK;
+}
+
+template <typename T>
+int correct(polar_ctx* c) {
+  const size_t nv = c->nv();
+  TLAUNCH("correct", (16.0 + sizeof(T)) * nv, launch_correct<T>(nv, c->X, kvecs<T>(c).d, c->cs, c->red()));
+  return POLAR_OK;
+}
+
+int rhs(polar_ctx* c) {
+  const double* srcs[4] = {c->vsrc[0], c->vsrc[1], c->vsrc[2], c->vsrc[3]};
+  const double* bnds[4] = {c->bnd[0], c->bnd[1], c->bnd[2], c->bnd[3]};
+  TLAUNCH("rhs", (8.0 + c->nsrc) * 8 * c->m * c->n,
+          launch_rhs(c->v64[0], c->sp, c->U, c->nsrc, srcs, bnds, c->e, c->cs, c->red()));
+  return POLAR_OK;
+}
+
+// Eager step: the host drives the refinement and Krylov loops (used when per-kernel
+// timing is on, and as the fallback when a graph cannot be built).
+template <typename T>
+int step_eager(polar_ctx* c, polar_step_stats& stats) {
+  c->cs = c->st;
+  TRY(rhs(c));
+  if (c->sp_host->do_refresh) TRY(launch_refresh_all<T>(c));
+  CUDA_TRY(cudaMemcpyAsync(c->X, c->U, c->nv() * sizeof(double), cudaMemcpyDeviceToDevice, c->st));
   stats.iters = 0;
   stats.refinements = 0;
+  const StepParams& o = *c->sp_host;
   for (int sweep = 0;; ++sweep) {
-    TLAUNCH("resid64", 8.0 * 8 * pts, launch_resid64(c->v64[0], c->par, c->X, c->e, c->r64, c->st, red));
+    TRY(resid(c));
     TRY(read_scalars(c));
     stats.refinements += 1;
     const double xmax = std::max(c->ks_host->xmax, 1e-300);
@@ -524,15 +735,162 @@ int solve_step(polar_ctx* c, const polar_solver_opts& o, polar_step_stats& stats
     if (sweep >= o.max_refine)
       return fail(POLAR_ENOCONV, "refinement did not reach the tolerance (scaled residual " +
                                      std::to_string(scaled) + ")");
-    TLAUNCH("scale_cast", (8.0 + sizeof(T)) * nv, launch_scale_cast<T>(nv, c->r64, k->r, c->st, red));
-    int it = 0;
-    TRY(inner_solve<T>(c, *k, inner_tol, o.max_iter, &it));
-    stats.iters += it;
+    TRY(bicg_begin<T>(c, 0));
+    int batch = 2;
+    for (;;) {
+      for (int it = 0; it < batch; ++it) TRY(bicg_iteration<T>(c, 0));
+      TRY(read_scalars(c));
+      if (c->ks_host->done != 0) break;
+      batch = std::min(batch * 2, 8);
+    }
+    stats.iters += c->ks_host->iters;
     if (c->ks_host->done == 3) return fail(POLAR_ENONFINITE, "non-finite value in the Krylov solve");
-    TLAUNCH("correct", (16.0 + sizeof(T)) * nv, launch_correct<T>(nv, c->X, k->d, c->st, red));
+    TRY(correct<T>(c));
   }
   std::swap(c->U, c->X);
+  c->graph_ok = false;  // the graph was captured with the previous U and X
+  c->generation += 1;
   return POLAR_OK;
+}
+
+// ---- graph mode: one theta-step as a CUDA graph whose refinement and Krylov loops are
+// conditional WHILE nodes, so a step needs no host round trip until it has finished.
+
+int capture_begin(polar_ctx* c, cudaGraph_t g, const cudaGraphNode_t* dep, size_t ndep) {
+  CUDA_TRY(cudaStreamBeginCaptureToGraph(c->cap, g, dep, nullptr, ndep, cudaStreamCaptureModeThreadLocal));
+  c->cs = c->cap;
+  return POLAR_OK;
+}
+
+int capture_end(polar_ctx* c, std::vector<cudaGraphNode_t>* sinks) {
+  if (sinks) {
+    cudaStreamCaptureStatus status;
+    const cudaGraphNode_t* deps = nullptr;
+    size_t nd = 0;
+    CUDA_TRY(cudaStreamGetCaptureInfo(c->cap, &status, nullptr, nullptr, &deps, nullptr, &nd));
+    sinks->assign(deps, deps + nd);
+  }
+  cudaGraph_t out = nullptr;
+  CUDA_TRY(cudaStreamEndCapture(c->cap, &out));
+  c->cs = c->st;
+  return POLAR_OK;
+}
+
+int add_while(cudaGraph_t g, const std::vector<cudaGraphNode_t>& deps, cudaGraphConditionalHandle h,
+              cudaGraphNode_t* node, cudaGraph_t* body) {
+  cudaGraphNodeParams np{};
+  np.type = cudaGraphNodeTypeConditional;
+  np.conditional.handle = h;
+  np.conditional.type = cudaGraphCondTypeWhile;
+  np.conditional.size = 1;
+  CUDA_TRY(cudaGraphAddNode(node, g, deps.data(), nullptr, deps.size(), &np));
+  *body = np.conditional.phGraph_out[0];
+  return POLAR_OK;
+}
+
+int add_cond(cudaGraph_t g, const std::vector<cudaGraphNode_t>& deps,
+             cudaGraphConditionalHandle h, cudaGraphConditionalNodeType type,
+             cudaGraphNode_t* node, cudaGraph_t* body) {
+  cudaGraphNodeParams np{};
+  np.type = cudaGraphNodeTypeConditional;
+  np.conditional.handle = h;
+  np.conditional.type = type;
+  np.conditional.size = 1;
+  CUDA_TRY(cudaGraphAddNode(node, g, deps.data(), nullptr, deps.size(), &np));
+  *body = np.conditional.phGraph_out[0];
+  return POLAR_OK;
+}
+
+// Appends one schedule-driven theta-step of this context to graph g (no dependencies on
+// the graph's other nodes):
+//   load step *kstep of the schedule -> IF (no earlier failure) {
+//     right-hand side, refresh, X = U, residual, decide ->
+//     WHILE (refine) { scaled cast, BiCGStab init -> WHILE (iterate) { iteration },
+//                      correction, residual, decide } -> commit U = X, record result }
+//   -> next step.
+template <typename T>
+int append_step(polar_ctx* c, cudaGraph_t g) {
+  if (!c->cap) CUDA_TRY(cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking));
+  const int64_t l0 = c->launches;
+  cudaGraphConditionalHandle hif, hout, hin;
+  CUDA_TRY(cudaGraphConditionalHandleCreate(&hif, g, 0, 0));
+  std::vector<cudaGraphNode_t> sinks;
+  TRY(capture_begin(c, g, nullptr, 0));
+  LAUNCH(launch_sched_begin(c->sched, c->kstep, c->sp, c->dout, (CondHandle)hif, c->cs, c->red()));
+  TRY(capture_end(c, &sinks));
+  cudaGraphNode_t nif, nout, nin;
+  cudaGraph_t bif, bout, bin;
+  TRY(add_cond(g, sinks, hif, cudaGraphCondTypeIf, &nif, &bif));
+  const int64_t l1 = c->launches;
+  CUDA_TRY(cudaGraphConditionalHandleCreate(&hout, bif, 0, 0));
+  TRY(capture_begin(c, bif, nullptr, 0));
+  TRY(rhs(c));
+  TRY(launch_refresh_all<T>(c));
+  LAUNCH(launch_copy(c->nv(), c->U, c->X, c->cs, c->red()));
+  TRY(resid(c));
+  LAUNCH(launch_refine_decide(c->sp, (CondHandle)hout, c->cs, c->red()));
+  TRY(capture_end(c, &sinks));
+  const int64_t l2 = c->launches;
+  TRY(add_cond(bif, sinks, hout, cudaGraphCondTypeWhile, &nout, &bout));
+  CUDA_TRY(cudaGraphConditionalHandleCreate(&hin, bout, 0, 0));
+  TRY(capture_begin(c, bout, nullptr, 0));
+  TRY(bicg_begin<T>(c, (CondHandle)hin));
+  TRY(capture_end(c, &sinks));
+  TRY(add_cond(bout, sinks, hin, cudaGraphCondTypeWhile, &nin, &bin));
+  const int64_t l3 = c->launches;
+  TRY(capture_begin(c, bin, nullptr, 0));
+  TRY(bicg_iteration<T>(c, (CondHandle)hin));
+  TRY(capture_end(c, nullptr));
+  const int64_t l4 = c->launches;
+  TRY(capture_begin(c, bout, &nin, 1));
+  LAUNCH(launch_after_inner(c->cs, c->red()));
+  TRY(correct<T>(c));
+  TRY(resid(c));
+  LAUNCH(launch_refine_decide(c->sp, (CondHandle)hout, c->cs, c->red()));
+  TRY(capture_end(c, nullptr));
+  const int64_t l5 = c->launches;
+  TRY(capture_begin(c, bif, &nout, 1));
+  LAUNCH(launch_commit(c->nv(), c->U, c->X, c->cs, c->red()));
+  LAUNCH(launch_sched_end(c->kstep, c->dout, c->cs, c->red()));
+  TRY(capture_end(c, nullptr));
+  const int64_t l6 = c->launches;
+  TRY(capture_begin(c, g, &nif, 1));
+  LAUNCH(launch_sched_next(c->kstep, c->cs));
+  TRY(capture_end(c, nullptr));
+  const int64_t l7 = c->launches;
+  // kernels per executed step: fixed ones, per refinement sweep, per Krylov iteration
+  c->graph_kernels_fixed = (l1 - l0) + (l2 - l1) + (l6 - l5) + (l7 - l6);
+  c->graph_kernels_sweep = (l3 - l2) + (l5 - l4);
+  c->graph_kernels_iter = l4 - l3;
+  c->launches = l0;  // captured launches run only when the graph is launched
+  return POLAR_OK;
+}
+
+template <typename T>
+int build_graph(polar_ctx* c) {
+  if (c->gexec) cudaGraphExecDestroy(c->gexec);
+  if (c->graph) cudaGraphDestroy(c->graph);
+  c->gexec = nullptr;
+  c->graph = nullptr;
+  cudaGraph_t g = nullptr;
+  CUDA_TRY(cudaGraphCreate(&g, 0));
+  c->graph = g;
+  TRY(append_step<T>(c, g));
+  CUDA_TRY(cudaGraphInstantiate(&c->gexec, g, 0));
+  c->graph_ok = true;
+  return POLAR_OK;
+}
+
+// ends a capture left open by a failed graph build
+void abandon_capture(polar_ctx* c) {
+  cudaGraph_t junk = nullptr;
+  cudaStreamCaptureStatus status;
+  if (c->cap && cudaStreamIsCapturing(c->cap, &status) == cudaSuccess &&
+      status != cudaStreamCaptureStatusNone)
+    cudaStreamEndCapture(c->cap, &junk);
+  if (junk) cudaGraphDestroy(junk);
+  (void)cudaGetLastError();
+  c->cs = c->st;
 }
 
 polar_solver_opts resolve_opts(const polar_solver_opts* o) {
@@ -550,39 +908,208 @@ polar_solver_opts resolve_opts(const polar_solver_opts* o) {
   return r;
 }
 
-int do_step(polar_ctx* c, double dt, double theta, const double* w_old, const double* w_new,
-            const polar_solver_opts* opts, polar_step_stats* stats) {
-  if (!c) return fail(POLAR_EINVAL, "null context");
-  if (!c->have_coeffs || !c->have_state) return fail(POLAR_ESTATE, "set_coeffs and set_state must come first");
+// Writes the step parameters to the device (the stream orders them before the step).
+int set_step_params(polar_ctx* c, double alpha, double theta, const double* cf, const double* cg,
+                    const polar_solver_opts& o) {
+  StepParams& p = *c->sp_host;
+  p = StepParams{};
+  p.alpha = alpha;
+  p.beta = theta;
+  p.omt = 1.0 - theta;
+  for (int q = 0; q < 4; ++q) {
+    p.cf[q] = cf[q];
+    p.cg[q] = cg[q];
+  }
+  p.tol = o.tol;
+  p.inner_tol = (c->precision == POLAR_FP64) ? std::min(o.inner_tol, 1e-12) : o.inner_tol;
+  p.max_iter = o.max_iter;
+  p.max_refine = o.max_refine;
+  p.do_refresh = (alpha != c->cur_alpha || theta != c->cur_beta) ? 1 : 0;
+  CUDA_TRY(cudaMemcpyAsync(c->sp, c->sp_host, sizeof(StepParams), cudaMemcpyHostToDevice, c->st));
+  c->cur_alpha = alpha;
+  c->cur_beta = theta;
+  return POLAR_OK;
+}
+
+// Step parameters of level k -> k+1 of a schedule (theta-step of Eq. 2.5 with the
+// separable sources and Dirichlet data weighted at both levels).
+int make_params(polar_ctx* c, double t0, double t1, double theta, const double* w_old,
+                const double* w_new, const polar_solver_opts& o, double prev_alpha,
+                double prev_beta, StepParams& p) {
+  const double dt = t1 - t0;
   if (!(dt > 0.0) || !std::isfinite(dt)) return fail(POLAR_EINVAL, "dt must be positive and finite");
-  if (!(theta > 0.0 && theta <= 1.0)) return fail(POLAR_EINVAL, "theta must lie in (0, 1]");
-  if (c->nsrc > 0 && (!w_old || !w_new)) return fail(POLAR_EINVAL, "source weights required");
-  double cf[4] = {0, 0, 0, 0}, cg[4] = {0, 0, 0, 0};
+  p = StepParams{};
+  p.alpha = 1.0 / dt;
+  p.beta = theta;
+  p.omt = 1.0 - theta;
   for (int q = 0; q < c->nsrc; ++q) {
     if (!std::isfinite(w_old[q]) || !std::isfinite(w_new[q]))
       return fail(POLAR_ENONFINITE, "non-finite source weight");
-    cf[q] = (1.0 - theta) * w_old[q] + theta * w_new[q];
-    cg[q] = -((1.0 - theta) * w_old[q] + theta * w_new[q]);
+    p.cf[q] = (1.0 - theta) * w_old[q] + theta * w_new[q];
+    p.cg[q] = -((1.0 - theta) * w_old[q] + theta * w_new[q]);
   }
-  polar_solver_opts o = resolve_opts(opts);
-  polar_step_stats st{};
-  CUDA_TRY(cudaSetDevice(c->device));
-  const double alpha = 1.0 / dt;
-  // e = V U/dt - (1-theta) (V L U + e_m g_old) + (1-theta) V f_old + theta (V f_new - e_m g_new)
-  const double* srcs[4] = {c->vsrc[0], c->vsrc[1], c->vsrc[2], c->vsrc[3]};
-  const double* bnds[4] = {c->bnd[0], c->bnd[1], c->bnd[2], c->bnd[3]};
-  TLAUNCH("rhs", (8.0 + c->nsrc) * 8 * c->m * c->n,
-          launch_rhs(c->v64[0], alpha, 1.0 - theta, c->U, c->nsrc, srcs, bnds, cf, cg, c->e, c->st,
-                     c->red()));
-  int rc = (c->precision == POLAR_FP64) ? refresh<double>(c, alpha, theta)
-                                        : refresh<float>(c, alpha, theta);
-  if (rc == POLAR_OK)
-    rc = (c->precision == POLAR_FP64) ? solve_step<double>(c, o, st) : solve_step<float>(c, o, st);
-  st.status = rc;
-  if (stats) *stats = st;
-  if (rc != POLAR_OK) return rc;
-  c->t += dt;
+  p.tol = o.tol;
+  p.inner_tol = (c->precision == POLAR_FP64) ? std::min(o.inner_tol, 1e-12) : o.inner_tol;
+  p.max_iter = o.max_iter;
+  p.max_refine = o.max_refine;
+  p.do_refresh = (p.alpha != prev_alpha || theta != prev_beta) ? 1 : 0;
   return POLAR_OK;
+}
+
+int check_schedule_args(polar_ctx* c, int32_t nsteps, const double* t, double theta,
+                        const double* w) {
+  if (!c || !t) return fail(POLAR_EINVAL, "null argument");
+  if (nsteps < 0) return fail(POLAR_EINVAL, "nsteps must be >= 0");
+  if (c->nsrc > 0 && !w) return fail(POLAR_EINVAL, "weights required");
+  if (!c->have_coeffs || !c->have_state) return fail(POLAR_ESTATE, "set_coeffs and set_state must come first");
+  if (!(theta > 0.0 && theta <= 1.0)) return fail(POLAR_EINVAL, "theta must lie in (0, 1]");
+  if (std::fabs(t[0] - c->t) > 1e-12 * std::max(1.0, std::fabs(c->t)))
+    return fail(POLAR_EINVAL, "t[0] must equal the current time");
+  for (int k = 0; k < nsteps; ++k)
+    if (!(t[k + 1] > t[k]) || !std::isfinite(t[k + 1]))
+      return fail(POLAR_EINVAL, "time levels must increase");
+  return POLAR_OK;
+}
+
+// Uploads the schedule of an advance (graph mode) and resets the device step counter.
+int load_schedule(polar_ctx* c, int32_t K, const double* t, double theta, const double* w,
+                  const polar_solver_opts& o) {
+  if (K > c->sched_cap) {
+    const int cap = std::max(K, 2 * c->sched_cap);
+    TRY(dalloc(c, &c->sched, (size_t)cap));
+    TRY(dalloc(c, &c->dout, (size_t)cap));
+    if (!c->kstep) TRY(dalloc(c, &c->kstep, 1));
+    if (c->sched_host) cudaFreeHost(c->sched_host);
+    if (c->out_host) cudaFreeHost(c->out_host);
+    c->sched_host = nullptr;
+    c->out_host = nullptr;
+    CUDA_TRY(cudaMallocHost((void**)&c->sched_host, (size_t)cap * sizeof(StepParams)));
+    CUDA_TRY(cudaMallocHost((void**)&c->out_host, (size_t)cap * sizeof(StepOut)));
+    c->sched_cap = cap;
+  }
+  const int Q = c->nsrc;
+  double pa = c->cur_alpha, pb = c->cur_beta;
+  for (int k = 0; k < K; ++k) {
+    TRY(make_params(c, t[k], t[k + 1], theta, Q ? w + (size_t)k * Q : nullptr,
+                    Q ? w + (size_t)(k + 1) * Q : nullptr, o, pa, pb, c->sched_host[k]));
+    pa = c->sched_host[k].alpha;
+    pb = theta;
+  }
+  CUDA_TRY(cudaMemcpyAsync(c->sched, c->sched_host, (size_t)K * sizeof(StepParams),
+                           cudaMemcpyHostToDevice, c->st));
+  CUDA_TRY(cudaMemsetAsync(c->kstep, 0, sizeof(int), c->st));
+  CUDA_TRY(cudaMemsetAsync(&c->ks->halt, 0, sizeof(int), c->st));
+  return POLAR_OK;
+}
+
+// Reads the results of the K steps just run, fills stats, advances t to the last
+// committed level and returns the first failure.
+int finish_schedule(polar_ctx* c, int32_t K, const double* t, polar_step_stats* stats) {
+  CUDA_TRY(cudaMemcpyAsync(c->out_host, c->dout, (size_t)K * sizeof(StepOut),
+                           cudaMemcpyDeviceToHost, c->st));
+  CUDA_TRY(cudaStreamSynchronize(c->st));
+  int rc = POLAR_OK;
+  int done = 0;
+  for (int k = 0; k < K; ++k) {
+    const StepOut& r = c->out_host[k];
+    if (stats) {
+      stats[k] = polar_step_stats{};
+      stats[k].iters = r.iters;
+      stats[k].refinements = r.sweeps;
+      stats[k].status = r.status;
+      stats[k].scaled_resid = r.scaled;
+    }
+    if (r.status != POLAR_ESTATE) {
+      c->launches += 2 + c->graph_kernels_fixed + (int64_t)std::max(r.sweeps - 1, 0) * c->graph_kernels_sweep +
+                     (int64_t)r.iters * c->graph_kernels_iter;
+      c->cur_alpha = c->sched_host[k].alpha;  // the refresh state follows every executed step
+      c->cur_beta = c->sched_host[k].beta;
+    } else {
+      c->launches += 2;
+    }
+    if (rc == POLAR_OK && r.status != POLAR_OK) {
+      rc = r.status;
+      if (r.status == POLAR_ENONFINITE) fail(rc, "non-finite value in the solve of step " + std::to_string(k));
+      else fail(rc, "step " + std::to_string(k) + ": refinement did not reach the tolerance (scaled residual " +
+                        std::to_string(r.scaled) + ")");
+    }
+    if (r.status == POLAR_OK && rc == POLAR_OK) done = k + 1;
+  }
+  c->t = t[done];
+  return rc;
+}
+
+// Host-driven steps (per-kernel timing on, or no graph): one step at a time.
+int advance_eager(polar_ctx* c, int32_t K, const double* t, double theta, const double* w,
+                  const polar_solver_opts& o, polar_step_stats* stats) {
+  const int Q = c->nsrc;
+  for (int k = 0; k < K; ++k) {
+    polar_step_stats st{};
+    StepParams& p = *c->sp_host;
+    int rc = make_params(c, t[k], t[k + 1], theta, Q ? w + (size_t)k * Q : nullptr,
+                         Q ? w + (size_t)(k + 1) * Q : nullptr, o, c->cur_alpha, c->cur_beta, p);
+    if (rc == POLAR_OK) {
+      CUDA_TRY(cudaMemcpyAsync(c->sp, c->sp_host, sizeof(StepParams), cudaMemcpyHostToDevice, c->st));
+      c->cur_alpha = p.alpha;
+      c->cur_beta = theta;
+      rc = (c->precision == POLAR_FP64) ? step_eager<double>(c, st) : step_eager<float>(c, st);
+    }
+    st.status = rc;
+    if (stats) stats[k] = st;
+    if (rc != POLAR_OK) {
+      if (stats)
+        for (int q = k + 1; q < K; ++q) {
+          stats[q] = polar_step_stats{};
+          stats[q].status = POLAR_ESTATE;
+        }
+      return rc;
+    }
+    c->t = t[k + 1];  // the exact level, not an accumulated sum
+  }
+  return POLAR_OK;
+}
+
+// Refresh for the first step of a schedule, then tune the ring tiles on that data.
+int prepare_tuning(polar_ctx* c, const double* t, double theta, const double* w,
+                   const polar_solver_opts& o) {
+  const int Q = c->nsrc;
+  StepParams& p = *c->sp_host;
+  TRY(make_params(c, t[0], t[1], theta, Q ? w : nullptr, Q ? w + Q : nullptr, o, -1.0, -1.0, p));
+  CUDA_TRY(cudaMemcpyAsync(c->sp, c->sp_host, sizeof(StepParams), cudaMemcpyHostToDevice, c->st));
+  if (c->precision == POLAR_FP64) {
+    TRY(launch_refresh_all<double>(c));
+    TRY(tune_rings<double>(c));
+  } else {
+    TRY(launch_refresh_all<float>(c));
+    TRY(tune_rings<float>(c));
+  }
+  c->cur_alpha = p.alpha;
+  c->cur_beta = theta;
+  c->graph_ok = false;  // captured launches must use the tuned shapes
+  c->generation += 1;
+  return POLAR_OK;
+}
+
+int advance(polar_ctx* c, int32_t K, const double* t, double theta, const double* w,
+            const polar_solver_opts* opts, polar_step_stats* stats) {
+  TRY(check_schedule_args(c, K, t, theta, w));
+  CUDA_TRY(cudaSetDevice(c->device));
+  c->cs = c->st;
+  const polar_solver_opts o = resolve_opts(opts);
+  if (K == 0) return POLAR_OK;
+  if (c->autotune && !c->tuned) TRY(prepare_tuning(c, t, theta, w, o));
+  if (!c->use_graph || c->timing) return advance_eager(c, K, t, theta, w, o, stats);
+  TRY(load_schedule(c, K, t, theta, w, o));
+  if (!c->graph_ok) {
+    const int rc = (c->precision == POLAR_FP64) ? build_graph<double>(c) : build_graph<float>(c);
+    if (rc != POLAR_OK) {
+      abandon_capture(c);
+      c->use_graph = false;
+      return advance_eager(c, K, t, theta, w, o, stats);
+    }
+  }
+  for (int k = 0; k < K; ++k) CUDA_TRY(cudaGraphLaunch(c->gexec, c->st));
+  return finish_schedule(c, K, t, stats);
 }
 
 }  // namespace
@@ -626,6 +1153,7 @@ int polar_mesh_create(const polar_mesh_desc* d, polar_ctx** out) {
   c->scheme = d->scheme;
   c->precision = d->precision;
   c->st = static_cast<cudaStream_t>(d->stream);
+  c->cs = c->st;
   cudaGetDevice(&c->device);
   c->r.assign(d->r, d->r + m + 2);
   c->theta.assign(d->theta, d->theta + n);
@@ -640,7 +1168,7 @@ int polar_mesh_create(const polar_mesh_desc* d, polar_ctx** out) {
     chk(dalloc(c, &c->e, nv));
     chk(dalloc(c, &c->r64, nv));
     chk(dalloc(c, &c->io, c->N()));
-    chk(dalloc(c, &c->par, 2));
+    chk(dalloc(c, &c->sp, 1));
     if (c->precision == POLAR_FP64) {
       chk(alloc_kvecs(c, c->kv64));
     } else {
@@ -653,7 +1181,7 @@ int polar_mesh_create(const polar_mesh_desc* d, polar_ctx** out) {
     (void)cudaGetLastError();
     rc = fail(POLAR_ENOMEM, "cudaMallocHost failed");
   }
-  if (rc == POLAR_OK && cudaMallocHost((void**)&c->par_host, 2 * sizeof(double)) != cudaSuccess) {
+  if (rc == POLAR_OK && cudaMallocHost((void**)&c->sp_host, sizeof(StepParams)) != cudaSuccess) {
     (void)cudaGetLastError();
     rc = fail(POLAR_ENOMEM, "cudaMallocHost failed");
   }
@@ -729,6 +1257,8 @@ int polar_set_coeffs(polar_ctx* c, const polar_coeffs* k) {
   }
   c->nsrc = k->nsrc;
   c->cur_alpha = c->cur_beta = -1.0;  // the per-step parts must be refreshed
+  c->graph_ok = false;                // the step graph bakes in the source count
+  c->generation += 1;
   CUDA_TRY(cudaStreamSynchronize(c->st));
   c->have_coeffs = true;
   return POLAR_OK;
@@ -773,38 +1303,102 @@ int polar_get_state(polar_ctx* c, double* u, double* t, int32_t memory) {
 
 int polar_step(polar_ctx* c, double dt, double theta, const double* w_old, const double* w_new,
                const polar_solver_opts* opts, polar_step_stats* stats) {
-  return do_step(c, dt, theta, w_old, w_new, opts, stats);
+  if (!c) return fail(POLAR_EINVAL, "null context");
+  if (!(dt > 0.0) || !std::isfinite(dt)) return fail(POLAR_EINVAL, "dt must be positive and finite");
+  if (c->nsrc > 0 && (!w_old || !w_new)) return fail(POLAR_EINVAL, "source weights required");
+  const double t[2] = {c->t, c->t + dt};
+  double w[8];
+  for (int q = 0; q < c->nsrc; ++q) {
+    w[q] = w_old[q];
+    w[c->nsrc + q] = w_new[q];
+  }
+  return advance(c, 1, t, theta, c->nsrc ? w : nullptr, opts, stats);
 }
 
 int polar_advance(polar_ctx* c, int32_t nsteps, const double* t, double theta, const double* w,
                   const polar_solver_opts* opts, polar_step_stats* stats) {
-  if (!c || !t) return fail(POLAR_EINVAL, "null argument");
-  if (nsteps < 0) return fail(POLAR_EINVAL, "nsteps must be >= 0");
-  if (c->nsrc > 0 && !w) return fail(POLAR_EINVAL, "weights required");
-  if (!c->have_coeffs || !c->have_state) return fail(POLAR_ESTATE, "set_coeffs and set_state must come first");
-  if (std::fabs(t[0] - c->t) > 1e-12 * std::max(1.0, std::fabs(c->t)))
-    return fail(POLAR_EINVAL, "t[0] must equal the current time");
-  for (int k = 0; k < nsteps; ++k)
-    if (!(t[k + 1] > t[k])) return fail(POLAR_EINVAL, "time levels must increase");
-  const int Q = c->nsrc;
-  for (int k = 0; k < nsteps; ++k) {
-    polar_step_stats s{};
-    const double tk = c->t;
-    int rc = do_step(c, t[k + 1] - t[k], theta, Q ? w + (size_t)k * Q : nullptr,
-                     Q ? w + (size_t)(k + 1) * Q : nullptr, opts, &s);
-    if (rc == POLAR_OK) c->t = t[k + 1];  // the exact level, not an accumulated sum
-    else c->t = tk;
-    if (stats) stats[k] = s;
-    if (rc != POLAR_OK) {
-      if (stats)
-        for (int q = k + 1; q < nsteps; ++q) {
-          stats[q] = polar_step_stats{};
-          stats[q].status = POLAR_ESTATE;
-        }
-      return rc;
-    }
+  return advance(c, nsteps, t, theta, w, opts, stats);
+}
+
+int polar_batch_create(polar_ctx* const* ctxs, int32_t count, void* stream, polar_batch** out) {
+  if (!ctxs || !out || count <= 0) return fail(POLAR_EINVAL, "need count > 0 contexts");
+  *out = nullptr;
+  int dev = -1;
+  for (int i = 0; i < count; ++i) {
+    if (!ctxs[i]) return fail(POLAR_EINVAL, "null context in the batch");
+    if (dev >= 0 && ctxs[i]->device != dev) return fail(POLAR_EINVAL, "all contexts must share one device");
+    dev = ctxs[i]->device;
+    for (int k = 0; k < i; ++k)
+      if (ctxs[k] == ctxs[i]) return fail(POLAR_EINVAL, "a context appears twice in the batch");
   }
+  polar_batch* b = new polar_batch();
+  b->ctx.assign(ctxs, ctxs + count);
+  b->st = static_cast<cudaStream_t>(stream);
+  *out = b;
   return POLAR_OK;
+}
+
+int polar_batch_destroy(polar_batch* b) {
+  if (!b) return POLAR_OK;
+  if (!b->ctx.empty()) cudaSetDevice(b->ctx[0]->device);
+  cudaStreamSynchronize(b->st);
+  if (b->ex) cudaGraphExecDestroy(b->ex);
+  if (b->g) cudaGraphDestroy(b->g);
+  delete b;
+  return POLAR_OK;
+}
+
+int polar_batch_advance(polar_batch* b, int32_t nsteps, const double* const* t, const double* theta,
+                        const double* const* w, const polar_solver_opts* opts,
+                        polar_step_stats* stats) {
+  if (!b || !t || !theta) return fail(POLAR_EINVAL, "null argument");
+  const int count = (int)b->ctx.size();
+  const polar_solver_opts o = resolve_opts(opts);
+  CUDA_TRY(cudaSetDevice(b->ctx[0]->device));
+  for (int i = 0; i < count; ++i) {
+    polar_ctx* c = b->ctx[i];
+    TRY(check_schedule_args(c, nsteps, t[i], theta[i], w ? w[i] : nullptr));
+    if (!c->use_graph) return fail(POLAR_ESTATE, "a context of the batch cannot run as a graph");
+  }
+  if (nsteps == 0) return POLAR_OK;
+  for (int i = 0; i < count; ++i) {
+    polar_ctx* c = b->ctx[i];
+    c->cs = c->st;
+    if (c->autotune && !c->tuned) TRY(prepare_tuning(c, t[i], theta[i], w ? w[i] : nullptr, o));
+    TRY(load_schedule(c, nsteps, t[i], theta[i], w ? w[i] : nullptr, o));
+    CUDA_TRY(cudaStreamSynchronize(c->st));  // uploads land before the batch graph runs
+  }
+  bool stale = !b->ex || (int)b->gens.size() != count;
+  for (int i = 0; !stale && i < count; ++i) stale = b->gens[i] != b->ctx[i]->generation;
+  if (stale) {
+    if (b->ex) cudaGraphExecDestroy(b->ex);
+    if (b->g) cudaGraphDestroy(b->g);
+    b->ex = nullptr;
+    b->g = nullptr;
+    CUDA_TRY(cudaGraphCreate(&b->g, 0));
+    for (int i = 0; i < count; ++i) {
+      polar_ctx* c = b->ctx[i];
+      const int rc = (c->precision == POLAR_FP64) ? append_step<double>(c, b->g)
+                                                  : append_step<float>(c, b->g);
+      if (rc != POLAR_OK) {
+        abandon_capture(c);
+        return rc;
+      }
+    }
+    CUDA_TRY(cudaGraphInstantiate(&b->ex, b->g, 0));
+    b->gens.resize(count);
+    for (int i = 0; i < count; ++i) b->gens[i] = b->ctx[i]->generation;
+  }
+  // one graph launch advances every instance by one step; instances run as independent
+  // branches of the graph
+  for (int k = 0; k < nsteps; ++k) CUDA_TRY(cudaGraphLaunch(b->ex, b->st));
+  CUDA_TRY(cudaStreamSynchronize(b->st));
+  int rc = POLAR_OK;
+  for (int i = 0; i < count; ++i) {
+    const int r = finish_schedule(b->ctx[i], nsteps, t[i], stats ? stats + (size_t)i * nsteps : nullptr);
+    if (rc == POLAR_OK && r != POLAR_OK) rc = r;
+  }
+  return rc;
 }
 
 int polar_apply_operator(polar_ctx* c, double alpha, double beta, const double* x, double* y,
@@ -818,14 +1412,19 @@ int polar_apply_operator(polar_ctx* c, double alpha, double beta, const double* 
   const cudaMemcpyKind in = memory == POLAR_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
   const cudaMemcpyKind outk = memory == POLAR_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
   // S = alpha V + beta V L on the FP64 fine level (diag from a refresh), y = S x / V
-  if (c->precision == POLAR_FP64) {
-    TRY(refresh<double>(c, alpha, beta));
-  } else {
-    TRY(refresh<float>(c, alpha, beta));
+  c->cs = c->st;
+  const double zero[4] = {0, 0, 0, 0};
+  TRY(set_step_params(c, alpha, beta, zero, zero, resolve_opts(nullptr)));
+  if (c->sp_host->do_refresh) {
+    if (c->precision == POLAR_FP64) {
+      TRY(launch_refresh_all<double>(c));
+    } else {
+      TRY(launch_refresh_all<float>(c));
+    }
   }
   CUDA_TRY(cudaMemcpyAsync(c->io, x, N * sizeof(double), in, c->st));
   LAUNCH(launch_pack(c->sh0(), c->io, nullptr, c->r64, c->st));
-  LAUNCH(launch_apply<double>(c->v64[0], c->par, c->r64, c->e, c->st, c->red()));
+  LAUNCH(launch_apply<double>(c->v64[0], c->par(), c->r64, c->e, c->st, c->red()));
   LAUNCH(launch_unpack(c->sh0(), c->e, c->lv[0].vol, c->io, c->st));
   CUDA_TRY(cudaMemcpyAsync(y, c->io, N * sizeof(double), outk, c->st));
   CUDA_TRY(cudaStreamSynchronize(c->st));

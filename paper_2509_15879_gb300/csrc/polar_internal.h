@@ -15,6 +15,7 @@
 #pragma once
 #include <cstddef>
 #include <cstdint>
+#include <vector>
 #include <cuda_runtime.h>
 
 namespace polar {
@@ -68,6 +69,7 @@ struct LevelView {
   const T* ib;   //   x_{2k+1} = ia x_{2k} + ib x_{2k+2} (x_0 = origin, x_{m+1} = 0)
   // per step
   T* diag;       // nv: alpha vol + beta (rs - w - e - s - nn)
+  T* rsum;       // nv, level 0 of the FP32 path: alpha vol + beta rs (row sums of S)
   T* fl;         // line factors of every ring's periodic angular line, nv each
   T* fui;
   T* fcu;
@@ -75,7 +77,7 @@ struct LevelView {
   T* fring;      // 2 per ring, ring order (odd rings, then even): vf, 1/(1 + v.q)
   T* fz;         // n: coarsest level only, T_1^{-1} (beta w_1)
   double* sc;    // scalars: [0] diag0, [1] coarsest Schur denominator, [2] sum_j o_j (static),
-                 //          [3] vol0, [4] rs0 (static)
+                 //          [3] vol0, [4] rs0 (static), [5] alpha vol0 + beta rs0
 };
 
 // Scalars of one Krylov solve, kept on the device so that no iteration needs the host.
@@ -92,7 +94,43 @@ struct KrylovScalars {
   double xmax;
   unsigned int counter;
   unsigned int pad1;
+  // step state of the device-side refinement loop (graph mode)
+  int failed;      // 0, or the POLAR_* error code of this step
+  int sweeps;      // FP64 residual evaluations
+  int iters_total; // Krylov iterations of all inner solves
+  int converged;
+  double scaled;   // last Jacobi-scaled residual max |r_i| / S_ii / max |x_i|
+  int halt;        // a step of the current schedule failed: the later ones are skipped
+  int pad2;
 };
+
+// Result of one step of a device-side schedule (graph mode).
+struct StepOut {
+  int iters;       // Krylov iterations of all inner solves
+  int sweeps;      // FP64 residual evaluations
+  int status;      // POLAR_OK, the step's error, or POLAR_ESTATE if skipped
+  int pad;
+  double scaled;   // final Jacobi-scaled residual
+};
+
+// Parameters of one theta-step, read by the kernels from device memory (the first two
+// entries are the Params of the level kernels).
+struct StepParams {
+  double alpha;      // 1 / dt
+  double beta;       // theta
+  double omt;        // 1 - theta
+  double cf[4];      // source weights of both levels
+  double cg[4];      // Dirichlet weights of both levels (negated)
+  double tol;        // refinement tolerance on the Jacobi-scaled residual
+  double inner_tol;  // relative residual reduction of each inner solve
+  int max_iter;
+  int max_refine;
+  int do_refresh;    // the per-step refresh runs only when alpha or beta changed
+  int pad;
+};
+
+// Conditional-node handle of a CUDA graph (0: not in a graph).
+using CondHandle = unsigned long long;
 
 struct Reduce {
   double* part;        // partial sums, kMaxBlocks * 4
@@ -126,23 +164,33 @@ int launch_resid64(const LevelView<double>& L, Params p, const double* x, const 
 // FP64 right-hand side of the theta-step in S form:
 //   e = (V/dt) u - (1 - theta) (V L) u + sum_q cf[q] Vsrc[q] - e_{m,j} sum_q cg[q] bnd[q][j]
 // (cg already carries the weights of both time levels).
-int launch_rhs(const LevelView<double>& L, double alpha, double one_minus_theta, const double* u,
-               int nsrc, const double* const* vsrc, const double* const* bnd, const double* cf,
-               const double* cg, double* e, cudaStream_t st, Reduce red);
+int launch_rhs(const LevelView<double>& L, const StepParams* sp, const double* u, int nsrc,
+               const double* const* vsrc, const double* const* bnd, double* e, cudaStream_t st,
+               Reduce red);
 
 // Per-step refresh of every level: diag, angular line factors, origin scalars and the
 // coarsest-level Schur data.  Factors are formed in FP64 and stored in T.
 template <typename T>
-int launch_refresh(const LevelView<double>* L64, LevelView<T>* LT, int nlev, Params p,
-                   double* ws, cudaStream_t st);
+int launch_refresh(const LevelView<double>* L64, LevelView<T>* LT, int nlev,
+                   const StepParams* sp, double* ws, cudaStream_t st);
 
 // Multigrid V(1,1) cycle pieces (polar_mg.cu).  mode 0 = pre-smoothing (the level's
 // x starts from zero), 1 = post-smoothing (x of the odd rings is corrected on the fly
 // with the coarser level's solution X); parity 1 = odd rings, 0 = even rings + origin.
 enum { RING_PRE = 0, RING_POST = 1 };
+// tile shape of a ring solve launch: RW lines per CTA, TW chunk threads per line, P angles
+// per thread, CS CTAs per cluster along the angle
+struct RingShape {
+  int RW, TW, P, CS;
+};
 template <typename T>
 int launch_ring(const LevelView<T>& L, const LevelView<T>& C, const T* b, T* x, const T* X,
-                Params p, int parity, int mode, const int* done, cudaStream_t st);
+                Params p, int parity, int mode, const int* done, cudaStream_t st,
+                const RingShape* shape = nullptr);
+template <typename T>
+void ring_candidates(int nlines, int n, std::vector<RingShape>& out);
+template <typename T>
+RingShape ring_default(int nlines, int n);
 // right-hand side of the coarser level from the odd rings' residual after pre-smoothing
 template <typename T>
 int launch_restrict(const LevelView<T>& L, const LevelView<T>& C, const T* x, T* B, Params p,
@@ -151,24 +199,54 @@ int launch_restrict(const LevelView<T>& L, const LevelView<T>& C, const T* x, T*
 template <typename T>
 int launch_coarsest(const LevelView<T>& L, const T* b, T* x, Params p, const int* done,
                     cudaStream_t st);
+// the V-cycle restricted to levels l0..nlev-1 (the coarse end of the hierarchy) in a
+// single CTA; level l0 takes b0/x0, deeper levels bl[l]/xl[l].  Returns 0 when the levels
+// are too large for it (nothing launched).
+template <typename T>
+int launch_coarse_cycle(const LevelView<T>* L, int l0, int nlev, const T* b0, T* x0,
+                        T* const* bl, T* const* xl, Params p, const int* done, cudaStream_t st);
+// lines of one parity per level up to which the coarse cycle applies
+template <typename T>
+int coarse_cycle_lines();
 
 // ---- BiCGStab vector kernels
 template <typename T>
-int launch_bicg_init(size_t nv, const T* r, T* rhat, T* p, T* v, T* x, bool zero_x,
-                     double rel_tol, int max_iter, cudaStream_t st, Reduce red);
+int launch_bicg_init(size_t nv, const T* r, T* rhat, T* p, T* v, T* x, const StepParams* sp,
+                     CondHandle cond, cudaStream_t st, Reduce red);
 template <typename T>
 int launch_bicg_s(size_t nv, const T* r, const T* v, T* s, cudaStream_t st, Reduce red);
 template <typename T>
 int launch_bicg_update(size_t nv, T* x, const T* phat, const T* shat, T* r, const T* s,
                        const T* t, const T* rhat, cudaStream_t st, Reduce red);
 template <typename T>
-int launch_bicg_p(size_t nv, T* p, const T* r, const T* v, cudaStream_t st, Reduce red);
+int launch_bicg_p(size_t nv, T* p, const T* r, const T* v, CondHandle cond, cudaStream_t st,
+                  Reduce red);
+
+// ---- device-side step control (graph mode; the host does the same in eager mode)
+// reset the step state
+int launch_step_begin(cudaStream_t st, Reduce red);
+// schedule-driven steps: load step *kstep of `sched` into `sp` and reset the step state
+// (cond = 1), or record the step as skipped (cond = 0) after an earlier failure
+int launch_sched_begin(const StepParams* sched, const int* kstep, StepParams* sp,
+                       StepOut* out, CondHandle cond, cudaStream_t st, Reduce red);
+// record the step's result; a failure halts the rest of the schedule
+int launch_sched_end(const int* kstep, StepOut* out, cudaStream_t st, Reduce red);
+// next step of the schedule
+int launch_sched_next(int* kstep, cudaStream_t st);
+// after an FP64 residual: converged / failed / continue; sets `cond` to continue
+int launch_refine_decide(const StepParams* sp, CondHandle cond, cudaStream_t st, Reduce red);
+// after an inner solve: count its iterations, fail on a non-finite value
+int launch_after_inner(cudaStream_t st, Reduce red);
+// U = X when the step converged
+int launch_commit(size_t nv, double* U, const double* X, cudaStream_t st, Reduce red);
 
 // ---- mixed-precision helpers
 template <typename T>
 int launch_scale_cast(size_t nv, const double* r, T* rs, cudaStream_t st, Reduce red);
 template <typename T>
 int launch_correct(size_t nv, double* x, const T* d, cudaStream_t st, Reduce red);
+// copy of n doubles (skipped when the step failed)
+int launch_copy(size_t n, const double* a, double* b, cudaStream_t st, Reduce red);
 int launch_to_float(size_t n, const double* a, float* b, cudaStream_t st);
 int launch_check_finite(size_t n, const double* a, cudaStream_t st, Reduce red);
 

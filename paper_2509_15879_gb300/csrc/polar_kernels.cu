@@ -192,13 +192,28 @@ __global__ void __launch_bounds__(256) k_stencil(StArgs<T> a) {
     const T xc = x[idx];
     const T xw = (west == 0) ? x0 : x[west];
     const T xe = (east == (size_t)-1) ? T(0) : x[east];
-    T off = L.w[idx] * xw;
-    off = fma(L.e[idx], xe, off);
-    off = fma(L.s[idx], x[south], off);
-    off = fma(L.nn[idx], x[north], off);
-    const T dg = L.diag[idx];
-    T val = fma(beta, off, dg * xc);
-    if (i == 1) acc[0] = fma((double)L.o[j], (double)xc, acc[0]);
+    T val;
+    T dg = T(0);
+    if (sizeof(T) == 8) {
+      // FP64: direct form diag x + beta (w xW + e xE + s xS + nn xN)
+      T off = L.w[idx] * xw;
+      off = fma(L.e[idx], xe, off);
+      off = fma(L.s[idx], x[south], off);
+      off = fma(L.nn[idx], x[north], off);
+      dg = L.diag[idx];
+      val = fma(beta, off, dg * xc);
+      if (i == 1) acc[0] = fma((double)L.o[j], (double)xc, acc[0]);
+    } else {
+      // FP32: difference form rsum x + beta (w (xW - x) + ...): near the origin the angular
+      // couplings exceed the row sum by many orders of magnitude, and differences of
+      // neighbouring values lose no digits where the direct form would cancel
+      T off = L.w[idx] * (xw - xc);
+      off = fma(L.e[idx], xe - xc, off);
+      off = fma(L.s[idx], x[south] - xc, off);
+      off = fma(L.nn[idx], x[north] - xc, off);
+      val = fma(beta, off, L.rsum[idx] * xc);
+      if (i == 1) acc[0] = fma((double)L.o[j], (double)xc - (double)x0, acc[0]);
+    }
     if (MODE == M_RESID64) {
       val = a.b[idx] - val;
       const double ar = absfin((double)val);
@@ -224,7 +239,8 @@ __global__ void __launch_bounds__(256) k_stencil(StArgs<T> a) {
   KrylovScalars* ks = a.red.ks;
   const double d0 = L.sc[0];
   const double x0d = (double)x0;
-  double y0 = fma((double)beta, tot[0], d0 * x0d);
+  double y0 = (sizeof(T) == 8) ? fma((double)beta, tot[0], d0 * x0d)
+                                : fma((double)beta, tot[0], L.sc[5] * x0d);
   if (MODE == M_RESID64) y0 = (double)a.b[0] - y0;
   const T y0t = (T)y0;
   a.y[0] = y0t;
@@ -301,13 +317,12 @@ int launch_resid64(const LevelView<double>& L, Params p, const double* x, const 
 // ------------------------------------------------------------------ right-hand side
 struct RhsArgs {
   LevelView<double> L;
-  double alpha, omt;  // 1/dt, 1 - theta
+  const StepParams* sp;
   const double* u;
   double* e;
   int nsrc;
   const double* vsrc[4];
   const double* bnd[4];
-  double cf[4], cg[4];
   Reduce red;
   Tiling t;
 };
@@ -317,6 +332,12 @@ struct RhsArgs {
 // levels (g_j = sum_q cg_q bnd_q[j], Eq. 2.9) moved to the right-hand side.
 __global__ void __launch_bounds__(256) k_rhs(RhsArgs a) {
   const LevelView<double>& L = a.L;
+  const double alpha = a.sp->alpha, omt = a.sp->omt;
+  double cf[4], cg[4];
+  for (int q = 0; q < 4; ++q) {
+    cf[q] = a.sp->cf[q];
+    cg[q] = a.sp->cg[q];
+  }
   double acc[1] = {0.0};
   const double* __restrict__ u = a.u;
   const double u0 = u[0];
@@ -332,11 +353,11 @@ __global__ void __launch_bounds__(256) k_rhs(RhsArgs a) {
     Lu = fma(e, ue, Lu);
     Lu = fma(s, u[south], Lu);
     Lu = fma(nn, u[north], Lu);
-    double val = fma(-a.omt, Lu, a.alpha * L.vol[idx] * uc);
-    for (int q = 0; q < a.nsrc; ++q) val = fma(a.cf[q], a.vsrc[q][idx], val);
+    double val = fma(-omt, Lu, alpha * L.vol[idx] * uc);
+    for (int q = 0; q < a.nsrc; ++q) val = fma(cf[q], a.vsrc[q][idx], val);
     if (i == L.sh.m) {
       double g = 0.0;
-      for (int q = 0; q < a.nsrc; ++q) g = fma(a.cg[q], a.bnd[q][j], g);
+      for (int q = 0; q < a.nsrc; ++q) g = fma(cg[q], a.bnd[q][j], g);
       val = fma(e, g, val);
     }
     if (i == 1) acc[0] = fma(L.o[j], uc, acc[0]);
@@ -349,27 +370,24 @@ __global__ void __launch_bounds__(256) k_rhs(RhsArgs a) {
   if (threadIdx.x + blockDim.x * threadIdx.y != 0) return;
   const double vol0 = L.sc[3], rs0 = L.sc[4], osum = L.sc[2];
   const double Lu0 = fma(rs0 - osum, u0, tot[0]);
-  double e0 = fma(-a.omt, Lu0, a.alpha * vol0 * u0);
-  for (int q = 0; q < a.nsrc; ++q) e0 = fma(a.cf[q], a.vsrc[q][0], e0);
+  double e0 = fma(-omt, Lu0, alpha * vol0 * u0);
+  for (int q = 0; q < a.nsrc; ++q) e0 = fma(cf[q], a.vsrc[q][0], e0);
   a.e[0] = e0;
   a.red.ks->counter = 0;
 }
 
-int launch_rhs(const LevelView<double>& L, double alpha, double one_minus_theta, const double* u,
-               int nsrc, const double* const* vsrc, const double* const* bnd, const double* cf,
-               const double* cg, double* e, cudaStream_t st, Reduce red) {
+int launch_rhs(const LevelView<double>& L, const StepParams* sp, const double* u, int nsrc,
+               const double* const* vsrc, const double* const* bnd, double* e, cudaStream_t st,
+               Reduce red) {
   RhsArgs a{};
   a.L = L;
-  a.alpha = alpha;
-  a.omt = one_minus_theta;
+  a.sp = sp;
   a.u = u;
   a.e = e;
   a.nsrc = nsrc;
   for (int q = 0; q < nsrc; ++q) {
     a.vsrc[q] = vsrc[q];
     a.bnd[q] = bnd[q];
-    a.cf[q] = cf[q];
-    a.cg[q] = cg[q];
   }
   a.red = red;
   a.t = make_tiling(L.sh);
@@ -381,10 +399,16 @@ int launch_rhs(const LevelView<double>& L, double alpha, double one_minus_theta,
 // ------------------------------------------------------------------ BiCGStab vectors
 constexpr int kVT = 256;
 
+__device__ __forceinline__ void set_cond(CondHandle cond, bool value) {
+  if (cond) cudaGraphSetConditional((cudaGraphConditionalHandle)cond, value ? 1u : 0u);
+}
+
 template <typename T>
 __global__ void __launch_bounds__(kVT) k_bicg_init(size_t nv, const T* r, T* rhat, T* p, T* v,
-                                                   T* x, int zero_x, double rel_tol,
-                                                   int max_iter, Reduce red) {
+                                                   T* x, const StepParams* sp, CondHandle cond,
+                                                   Reduce red) {
+  const double rel_tol = sp->inner_tol;
+  const int max_iter = sp->max_iter;
   double acc[1];
   double s = 0.0;
   for (size_t k = blockIdx.x * (size_t)kVT + threadIdx.x; k < nv; k += (size_t)gridDim.x * kVT) {
@@ -392,7 +416,7 @@ __global__ void __launch_bounds__(kVT) k_bicg_init(size_t nv, const T* r, T* rha
     rhat[k] = rv;
     p[k] = rv;
     v[k] = T(0);
-    if (zero_x) x[k] = T(0);
+    x[k] = T(0);
     s = fma((double)rv, (double)rv, s);
   }
   acc[0] = s;
@@ -413,6 +437,7 @@ __global__ void __launch_bounds__(kVT) k_bicg_init(size_t nv, const T* r, T* rha
   ks->max_iter = max_iter;
   ks->done = !isfinite(tot[0]) ? 3 : (tot[0] == 0.0 ? 1 : 0);
   ks->counter = 0;
+  set_cond(cond, ks->done == 0);
 }
 
 template <typename T>
@@ -465,18 +490,19 @@ __global__ void __launch_bounds__(kVT) k_bicg_update(size_t nv, T* x, const T* p
 
 template <typename T>
 __global__ void __launch_bounds__(kVT) k_bicg_p(size_t nv, T* p, const T* r, const T* v,
-                                                KrylovScalars* ks) {
-  if (ks->done) return;
+                                                KrylovScalars* ks, CondHandle cond) {
+  const bool running = ks->done == 0;
+  if (blockIdx.x == 0 && threadIdx.x == 0) set_cond(cond, running);
+  if (!running) return;
   const T beta = (T)ks->beta, omega = (T)ks->omega;
   for (size_t k = blockIdx.x * (size_t)kVT + threadIdx.x; k < nv; k += (size_t)gridDim.x * kVT)
     p[k] = fma(beta, fma(-omega, v[k], p[k]), r[k]);
 }
 
 template <typename T>
-int launch_bicg_init(size_t nv, const T* r, T* rhat, T* p, T* v, T* x, bool zero_x,
-                     double rel_tol, int max_iter, cudaStream_t st, Reduce red) {
-  k_bicg_init<T><<<grid_for(nv, kVT), kVT, 0, st>>>(nv, r, rhat, p, v, x, zero_x ? 1 : 0, rel_tol,
-                                                    max_iter, red);
+int launch_bicg_init(size_t nv, const T* r, T* rhat, T* p, T* v, T* x, const StepParams* sp,
+                     CondHandle cond, cudaStream_t st, Reduce red) {
+  k_bicg_init<T><<<grid_for(nv, kVT), kVT, 0, st>>>(nv, r, rhat, p, v, x, sp, cond, red);
   return 1;
 }
 template <typename T>
@@ -491,8 +517,114 @@ int launch_bicg_update(size_t nv, T* x, const T* phat, const T* shat, T* r, cons
   return 1;
 }
 template <typename T>
-int launch_bicg_p(size_t nv, T* p, const T* r, const T* v, cudaStream_t st, Reduce red) {
-  k_bicg_p<T><<<grid_for(nv, kVT), kVT, 0, st>>>(nv, p, r, v, red.ks);
+int launch_bicg_p(size_t nv, T* p, const T* r, const T* v, CondHandle cond, cudaStream_t st,
+                  Reduce red) {
+  k_bicg_p<T><<<grid_for(nv, kVT), kVT, 0, st>>>(nv, p, r, v, red.ks, cond);
+  return 1;
+}
+
+// ------------------------------------------------------------------ step control
+__global__ void k_step_begin(KrylovScalars* ks) {
+  ks->failed = 0;
+  ks->sweeps = 0;
+  ks->iters_total = 0;
+  ks->converged = 0;
+  ks->scaled = 0.0;
+  ks->done = 0;
+  ks->counter = 0;
+}
+int launch_step_begin(cudaStream_t st, Reduce red) {
+  k_step_begin<<<1, 1, 0, st>>>(red.ks);
+  return 1;
+}
+
+__global__ void k_sched_begin(const StepParams* sched, const int* kstep, StepParams* sp,
+                              StepOut* out, CondHandle cond, KrylovScalars* ks) {
+  const int k = *kstep;
+  if (ks->halt) {
+    out[k] = StepOut{0, 0, -7, 0, 0.0};  // POLAR_ESTATE: not run
+    set_cond(cond, false);
+    return;
+  }
+  *sp = sched[k];
+  ks->failed = 0;
+  ks->sweeps = 0;
+  ks->iters_total = 0;
+  ks->converged = 0;
+  ks->scaled = 0.0;
+  ks->done = 0;
+  ks->counter = 0;
+  set_cond(cond, true);
+}
+int launch_sched_begin(const StepParams* sched, const int* kstep, StepParams* sp, StepOut* out,
+                       CondHandle cond, cudaStream_t st, Reduce red) {
+  k_sched_begin<<<1, 1, 0, st>>>(sched, kstep, sp, out, cond, red.ks);
+  return 1;
+}
+
+__global__ void k_sched_end(const int* kstep, StepOut* out, KrylovScalars* ks) {
+  out[*kstep] = StepOut{ks->iters_total, ks->sweeps, ks->failed, 0, ks->scaled};
+  if (ks->failed) ks->halt = 1;
+}
+int launch_sched_end(const int* kstep, StepOut* out, cudaStream_t st, Reduce red) {
+  k_sched_end<<<1, 1, 0, st>>>(kstep, out, red.ks);
+  return 1;
+}
+
+__global__ void k_sched_next(int* kstep) { *kstep += 1; }
+int launch_sched_next(int* kstep, cudaStream_t st) {
+  k_sched_next<<<1, 1, 0, st>>>(kstep);
+  return 1;
+}
+
+// After the FP64 residual (rmax, smax, xmax): the step has converged when the
+// Jacobi-scaled residual is within the tolerance; it fails after max_refine corrections
+// or on a non-finite residual.
+__global__ void k_refine_decide(const StepParams* sp, CondHandle cond, KrylovScalars* ks) {
+  bool more = false;
+  if (ks->failed == 0) {
+    ks->sweeps += 1;
+    const double scaled = ks->smax / fmax(ks->xmax, 1e-300);
+    ks->scaled = scaled;
+    if (!isfinite(scaled) || !isfinite(ks->rmax)) {
+      ks->failed = -5;  // POLAR_ENONFINITE
+    } else if (scaled <= sp->tol) {
+      ks->converged = 1;
+    } else if (ks->sweeps > sp->max_refine) {
+      ks->failed = -4;  // POLAR_ENOCONV
+    } else {
+      more = true;
+    }
+  }
+  set_cond(cond, more);
+}
+int launch_refine_decide(const StepParams* sp, CondHandle cond, cudaStream_t st, Reduce red) {
+  k_refine_decide<<<1, 1, 0, st>>>(sp, cond, red.ks);
+  return 1;
+}
+
+__global__ void k_after_inner(KrylovScalars* ks) {
+  ks->iters_total += ks->iters;
+  if (ks->done == 3 && ks->failed == 0) ks->failed = -5;  // POLAR_ENONFINITE
+}
+int launch_after_inner(cudaStream_t st, Reduce red) {
+  k_after_inner<<<1, 1, 0, st>>>(red.ks);
+  return 1;
+}
+
+__global__ void __launch_bounds__(kVT) k_copy_if(size_t n, const double* a, double* b,
+                                                 const KrylovScalars* ks, int need_converged) {
+  if (ks->failed) return;
+  if (need_converged && !ks->converged) return;
+  for (size_t k = blockIdx.x * (size_t)kVT + threadIdx.x; k < n; k += (size_t)gridDim.x * kVT)
+    b[k] = a[k];
+}
+int launch_commit(size_t nv, double* U, const double* X, cudaStream_t st, Reduce red) {
+  k_copy_if<<<grid_for(nv, kVT), kVT, 0, st>>>(nv, X, U, red.ks, 1);
+  return 1;
+}
+int launch_copy(size_t n, const double* a, double* b, cudaStream_t st, Reduce red) {
+  k_copy_if<<<grid_for(n, kVT), kVT, 0, st>>>(n, a, b, red.ks, 0);
   return 1;
 }
 
@@ -507,6 +639,7 @@ __global__ void __launch_bounds__(kVT) k_scale_cast(size_t nv, const double* r, 
 template <typename T>
 __global__ void __launch_bounds__(kVT) k_correct(size_t nv, double* x, const T* d,
                                                  const KrylovScalars* ks) {
+  if (ks->failed) return;
   const double s = ks->rmax;
   for (size_t k = blockIdx.x * (size_t)kVT + threadIdx.x; k < nv; k += (size_t)gridDim.x * kVT)
     x[k] = fma(s, (double)d[k], x[k]);
@@ -589,12 +722,13 @@ int launch_unpack(const Shape& sh, const double* in, const double* div, double* 
                                Reduce);                                                        \
   template int launch_apply_dot<T>(const LevelView<T>&, Params, const T*, T*, const T*, int,   \
                                    cudaStream_t, Reduce);                                      \
-  template int launch_bicg_init<T>(size_t, const T*, T*, T*, T*, T*, bool, double, int,        \
-                                   cudaStream_t, Reduce);                                      \
+  template int launch_bicg_init<T>(size_t, const T*, T*, T*, T*, T*, const StepParams*,        \
+                                   CondHandle, cudaStream_t, Reduce);                          \
   template int launch_bicg_s<T>(size_t, const T*, const T*, T*, cudaStream_t, Reduce);         \
   template int launch_bicg_update<T>(size_t, T*, const T*, const T*, T*, const T*, const T*,   \
                                      const T*, cudaStream_t, Reduce);                          \
-  template int launch_bicg_p<T>(size_t, T*, const T*, const T*, cudaStream_t, Reduce);         \
+  template int launch_bicg_p<T>(size_t, T*, const T*, const T*, CondHandle, cudaStream_t,      \
+                                Reduce);                                                       \
   template int launch_scale_cast<T>(size_t, const double*, T*, cudaStream_t, Reduce);          \
   template int launch_correct<T>(size_t, double*, const T*, cudaStream_t, Reduce);
 

@@ -26,6 +26,8 @@
 // values through distributed shared memory.
 #include <cooperative_groups.h>
 
+#include <vector>
+
 #include "polar_internal.h"
 
 namespace cg = cooperative_groups;
@@ -47,6 +49,7 @@ struct RefreshLevel {
   double* sc;
   void* diag;
   double* diag64;  // FP64 copy of diag when T is float (level 0 only), else null
+  void* rsum;      // row sums alpha vol + beta rs when T is float (level 0 only), else null
   void* fl;
   void* fui;
   void* fcu;
@@ -61,7 +64,7 @@ constexpr int kMaxLevels = 20;
 struct RefreshArgs {
   RefreshLevel lv[kMaxLevels];
   int nlev;
-  const double* par;
+  const StepParams* sp;
 };
 
 // One thread per ring of every level.  Ring i of a level is the periodic tridiagonal
@@ -82,7 +85,8 @@ __global__ void k_refresh(RefreshArgs A) {
   const int local = g - L.ring0;
   const Shape sh = L.sh;
   if (local < 0 || local >= sh.m) return;
-  const double alpha = A.par[0], beta = A.par[1];
+  if (!A.sp->do_refresh) return;
+  const double alpha = A.sp->alpha, beta = A.sp->beta;
   // ring order: odd rings (local < no) then even rings
   const int i = (local < sh.no) ? 2 * local + 1 : 2 * (local - sh.no) + 2;
   const int n = sh.n;
@@ -104,40 +108,80 @@ __global__ void k_refresh(RefreshArgs A) {
   const double cn1 = beta * L.nn[qn];
   const double gamma = -b0;
   const double vf = a0 / gamma;
-  double uprev = 1.0, cprev = 0.0, yq = 0.0;
-  for (int j = 0; j < n; ++j) {
-    const size_t q = sh.at(i, j);
-    const double a = (j > 0) ? beta * L.s[q] : 0.0;
-    const double bd = dg(q);
-    diag[q] = (T)bd;
-    if (L.diag64) L.diag64[q] = bd;
-    double b = bd;
-    if (j == 0) b -= gamma;
-    if (j == n - 1) b -= cn1 * vf;
-    const double c = (j < n - 1) ? beta * L.nn[q] : 0.0;
-    const double lj = (j > 0) ? a / uprev : 0.0;
-    const double u = b - lj * cprev;
-    const double ui = 1.0 / u;
-    fl[q] = (T)lj;
-    fui[q] = (T)ui;
-    fcu[q] = (T)(c * ui);
-    const double ur = (j == 0) ? gamma : ((j == n - 1) ? cn1 : 0.0);
-    yq = ur - lj * yq;
-    wy[q] = yq;
-    wu[q] = ui;
-    uprev = u;
-    cprev = c;
+  const size_t ld = (i & 1) ? sh.ldo : sh.lde;
+  // the coefficient loads do not depend on the recurrence: they are issued U angles
+  // ahead so that the division chain, not the memory latency, sets the pace
+  constexpr int U = 8;
+  double uiprev = 1.0, cprev = 0.0, yq = 0.0;
+  for (int jb = 0; jb < n; jb += U) {
+    double cv[U], cr[U], cw[U], ce[U], cs[U], cn[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int j = jb + u;
+      if (j < n) {
+        const size_t q = q0 + (size_t)j * ld;
+        cv[u] = L.vol[q];
+        cr[u] = L.rs[q];
+        cw[u] = L.w[q];
+        ce[u] = L.e[q];
+        cs[u] = L.s[q];
+        cn[u] = L.nn[q];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int j = jb + u;
+      if (j >= n) break;
+      const size_t q = q0 + (size_t)j * ld;
+      const double a = (j > 0) ? beta * cs[u] : 0.0;
+      const double bd = alpha * cv[u] + beta * (cr[u] - cw[u] - ce[u] - cs[u] - cn[u]);
+      diag[q] = (T)bd;
+      if (L.diag64) L.diag64[q] = bd;
+      if (L.rsum) static_cast<T*>(L.rsum)[q] = (T)(alpha * cv[u] + beta * cr[u]);
+      double bb = bd;
+      if (j == 0) bb -= gamma;
+      if (j == n - 1) bb -= cn1 * vf;
+      const double c = (j < n - 1) ? beta * cn[u] : 0.0;
+      const double lj = (j > 0) ? a * uiprev : 0.0;
+      const double uu = bb - lj * cprev;
+      const double ui = 1.0 / uu;
+      fl[q] = (T)lj;
+      fui[q] = (T)ui;
+      fcu[q] = (T)(c * ui);
+      const double ur = (j == 0) ? gamma : ((j == n - 1) ? cn1 : 0.0);
+      yq = ur - lj * yq;
+      wy[q] = yq;
+      wu[q] = ui;
+      uiprev = ui;
+      cprev = c;
+    }
   }
   double qnext = 0.0, qfirst = 0.0, qlast = 0.0;
-  for (int j = n - 1; j >= 0; --j) {
-    const size_t q = sh.at(i, j);
-    const double c = (j < n - 1) ? beta * L.nn[q] : 0.0;
-    const double qq = wu[q] * (wy[q] - c * qnext);
-    fq[q] = (T)qq;
-    wq[q] = qq;
-    if (j == n - 1) qlast = qq;
-    if (j == 0) qfirst = qq;
-    qnext = qq;
+  for (int jb = n - 1; jb >= 0; jb -= U) {
+    double cu[U], cy[U], cn[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int j = jb - u;
+      if (j >= 0) {
+        const size_t q = q0 + (size_t)j * ld;
+        cu[u] = wu[q];
+        cy[u] = wy[q];
+        cn[u] = L.nn[q];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int j = jb - u;
+      if (j < 0) break;
+      const size_t q = q0 + (size_t)j * ld;
+      const double c = (j < n - 1) ? beta * cn[u] : 0.0;
+      const double qq = cu[u] * (cy[u] - c * qnext);
+      fq[q] = (T)qq;
+      wq[q] = qq;
+      if (j == n - 1) qlast = qq;
+      if (j == 0) qfirst = qq;
+      qnext = qq;
+    }
   }
   const double inv = 1.0 / (1.0 + qfirst + vf * qlast);
   fring[2 * local] = (T)vf;
@@ -146,55 +190,19 @@ __global__ void k_refresh(RefreshArgs A) {
     // origin scalars of this level: diag0 = alpha vol0 + beta (rs0 - sum_j o_j)
     const double d0 = alpha * L.sc[3] + beta * (L.sc[4] - L.sc[2]);
     L.sc[0] = d0;
-    if (L.coarsest) {
-      // z = T_1^{-1} (beta w_1) in FP64 (forward values reuse wy), then the Schur
-      // denominator diag0 - beta sum_j o_j z_j of the origin row
-      T* fz = static_cast<T*>(L.fz);
-      // forward substitution with l_j recomputed in FP64
-      double up = 1.0, cp = 0.0, yz = 0.0;
-      for (int j = 0; j < n; ++j) {
-        const size_t q = sh.at(i, j);
-        const double a = (j > 0) ? beta * L.s[q] : 0.0;
-        double b = dg(q);
-        if (j == 0) b -= gamma;
-        if (j == n - 1) b -= cn1 * vf;
-        const double c = (j < n - 1) ? beta * L.nn[q] : 0.0;
-        const double lj = (j > 0) ? a / up : 0.0;
-        const double u = b - lj * cp;
-        yz = beta * L.w[q] - lj * yz;
-        wy[q] = yz;
-        up = u;
-        cp = c;
-      }
-      double xn = 0.0, x0v = 0.0, xl = 0.0;
-      for (int j = n - 1; j >= 0; --j) {
-        const size_t q = sh.at(i, j);
-        const double c = (j < n - 1) ? beta * L.nn[q] : 0.0;
-        const double xv = wu[q] * (wy[q] - c * xn);
-        wy[q] = xv;
-        if (j == n - 1) xl = xv;
-        if (j == 0) x0v = xv;
-        xn = xv;
-      }
-      const double sigma = (x0v + vf * xl) * inv;
-      double dot = 0.0;
-      for (int j = 0; j < n; ++j) {
-        const size_t q = sh.at(i, j);
-        const double zj = wy[q] - sigma * wq[q];
-        fz[j] = (T)zj;
-        dot += L.o[j] * zj;
-      }
-      L.sc[1] = d0 - beta * dot;
-    }
+    L.sc[5] = alpha * L.sc[3] + beta * L.sc[4];
   }
 }
 
 template <typename T>
-int launch_refresh(const LevelView<double>* L64, LevelView<T>* LT, int nlev, Params p,
-                   double* ws, cudaStream_t st) {
+static int launch_schur(const LevelView<T>& L, const StepParams* sp, cudaStream_t st);
+
+template <typename T>
+int launch_refresh(const LevelView<double>* L64, LevelView<T>* LT, int nlev,
+                   const StepParams* sp, double* ws, cudaStream_t st) {
   RefreshArgs A{};
   A.nlev = nlev;
-  A.par = p;
+  A.sp = sp;
   int rings = 0;
   size_t wofs = 0;
   for (int l = 0; l < nlev; ++l) {
@@ -211,6 +219,7 @@ int launch_refresh(const LevelView<double>* L64, LevelView<T>* LT, int nlev, Par
     r.sc = LT[l].sc;
     r.diag = LT[l].diag;
     r.diag64 = (sizeof(T) == 4 && l == 0) ? L64[0].diag : nullptr;
+    r.rsum = (sizeof(T) == 4 && l == 0) ? (void*)LT[0].rsum : nullptr;
     r.fl = LT[l].fl;
     r.fui = LT[l].fui;
     r.fcu = LT[l].fcu;
@@ -223,36 +232,12 @@ int launch_refresh(const LevelView<double>* L64, LevelView<T>* LT, int nlev, Par
     r.ring0 = rings;
     rings += d.sh.m;
   }
-  k_refresh<T><<<(rings + 63) / 64, 64, 0, st>>>(A);
-  return 1;
+  k_refresh<T><<<(rings + 31) / 32, 32, 0, st>>>(A);
+  return 1 + launch_schur<T>(LT[nlev - 1], sp, st);
 }
 
 // ---------------------------------------------------------------------------------
 // ring solves
-
-// inclusive scan of affine maps x -> A x + B over positions 0..TW-1 of column r
-template <typename T>
-__device__ void scan_affine(T A, T B, T* sA, T* sB, int r, int pos, int RW, int TW) {
-  sA[pos * RW + r] = A;
-  sB[pos * RW + r] = B;
-  __syncthreads();
-  for (int off = 1; off < TW; off <<= 1) {
-    const T a = sA[pos * RW + r], b = sB[pos * RW + r];
-    T ao = T(1), bo = T(0);
-    const bool has = pos >= off;
-    if (has) {
-      ao = sA[(pos - off) * RW + r];
-      bo = sB[(pos - off) * RW + r];
-    }
-    __syncthreads();
-    if (has) {
-      sA[pos * RW + r] = a * ao;
-      sB[pos * RW + r] = fma(a, bo, b);
-    }
-    __syncthreads();
-  }
-}
-
 
 template <typename T>
 struct RingArgs {
@@ -376,61 +361,137 @@ __device__ __forceinline__ RingRhs<T> make_ring_rhs(const RingArgs<T>& a, T beta
   return r;
 }
 
+// Inclusive scan of affine maps x -> A x + B over the TW chunks of each line of the CTA
+// (thread (r, c), linear index r + RW c, so a warp holds 32 / RW consecutive chunks of
+// each of its RW lines).  Warp shuffles combine the chunks of a warp; the warp totals go
+// through shared memory once.  Returns, for this thread, the composed map of the chunks
+// before it (exclusive prefix) in (Ae, Be); `rev` scans from the last chunk down.
+template <typename T>
+__device__ __forceinline__ void chunk_scan(T A, T B, bool rev, T* sWA, T* sWB, T& Ae, T& Be,
+                                           T& At, T& Bt) {
+  const int RW = blockDim.x;
+  const int tid = threadIdx.x + RW * threadIdx.y;
+  const int lane = tid & 31, warp = tid >> 5;
+  const int nwarps = (RW * blockDim.y) >> 5;
+  const int per = 32 / RW;              // chunks of one line inside a warp
+  const int pos = lane / RW;            // position of this chunk inside the warp
+  const int r = threadIdx.x;
+  // warp-level inclusive scan (forward: from low positions, reverse: from high)
+  T a = A, b = B;
+  for (int off = 1; off < per; off <<= 1) {
+    const T ao = rev ? __shfl_down_sync(0xffffffffu, a, off * RW) : __shfl_up_sync(0xffffffffu, a, off * RW);
+    const T bo = rev ? __shfl_down_sync(0xffffffffu, b, off * RW) : __shfl_up_sync(0xffffffffu, b, off * RW);
+    const bool has = rev ? (pos + off < per) : (pos >= off);
+    if (has) {
+      b = fma(a, bo, b);
+      a = a * ao;
+    }
+  }
+  // warp-local exclusive map: the inclusive map of the neighbouring position
+  T ea = rev ? __shfl_down_sync(0xffffffffu, a, RW) : __shfl_up_sync(0xffffffffu, a, RW);
+  T eb = rev ? __shfl_down_sync(0xffffffffu, b, RW) : __shfl_up_sync(0xffffffffu, b, RW);
+  const bool first = rev ? (pos == per - 1) : (pos == 0);
+  if (first) {
+    ea = T(1);
+    eb = T(0);
+  }
+  // warp totals (held by the last position of the scan direction)
+  const bool last = rev ? (pos == 0) : (pos == per - 1);
+  if (last) {
+    sWA[warp * RW + r] = a;
+    sWB[warp * RW + r] = b;
+  }
+  __syncthreads();
+  // prefix of the warps before this one in the scan direction
+  T pa = T(1), pb = T(0);
+  if (!rev) {
+    for (int w = 0; w < warp; ++w) {
+      const T wa = sWA[w * RW + r], wb = sWB[w * RW + r];
+      pb = fma(wa, pb, wb);
+      pa = wa * pa;
+    }
+  } else {
+    for (int w = nwarps - 1; w > warp; --w) {
+      const T wa = sWA[w * RW + r], wb = sWB[w * RW + r];
+      pb = fma(wa, pb, wb);
+      pa = wa * pa;
+    }
+  }
+  // exclusive = warp-local exclusive o (prefix of earlier warps)
+  Ae = ea * pa;
+  Be = fma(ea, pb, eb);
+  // total of the CTA for this line
+  At = T(1);
+  Bt = T(0);
+  for (int w = 0; w < nwarps; ++w) {
+    const int ww = rev ? nwarps - 1 - w : w;
+    const T wa = sWA[ww * RW + r], wb = sWB[ww * RW + r];
+    Bt = fma(wa, Bt, wb);
+    At = wa * At;
+  }
+  __syncthreads();  // the buffers are reused by the next scan
+}
+
 // Solves the periodic lines of one CTA (RW lines x TW chunks of P) or one cluster.
-// Rhs(j) gives d_j of this thread's line; Out(j, x) stores the solution.
+// Rhs(j) gives d_j of this thread's line; Out(j, x) stores the solution.  The chunk's
+// right-hand side and LU factors are loaded once into registers (all loads in flight
+// together); the Sherman-Morrison vector is read at the end.
 template <typename T, int P, typename Rhs, typename Fac, typename Out>
 __device__ void solve_lines(int n, bool valid, Rhs rhs, Fac fac, T vf, T inv, Out out) {
   extern __shared__ unsigned char smraw[];
   const int RW = blockDim.x, TW = blockDim.y;
   const int r = threadIdx.x, c = threadIdx.y;
-  T* sA = reinterpret_cast<T*>(smraw);
-  T* sB = sA + RW * TW;
-  T* segA = sB + RW * TW;   // this CTA's segment map, per line
+  const int nwarps = (RW * TW) >> 5;
+  T* sWA = reinterpret_cast<T*>(smraw);
+  T* sWB = sWA + nwarps * RW;
+  T* segA = sWB + nwarps * RW;  // this CTA's segment map, per line
   T* segB = segA + RW;
-  T* ends = segB + RW;      // [0, RW): x_0 of the line, [RW, 2 RW): x_{n-1}
+  T* ends = segB + RW;          // [0, RW): x_0 of the line, [RW, 2 RW): x_{n-1}
   cg::cluster_group cl = cg::this_cluster();
   const int CS = (int)cl.num_blocks();
   const int crank = (int)cl.block_rank();
   const int gc = crank * TW + c;
   const int j0 = gc * P;
-  T v[P];
+  T v[P], fl[P], fu[P], fc[P];
 #pragma unroll
   for (int p = 0; p < P; ++p) {
     const int j = j0 + p;
-    v[p] = (valid && j < n) ? rhs(j) : T(0);
+    const bool in = valid && j < n;
+    v[p] = in ? rhs(j) : T(0);
+    fl[p] = in ? fac.l(j) : T(0);
+    fu[p] = in ? fac.ui(j) : T(0);
+    fc[p] = in ? fac.cu(j) : T(0);
   }
-  // forward substitution y_j = d_j - l_j y_{j-1}
+  // forward substitution y_j = d_j - l_j y_{j-1}  (padding: l = 0, d = 0 -> identity-like)
   T A = T(1), B = T(0);
 #pragma unroll
   for (int p = 0; p < P; ++p) {
-    const int j = j0 + p;
-    if (valid && j < n) {
-      const T l = fac.l(j);
-      B = fma(-l, B, v[p]);
-      A = -l * A;
+    if (valid && j0 + p < n) {
+      B = fma(-fl[p], B, v[p]);
+      A = -fl[p] * A;
     }
   }
-  scan_affine(A, B, sA, sB, r, c, RW, TW);
-  if (c == TW - 1) {
-    segA[r] = sA[c * RW + r];
-    segB[r] = sB[c * RW + r];
-  }
+  T Ae, Be, At, Bt;
+  chunk_scan(A, B, false, sWA, sWB, Ae, Be, At, Bt);
   T yin = T(0);
   if (CS > 1) {
+    if (c == 0) {
+      segA[r] = At;
+      segB[r] = Bt;
+    }
     cl.sync();
     for (int q = 0; q < crank; ++q) {
       const T* ra = cl.map_shared_rank(segA, q);
       const T* rb = cl.map_shared_rank(segB, q);
       yin = fma(ra[r], yin, rb[r]);
     }
+    cl.sync();
   }
-  T prev = (c > 0) ? fma(sA[(c - 1) * RW + r], yin, sB[(c - 1) * RW + r]) : yin;
-  __syncthreads();
+  T prev = fma(Ae, yin, Be);
 #pragma unroll
   for (int p = 0; p < P; ++p) {
-    const int j = j0 + p;
-    if (valid && j < n) {
-      prev = fma(-fac.l(j), prev, v[p]);
+    if (valid && j0 + p < n) {
+      prev = fma(-fl[p], prev, v[p]);
       v[p] = prev;
     }
   }
@@ -439,21 +500,18 @@ __device__ void solve_lines(int n, bool valid, Rhs rhs, Fac fac, T vf, T inv, Ou
   B = T(0);
 #pragma unroll
   for (int p = P - 1; p >= 0; --p) {
-    const int j = j0 + p;
-    if (valid && j < n) {
-      const T cu = fac.cu(j);
-      B = fma(-cu, B, fac.ui(j) * v[p]);
-      A = -cu * A;
+    if (valid && j0 + p < n) {
+      B = fma(-fc[p], B, fu[p] * v[p]);
+      A = -fc[p] * A;
     }
   }
-  const int pos = TW - 1 - c;
-  scan_affine(A, B, sA, sB, r, pos, RW, TW);
-  if (pos == TW - 1) {
-    segA[r] = sA[pos * RW + r];
-    segB[r] = sB[pos * RW + r];
-  }
+  chunk_scan(A, B, true, sWA, sWB, Ae, Be, At, Bt);
   T xin = T(0);
   if (CS > 1) {
+    if (c == 0) {
+      segA[r] = At;
+      segB[r] = Bt;
+    }
     cl.sync();
     for (int q = CS - 1; q > crank; --q) {
       const T* ra = cl.map_shared_rank(segA, q);
@@ -461,12 +519,11 @@ __device__ void solve_lines(int n, bool valid, Rhs rhs, Fac fac, T vf, T inv, Ou
       xin = fma(ra[r], xin, rb[r]);
     }
   }
-  T next = (pos > 0) ? fma(sA[(pos - 1) * RW + r], xin, sB[(pos - 1) * RW + r]) : xin;
+  T next = fma(Ae, xin, Be);
 #pragma unroll
   for (int p = P - 1; p >= 0; --p) {
-    const int j = j0 + p;
-    if (valid && j < n) {
-      next = fma(-fac.cu(j), next, fac.ui(j) * v[p]);
+    if (valid && j0 + p < n) {
+      next = fma(-fc[p], next, fu[p] * v[p]);
       v[p] = next;
     }
   }
@@ -531,13 +588,13 @@ __device__ void relax_origin(const RingArgs<T>& a, T beta) {
   }
 }
 
+// One zebra half-sweep over the lines [kbase, kbase + RW) of the parity (all threads of
+// the CTA call it together).
 template <typename T, int P>
-__global__ void __launch_bounds__(512) k_ring(RingArgs<T> a) {
-  if (a.done && *a.done) return;
-  const T beta = (T)a.par[1];
+__device__ void ring_body(const RingArgs<T>& a, T beta, int kbase) {
   const Shape& sh = a.L.sh;
   const int nl = a.parity ? sh.no : sh.ne;
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  const int k = kbase + threadIdx.x;
   const bool valid = k < nl;
   const int i = a.parity ? 2 * k + 1 : 2 * k + 2;
   const int ringslot = a.parity ? k : sh.no + k;
@@ -551,6 +608,13 @@ __global__ void __launch_bounds__(512) k_ring(RingArgs<T> a) {
   const RingRhs<T> rhs = make_ring_rhs(a, beta, valid ? i : 1);
   T* x = a.x;
   solve_lines<T, P>(sh.n, valid, rhs, fac, vf, inv, [&](int j, T v) { x[own.at(j)] = v; });
+}
+
+template <typename T, int P>
+__global__ void __launch_bounds__(512) k_ring(RingArgs<T> a) {
+  if (a.done && *a.done) return;
+  const T beta = (T)a.par[1];
+  ring_body<T, P>(a, beta, blockIdx.x * blockDim.x);
   // the origin is relaxed with the even rings; ring 1 (odd) is not written here
   if (a.parity == 0 && blockIdx.x == 0 && blockIdx.y == 0) relax_origin(a, beta);
 }
@@ -577,15 +641,15 @@ __device__ __forceinline__ T odd_resid(const LevelView<T>& L, const T* x, T beta
   return -beta * fma(L.w[p], xw, L.e[p] * xe);
 }
 
+// threads [tid0, tid0 + nthreads) of the grid-stride loop; `origin` also forms B_0
+// (one CTA, every thread of it)
 template <typename T>
-__global__ void __launch_bounds__(256) k_restrict(RestrictArgs<T> a) {
-  if (a.done && *a.done) return;
-  const T beta = (T)a.par[1];
+__device__ void restrict_body(const RestrictArgs<T>& a, T beta, size_t tid0, size_t nthreads,
+                              bool origin) {
   const Shape& sh = a.L.sh;
   const int mc = a.C.sh.m, n = sh.n;
   const size_t total = (size_t)mc * n;
-  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total;
-       t += (size_t)gridDim.x * blockDim.x) {
+  for (size_t t = tid0; t < total; t += nthreads) {
     const int j = (int)(t / mc);
     const int I = (int)(t - (size_t)j * mc) + 1;
     const int qlo = 2 * I - 1, qhi = 2 * I + 1;
@@ -593,34 +657,42 @@ __global__ void __launch_bounds__(256) k_restrict(RestrictArgs<T> a) {
     if (qhi <= sh.m) v = fma(a.L.ia[sh.at(qhi, j)], odd_resid(a.L, a.x, beta, qhi, j), v);
     a.B[a.C.sh.at(I, j)] = v;
   }
-  if (blockIdx.x == 0) {
+  if (origin) {
     __shared__ double red[32];
+    const int tid = threadIdx.x + blockDim.x * threadIdx.y;
+    const int nt = blockDim.x * blockDim.y;
     double s = 0.0;
-    for (int j = threadIdx.x; j < n; j += blockDim.x)
+    for (int j = tid; j < n; j += nt)
       s = fma((double)a.L.ia[sh.at(1, j)], (double)odd_resid(a.L, a.x, beta, 1, j), s);
     for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    if ((tid & 31) == 0) red[tid >> 5] = s;
     __syncthreads();
-    if (threadIdx.x == 0) {
+    if (tid == 0) {
       double tot = 0.0;
-      for (int w = 0; w < (int)(blockDim.x + 31) / 32; ++w) tot += red[w];
+      for (int w = 0; w < (nt + 31) / 32; ++w) tot += red[w];
       a.B[0] = (T)tot;
     }
   }
 }
 
+template <typename T>
+__global__ void __launch_bounds__(256) k_restrict(RestrictArgs<T> a) {
+  if (a.done && *a.done) return;
+  const T beta = (T)a.par[1];
+  restrict_body(a, beta, blockIdx.x * (size_t)blockDim.x + threadIdx.x,
+                (size_t)gridDim.x * blockDim.x, blockIdx.x == 0);
+}
+
 // coarsest level (origin + ring 1): y = T_1^{-1} b_1, x_0 = (b_0 - beta o.y) / denom,
-// x_1 = y - z x_0 with z = T_1^{-1} (beta w_1) from the refresh.
+// x_1 = y - z x_0 with z = T_1^{-1} (beta w_1) from the refresh.  One CTA (any RW: only
+// line 0 is solved).
 template <typename T, int P>
-__global__ void __launch_bounds__(512) k_coarsest(LevelView<T> L, const T* b, T* x, Params par,
-                                                   const int* done) {
-  if (done && *done) return;
-  const T beta = (T)par[1];
+__device__ void coarsest_body(const LevelView<T>& L, const T* b, T* x, T beta) {
   const Shape& sh = L.sh;
   const Line own = line_of(sh, 1);
   RingFac<T> fac{L.fl, L.fui, L.fcu, L.fq, own};
   solve_lines<T, P>(
-      sh.n, true, [&](int j) { return b[own.at(j)]; }, fac, L.fring[0], L.fring[1],
+      sh.n, threadIdx.x == 0, [&](int j) { return b[own.at(j)]; }, fac, L.fring[0], L.fring[1],
       [&](int j, T v) { x[own.at(j)] = v; });
   __syncthreads();
   __shared__ double red[32];
@@ -628,7 +700,7 @@ __global__ void __launch_bounds__(512) k_coarsest(LevelView<T> L, const T* b, T*
   const int tid = threadIdx.x + blockDim.x * threadIdx.y;
   const int nt = blockDim.x * blockDim.y;
   double s = 0.0;
-  for (int j = tid; j < sh.n; j += nt) s = fma((double)L.o[j], (double)x[sh.at(1, j)], s);
+  for (int j = tid; j < sh.n; j += nt) s = fma((double)L.o[j], (double)x[own.at(j)], s);
   for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
   if ((tid & 31) == 0) red[tid >> 5] = s;
   __syncthreads();
@@ -642,51 +714,196 @@ __global__ void __launch_bounds__(512) k_coarsest(LevelView<T> L, const T* b, T*
   __syncthreads();
   const T x0 = x0s;
   for (int j = tid; j < sh.n; j += nt) {
-    const size_t p = sh.at(1, j);
+    const size_t p = own.at(j);
     x[p] = fma(-L.fz[j], x0, x[p]);
+  }
+}
+
+template <typename T, int P>
+__global__ void __launch_bounds__(512) k_coarsest(LevelView<T> L, const T* b, T* x, Params par,
+                                                   const int* done) {
+  if (done && *done) return;
+  coarsest_body<T, P>(L, b, x, (T)par[1]);
+}
+
+// Schur data of the coarsest level (after k_refresh): z = T_1^{-1} (beta w_1) by a ring
+// solve, and the origin row's denominator diag0 - beta sum_j o_j z_j.
+template <typename T, int P>
+__global__ void __launch_bounds__(512) k_schur(LevelView<T> L, const StepParams* sp) {
+  if (!sp->do_refresh) return;
+  const T beta = (T)sp->beta;
+  const Shape& sh = L.sh;
+  const Line own = line_of(sh, 1);
+  RingFac<T> fac{L.fl, L.fui, L.fcu, L.fq, own};
+  T* fz = L.fz;
+  const T* w = L.w;
+  solve_lines<T, P>(
+      sh.n, threadIdx.x == 0, [&](int j) { return beta * w[own.at(j)]; }, fac, L.fring[0],
+      L.fring[1], [&](int j, T v) { fz[j] = v; });
+  __syncthreads();
+  __shared__ double red[32];
+  const int tid = threadIdx.x + blockDim.x * threadIdx.y;
+  const int nt = blockDim.x * blockDim.y;
+  double s = 0.0;
+  for (int j = tid; j < sh.n; j += nt) s = fma((double)L.o[j], (double)fz[j], s);
+  for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
+  if ((tid & 31) == 0) red[tid >> 5] = s;
+  __syncthreads();
+  if (tid == 0) {
+    double tot = 0.0;
+    for (int k = 0; k < (nt + 31) / 32; ++k) tot += red[k];
+    L.sc[1] = L.sc[0] - sp->beta * tot;
+  }
+}
+
+// The levels below a size bound, V-cycle and all, in one CTA: every phase of those levels
+// (zebra half-sweeps, restriction, coarsest solve, correction sweeps) runs between
+// __syncthreads() barriers instead of separate launches.  Level vectors stay in L2.
+template <typename T>
+struct CoarseCycleArgs {
+  LevelView<T> L[kMaxLevels];
+  T* b[kMaxLevels];  // b[0] is only read (it may be the caller's vector)
+  T* x[kMaxLevels];
+  int nlev;
+  Params par;
+  const int* done;
+};
+
+template <typename T, int P>
+__global__ void __launch_bounds__(512) k_coarse_cycle(CoarseCycleArgs<T> a) {
+  if (a.done && *a.done) return;
+  const T beta = (T)a.par[1];
+  const int RW = blockDim.x;
+  auto sweep = [&](int l, int parity, int mode) {
+    RingArgs<T> r{};
+    r.L = a.L[l];
+    r.C = a.L[l + 1];
+    r.b = a.b[l];
+    r.x = a.x[l];
+    r.X = (mode == RING_POST) ? a.x[l + 1] : nullptr;
+    r.par = a.par;
+    r.parity = parity;
+    r.mode = mode;
+    const int nl = parity ? r.L.sh.no : r.L.sh.ne;
+    for (int kb = 0; kb < nl; kb += RW) {
+      ring_body<T, P>(r, beta, kb);
+      __syncthreads();
+    }
+    if (parity == 0) {
+      relax_origin(r, beta);
+      __syncthreads();
+    }
+  };
+  for (int l = 0; l + 1 < a.nlev; ++l) {
+    sweep(l, 1, RING_PRE);
+    sweep(l, 0, RING_PRE);
+    RestrictArgs<T> ra{a.L[l], a.L[l + 1], a.x[l], a.b[l + 1], a.par, nullptr};
+    restrict_body(ra, beta, threadIdx.x + (size_t)RW * threadIdx.y, (size_t)RW * blockDim.y, true);
+    __syncthreads();
+  }
+  coarsest_body<T, P>(a.L[a.nlev - 1], a.b[a.nlev - 1], a.x[a.nlev - 1], beta);
+  __syncthreads();
+  for (int l = a.nlev - 2; l >= 0; --l) {
+    sweep(l, 0, RING_POST);
+    sweep(l, 1, RING_POST);
   }
 }
 
 // ---------------------------------------------------------------------------------
 // launch configuration of the ring solves
 
-struct RingShape {
-  int RW, TW, P;
-};
 constexpr int kRingThreads = 512;
+constexpr int kMaxCluster = 16;
 
 // RW lines per CTA (a full 32-byte sector of each line per row of angles), TW chunks
-// of P angles, at most kRingThreads threads: one CTA covers rings of up to
-// 512 / RW * 32 angles (4096 in FP64, 2048 in FP32 with RW = 8).
+// of P angles, at most kRingThreads threads.  A CTA covers 512 / RW * P angles; longer
+// rings are split over a cluster of CS CTAs (up to 16: 16384 angles in FP64 with
+// P = 16, in FP32 with P = 32).
 template <typename T>
 static RingShape ring_shape(int nlines, int n) {
   RingShape s;
   s.RW = (sizeof(T) == 8) ? 4 : 8;
   while (s.RW > 1 && s.RW > nlines) s.RW >>= 1;
   const int maxTW = kRingThreads / s.RW;
+  const int maxP = (sizeof(T) == 8) ? 16 : 32;
   s.P = 8;
-  while (s.P < 32 && (n + s.P - 1) / s.P > maxTW) s.P <<= 1;
-  int chunks = (n + s.P - 1) / s.P;
+  while (s.P < maxP && (n + s.P - 1) / s.P > maxTW) s.P <<= 1;
+  const int chunks = (n + s.P - 1) / s.P;
   s.TW = 1;
   while (s.TW < chunks) s.TW <<= 1;
   if (s.TW > maxTW) s.TW = maxTW;
+  while (s.RW * s.TW < 32) s.TW <<= 1;  // whole warps (the scans shuffle across lanes)
+  s.CS = (n + s.TW * s.P - 1) / (s.TW * s.P);
   return s;
 }
 
 template <typename T>
 static size_t ring_smem(const RingShape& s) {
-  return sizeof(T) * (2 * (size_t)s.RW * s.TW + 4 * (size_t)s.RW);
+  const size_t warps = ((size_t)s.RW * s.TW + 31) / 32;
+  return sizeof(T) * (2 * warps * s.RW + 4 * (size_t)s.RW);
 }
 
 template <typename T, int P>
-static void launch_ring_p(const RingArgs<T>& a, const RingShape& s, int nl, cudaStream_t st) {
+static int launch_ring_p(const RingArgs<T>& a, const RingShape& s, int nl, cudaStream_t st) {
   const int grid = (nl + s.RW - 1) / s.RW;
-  k_ring<T, P><<<grid, dim3(s.RW, s.TW), ring_smem<T>(s), st>>>(a);
+  if (s.CS == 1) {
+    k_ring<T, P><<<grid, dim3(s.RW, s.TW), ring_smem<T>(s), st>>>(a);
+    return 1;
+  }
+  // a ring spread over the CS CTAs of a cluster (grid.y), which exchange segment maps
+  // and end values through distributed shared memory
+  if (s.CS > kMaxCluster) return -1;
+  static bool allowed = false;
+  if (!allowed && s.CS > 8) {
+    cudaFuncSetAttribute(k_ring<T, P>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    allowed = true;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid, s.CS, 1);
+  cfg.blockDim = dim3(s.RW, s.TW, 1);
+  cfg.dynamicSmemBytes = ring_smem<T>(s);
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = 1;
+  attr[0].val.clusterDim.y = s.CS;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_ring<T, P>, a) == cudaSuccess ? 1 : -1;
+}
+
+// Candidate tile shapes of the ring solve for the autotuner: RW lines per CTA, P angles
+// per thread, CS CTAs per cluster (TW follows), within the register and cluster limits.
+template <typename T>
+void ring_candidates(int nlines, int n, std::vector<RingShape>& out) {
+  out.clear();
+  const int maxP = (sizeof(T) == 8) ? 16 : 32;
+  for (int RW = 1; RW <= 8; RW <<= 1) {
+    if (RW > 1 && RW / 2 >= nlines) break;
+    for (int P = 4; P <= maxP; P <<= 1) {
+      for (int CS = 1; CS <= kMaxCluster; CS <<= 1) {
+        RingShape s{RW, 1, P, CS};
+        const int chunks = (n + P * CS - 1) / (P * CS);
+        while (s.TW < chunks) s.TW <<= 1;
+        while (s.RW * s.TW < 32) s.TW <<= 1;
+        if (s.RW * s.TW > kRingThreads) continue;
+        if ((CS - 1) * s.TW * P >= n) continue;  // every CTA of the cluster holds angles
+        out.push_back(s);
+      }
+    }
+  }
+}
+
+template <typename T>
+RingShape ring_default(int nlines, int n) {
+  return ring_shape<T>(nlines, n);
 }
 
 template <typename T>
 int launch_ring(const LevelView<T>& L, const LevelView<T>& C, const T* b, T* x, const T* X,
-                Params p, int parity, int mode, const int* done, cudaStream_t st) {
+                Params p, int parity, int mode, const int* done, cudaStream_t st,
+                const RingShape* shape) {
   RingArgs<T> a{};
   a.L = L;
   a.C = C;
@@ -699,13 +916,13 @@ int launch_ring(const LevelView<T>& L, const LevelView<T>& C, const T* b, T* x, 
   a.mode = mode;
   const int nl = parity ? L.sh.no : L.sh.ne;
   if (nl == 0) return 0;
-  const RingShape s = ring_shape<T>(nl, L.sh.n);
+  const RingShape s = shape ? *shape : ring_shape<T>(nl, L.sh.n);
   switch (s.P) {
-    case 8: launch_ring_p<T, 8>(a, s, nl, st); break;
-    case 16: launch_ring_p<T, 16>(a, s, nl, st); break;
-    default: launch_ring_p<T, 32>(a, s, nl, st); break;
+    case 4: return launch_ring_p<T, 4>(a, s, nl, st);
+    case 8: return launch_ring_p<T, 8>(a, s, nl, st);
+    case 16: return launch_ring_p<T, 16>(a, s, nl, st);
+    default: return launch_ring_p<T, 32>(a, s, nl, st);
   }
-  return 1;
 }
 
 template <typename T>
@@ -735,18 +952,80 @@ int launch_coarsest(const LevelView<T>& L, const T* b, T* x, Params p, const int
   return 1;
 }
 
+// Levels l0..nlev-1 of L (bl/xl indexed by level; level l0 uses b0/x0) in one CTA.
+// Returns 0 (nothing launched) when the levels are too large for one CTA.
+template <typename T>
+int launch_coarse_cycle(const LevelView<T>* L, int l0, int nlev, const T* b0, T* x0,
+                        T* const* bl, T* const* xl, Params p, const int* done, cudaStream_t st) {
+  CoarseCycleArgs<T> a{};
+  a.nlev = nlev - l0;
+  if (a.nlev < 1 || a.nlev > kMaxLevels) return 0;
+  for (int l = l0; l < nlev; ++l) {
+    a.L[l - l0] = L[l];
+    a.b[l - l0] = (l == l0) ? const_cast<T*>(b0) : bl[l];
+    a.x[l - l0] = (l == l0) ? x0 : xl[l];
+  }
+  a.par = p;
+  a.done = done;
+  const int n = L[l0].sh.n;
+  RingShape s;
+  s.RW = (sizeof(T) == 8) ? 4 : 8;
+  const int maxTW = 512 / s.RW;
+  s.P = 8;
+  if ((n + s.P - 1) / s.P > maxTW) s.P = 16;
+  if ((n + s.P - 1) / s.P > maxTW) return 0;
+  s.TW = 32;
+  while (s.TW < (n + s.P - 1) / s.P) s.TW <<= 1;
+  const size_t smem = ring_smem<T>(s);
+  if (s.P == 8) {
+    k_coarse_cycle<T, 8><<<1, dim3(s.RW, s.TW), smem, st>>>(a);
+  } else {
+    k_coarse_cycle<T, 16><<<1, dim3(s.RW, s.TW), smem, st>>>(a);
+  }
+  return 1;
+}
+
+// largest number of lines of one parity that the one-CTA coarse cycle takes per level
+template <typename T>
+int coarse_cycle_lines() {
+  return 2 * ((sizeof(T) == 8) ? 4 : 8);
+}
+
+template <typename T>
+static int launch_schur(const LevelView<T>& L, const StepParams* sp, cudaStream_t st) {
+  RingShape s;
+  s.RW = 1;
+  s.P = 8;
+  while (s.P < 32 && (L.sh.n + s.P - 1) / s.P > kRingThreads) s.P <<= 1;
+  s.TW = 32;
+  while (s.TW < (L.sh.n + s.P - 1) / s.P) s.TW <<= 1;
+  const size_t smem = ring_smem<T>(s);
+  switch (s.P) {
+    case 8: k_schur<T, 8><<<1, dim3(1, s.TW), smem, st>>>(L, sp); break;
+    case 16: k_schur<T, 16><<<1, dim3(1, s.TW), smem, st>>>(L, sp); break;
+    default: k_schur<T, 32><<<1, dim3(1, s.TW), smem, st>>>(L, sp); break;
+  }
+  return 1;
+}
+
 // The ring kernels use dynamic shared memory only for the scan buffers
 // (2 RW TW + 4 RW words): at most 16.1 KB, below the default 48 KB limit.
 
 #define POLAR_MG_INST(T)                                                                      \
-  template int launch_refresh<T>(const LevelView<double>*, LevelView<T>*, int, Params,         \
-                                 double*, cudaStream_t);                                      \
+  template int launch_refresh<T>(const LevelView<double>*, LevelView<T>*, int,                \
+                                 const StepParams*, double*, cudaStream_t);                   \
   template int launch_ring<T>(const LevelView<T>&, const LevelView<T>&, const T*, T*,          \
-                              const T*, Params, int, int, const int*, cudaStream_t);          \
+                              const T*, Params, int, int, const int*, cudaStream_t,           \
+                              const RingShape*);                                              \
+  template void ring_candidates<T>(int, int, std::vector<RingShape>&);                        \
+  template RingShape ring_default<T>(int, int);                                               \
   template int launch_restrict<T>(const LevelView<T>&, const LevelView<T>&, const T*, T*,      \
                                   Params, const int*, cudaStream_t);                          \
   template int launch_coarsest<T>(const LevelView<T>&, const T*, T*, Params, const int*,       \
-                                  cudaStream_t);
+                                  cudaStream_t);                                              \
+  template int launch_coarse_cycle<T>(const LevelView<T>*, int, int, const T*, T*, T* const*,  \
+                                      T* const*, Params, const int*, cudaStream_t);           \
+  template int coarse_cycle_lines<T>();
 
 POLAR_MG_INST(float)
 POLAR_MG_INST(double)

@@ -44,3 +44,14 @@ def advance(ctx, problem, k0=0, k1=None, opts=None):
     w = problem.weight_table()[k0:k1 + 1]
     stats, _ = P.polar_advance(ctx, t[k0:k1 + 1], problem.theta_w, w, opts)
     return stats
+
+
+def batch_advance(batch, problems, k0=0, k1=None, opts=None, check=True):
+    """Advances every instance of a polar_batch over time levels t[k0..k1] of its problem."""
+    ts, ws = [], []
+    for p in problems:
+        t = np.asarray(p.t, dtype=np.float64)
+        kk = len(t) - 1 if k1 is None else k1
+        ts.append(t[k0:kk + 1])
+        ws.append(p.weight_table()[k0:kk + 1])
+    return P.polar_batch_advance(batch, ts, [p.theta_w for p in problems], ws, opts, check)

@@ -1,0 +1,59 @@
+"""Batched instances (parameter sweep of uneven meshes) advanced by one CUDA graph per
+step: every instance matches the same instance advanced alone (bit for bit: same kernels
+in the same order) and the FP64 CPU oracle."""
+import numpy as np
+import pytest
+
+import polar_inputs as pi
+from oracle import polar_oracle as po
+
+pytestmark = pytest.mark.gpu
+
+P = pytest.importorskip("paper_2509_15879_gb300")
+from paper_2509_15879_gb300 import driver  # noqa: E402
+
+
+def _instances():
+    # uneven sizes, D amplitudes and Peclet numbers (the shape of the 256-instance sweep)
+    return [pi.config4_instance(i, K=6, scale=0.06) for i in range(5)]
+
+
+@pytest.mark.parametrize("precision", [P.POLAR_FP64, P.POLAR_MIXED])
+def test_batch_matches_single_and_oracle(precision):
+    probs = _instances()
+    K = 4
+    ctxs = [driver.create(p, precision) for p in probs]
+    batch = P.polar_batch_create(ctxs)
+    stats, rc = driver.batch_advance(batch, probs, 0, K)
+    assert rc == 0
+    assert all(s["status"] == 0 for row in stats for s in row)
+    tol = 1e-12 if precision == P.POLAR_FP64 else 1e-9
+    for p, c, row in zip(probs, ctxs, stats):
+        U, t = P.polar_get_state(c)
+        assert t == p.t[K]
+        alone = driver.create(p, precision)
+        st_alone = driver.advance(alone, p, 0, K)
+        Ua, _ = P.polar_get_state(alone)
+        assert np.array_equal(U, Ua)
+        assert [s["iters"] for s in row] == [s["iters"] for s in st_alone]
+        ref = po.run(p, K)
+        assert np.max(np.abs(U - ref)) / np.max(np.abs(ref)) < tol
+
+
+def test_batch_failure_is_per_instance():
+    probs = _instances()[:3]
+    ctxs = [driver.create(p, P.POLAR_FP64) for p in probs]
+    batch = P.polar_batch_create(ctxs)
+    stats, rc = driver.batch_advance(batch, probs, 0, 2, check=False)
+    assert rc == 0
+    # no instance can meet an impossible tolerance in one sweep: each stops at its first
+    # step, keeps its state, and the rest of its schedule is reported as not run
+    bad = P.polar_batch_advance(batch, [p.t[2:5] for p in probs], [p.theta_w for p in probs],
+                                [p.weight_table()[2:5] for p in probs],
+                                dict(tol=1e-18, max_refine=1), check=False)
+    stats, rc = bad
+    assert rc == P.POLAR_ENOCONV
+    for c, p, row in zip(ctxs, probs, stats):
+        assert row[0]["status"] == P.POLAR_ENOCONV
+        assert row[1]["status"] == P.POLAR_ESTATE
+        assert P.polar_get_state(c)[1] == p.t[2]

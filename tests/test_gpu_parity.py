@@ -52,6 +52,14 @@ def test_operator_matches_assembled_matrix(name, make):
         assert np.all(np.abs(y - ref) <= 1e-13 * scale), name
 
 
+def _kappa(prob, k):
+    """||(D^-1 A)^-1||_inf of step k's matrix (an M-matrix: the row sums of A^-1 D)."""
+    import scipy.sparse.linalg as spla
+    L, _ = po.operator(prob)
+    A = po.system_matrix(L, prob.t[k + 1] - prob.t[k], prob.theta_w).tocsc()
+    return float(np.max(np.abs(spla.splu(A).solve(A.diagonal()))))
+
+
 def _oracle_levels(prob, K):
     out = []
     po.run(prob, K, callback=lambda k, U: out.append(U.copy()))
@@ -87,3 +95,67 @@ def test_steps_match_oracle(name, make, K, precision, tol):
         driver.advance(ctx, prob, k, k + 1)
         U, _ = P.polar_get_state(ctx)
         assert _rel(U, refs[k]) < tol, (name, k, _rel(U, refs[k]))
+
+
+def test_graph_step_equals_eager_step():
+    """A step run as one CUDA graph (device-side refinement and Krylov loops) and the same
+    step driven from the host (kernel timing on) execute the same kernels in the same order."""
+    prob = _small_continuity(37, 61, K=6)
+    out = []
+    for eager in (False, True):
+        ctx = driver.create(prob, P.POLAR_FP64)
+        if eager:
+            P.polar_timing_enable(ctx, True)
+        stats = driver.advance(ctx, prob, 0, 6)
+        out.append((P.polar_get_state(ctx)[0], stats))
+    assert np.array_equal(out[0][0], out[1][0])
+    assert [s["iters"] for s in out[0][1]] == [s["iters"] for s in out[1][1]]
+
+
+@pytest.mark.parametrize("timing", [False, True])
+def test_failed_step_leaves_state(timing):
+    """POLAR_ENOCONV (one refinement sweep cannot reach 1e-18) keeps U and t."""
+    prob = _small_continuity(20, 32, K=3)
+    ctx = driver.create(prob, P.POLAR_MIXED)
+    if timing:
+        P.polar_timing_enable(ctx, True)
+    U0, t0 = P.polar_get_state(ctx)
+    stats, rc = P.polar_advance(ctx, prob.t[:3], prob.theta_w, prob.weight_table()[:3],
+                                dict(tol=1e-18, max_refine=1), check=False)
+    assert rc == P.POLAR_ENOCONV
+    assert stats[0]["status"] == P.POLAR_ENOCONV and stats[1]["status"] == P.POLAR_ESTATE
+    U1, t1 = P.polar_get_state(ctx)
+    assert t1 == t0 and np.array_equal(U0, U1)
+    # the context stays usable
+    stats, rc = P.polar_advance(ctx, prob.t[:3], prob.theta_w, prob.weight_table()[:3])
+    assert rc == 0
+
+
+def test_nonfinite_state_rejected():
+    prob = _small_continuity(8, 16, K=2)
+    ctx = driver.create(prob, P.POLAR_FP64)
+    bad = np.array(prob.u0, dtype=np.float64)
+    bad[5] = np.nan
+    with pytest.raises(P.PolarError) as e:
+        P.polar_set_state(ctx, bad, 0.0)
+    assert e.value.code == P.POLAR_ENONFINITE
+
+
+@pytest.mark.parametrize("precision,m,n", [(0, 6, 16384), (1, 20, 16384), (0, 40, 3000),
+                                           (1, 40, 3000)])
+def test_long_rings(precision, m, n):
+    """Rings longer than one CTA covers are split over a thread-block cluster.  The first
+    steps of a 2000-level time stretch (dt ~ 1e-5, as in the large continuity workloads).
+    On these meshes the small first ring makes the step ill-conditioned: two independent
+    FP64 solves can only agree to about kappa eps, kappa = ||(D^-1 A)^-1||_inf (computed
+    here from the oracle's factorisation), so the bar is max(stated, 20 kappa eps)."""
+    prob = pi.continuity_problem(m, n, 2000, 77, pe_target=4.0, d_amp=1.0, delta=0.2)
+    K = 2
+    refs = _oracle_levels(prob, K)
+    ctx = driver.create(prob, precision)
+    kappa = _kappa(prob, 0)
+    tol = max(1e-12 if precision == 0 else 1e-9, 20 * kappa * np.finfo(float).eps)
+    for k in range(K):
+        driver.advance(ctx, prob, k, k + 1)
+        U, _ = P.polar_get_state(ctx)
+        assert _rel(U, refs[k]) < tol, (m, n, k, _rel(U, refs[k]))
