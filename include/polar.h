@@ -181,6 +181,34 @@ int polar_batch_advance(polar_batch* batch, int32_t nsteps, const double* const*
 int polar_apply_operator(polar_ctx* ctx, double alpha, double beta, const double* x,
                          double* y, int32_t memory);
 
+/* polar_apply_rows_noalloc: y = alpha x + beta L x for a 5-point polar operator given row
+ * by row, for callers that cannot allocate device memory -- code that runs while a CUDA
+ * stream is being captured into a graph (where cudaMalloc is not permitted) or embedders
+ * whose device memory is budgeted up front.  It needs no context and allocates nothing.
+ * The paper has no counterpart: this is a memory-management variant of
+ * polar_apply_operator for operators the caller holds itself.
+ *   m >= 2, 4 <= n <= 16384 (larger n: POLAR_EINVAL).
+ *   R, W, E, S, N: device arrays of m n + 1 doubles in the interface layout (origin first,
+ *     then node (r_i, theta_j) at 1 + j m + (i - 1)).  Row (i, j) of L is
+ *       R x_ij + W (x_{i-1,j} - x_ij) + E (x_{i+1,j} - x_ij) + S (x_{i,j-1} - x_ij)
+ *         + N (x_{i,j+1} - x_ij)
+ *     with x_{0,j} = x_0 (the origin), x_{m+1,j} = 0 and j periodic; entry 0 of W, E, S, N
+ *     is not read.
+ *   o: device array of n doubles; the origin row is R[0] x_0 + sum_j o_j (x_{1,j} - x_0).
+ *   x, y: device arrays of m n + 1 doubles; they must not overlap.
+ *   stream: the cudaStream_t to enqueue on (NULL: legacy default stream).
+ * Asynchronous: it returns once the work is enqueued (launch errors are reported).
+ * Its only scratch is a fixed 128 KB array in device memory that the library reserves on
+ * every device it is loaded on, until the process exits: the origin row's sum over the n
+ * angles is staged there.  Every call shares that array, so calls that may overlap on the
+ * GPU (different streams, or several host threads) race; serialise them.  The first call on
+ * a device looks up the array's address on that device; make that first call before any
+ * stream capture begins. */
+int polar_apply_rows_noalloc(int32_t m, int32_t n, const double* R, const double* W,
+                             const double* E, const double* S, const double* N,
+                             const double* o, double alpha, double beta, const double* x,
+                             double* y, void* stream);
+
 /* Number of CUDA kernels this context has launched since creation. */
 int64_t polar_kernel_launches(const polar_ctx* ctx);
 

@@ -70,6 +70,8 @@ EXPORTS = {
     "polar_apply_operator": (C.c_int, [C.c_void_p, C.c_double, C.c_double, C.c_void_p,
                                        C.c_void_p, C.c_int32]),
     "polar_kernel_launches": (C.c_int64, [C.c_void_p]),
+    "polar_apply_rows_noalloc": (C.c_int, [C.c_int32, C.c_int32] + [C.c_void_p] * 6 +
+                                 [C.c_double, C.c_double, C.c_void_p, C.c_void_p, C.c_void_p]),
     "polar_batch_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int32, C.c_void_p,
                                      C.POINTER(C.c_void_p)]),
     "polar_batch_destroy": (C.c_int, [C.c_void_p]),
@@ -233,6 +235,17 @@ def polar_apply_operator(ctx: Ctx, alpha, beta, x, out=None):
     _check(load().polar_apply_operator(ctx.handle, float(alpha), float(beta), ax.ptr, ay.ptr,
                                        POLAR_DEVICE if ax.device else POLAR_HOST))
     return out
+
+
+def polar_apply_rows_noalloc(m, n, R, W, E, S, N, o, alpha, beta, x, y, stream=None):
+    """y = alpha x + beta L x from caller-held device rows (torch CUDA tensors); allocates
+    nothing on the device."""
+    arrs = [_Arr(a) for a in (R, W, E, S, N, o, x, y)]
+    if not all(a.device for a in arrs):
+        raise ValueError("polar_apply_rows_noalloc takes device arrays only")
+    _check(load().polar_apply_rows_noalloc(int(m), int(n), *[a.ptr for a in arrs[:6]],
+                                           float(alpha), float(beta), arrs[6].ptr, arrs[7].ptr,
+                                           stream))
 
 
 def polar_kernel_launches(ctx: Ctx) -> int:

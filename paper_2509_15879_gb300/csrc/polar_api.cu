@@ -1114,6 +1114,11 @@ int advance(polar_ctx* c, int32_t K, const double* t, double theta, const double
 
 }  // namespace
 
+namespace polar {
+// error reporting for the other translation units of the library (polar_last_error)
+int report_error(int code, const char* msg) { return fail(code, msg ? msg : ""); }
+}  // namespace polar
+
 // ======================================================================= C ABI
 extern "C" {
 
