@@ -73,8 +73,10 @@ class Geometry:
         return 1 + j * self.m + (i - 1)
 
 
-def conservative_operator(prob):
-    """Sparse L (N x N) and boundary map B (N x n) of the CONSERVATIVE scheme.
+def conservative_operator(prob, rows=None):
+    """Sparse L and boundary map B of the CONSERVATIVE scheme: N x N and N x n, or, when
+    ``rows`` (sorted distinct vector indices) is given, only those rows (len(rows) x N and
+    len(rows) x n), built from the faces of those cells alone.
 
     Radial face (i+1/2, j), i = 0..m: length w_j r_{i+1/2}, spacing h_{i+1},
       flux = w_j r_{i+1/2} [ (D/h_{i+1} + v+) U_in - (D/h_{i+1} + v-) U_out ],
@@ -85,30 +87,48 @@ def conservative_operator(prob):
     """
     g = Geometry(prob.r, prob.theta)
     m, n, N = g.m, g.n, g.N
-    rows, cols, vals = [], [], []
+    rows_, cols, vals = [], [], []
     brow, bcol, bval = [], [], []
 
     def add(rw, cl, v):
-        rows.append(np.ravel(rw)); cols.append(np.ravel(cl)); vals.append(np.ravel(v))
+        rows_.append(np.ravel(rw)); cols.append(np.ravel(cl)); vals.append(np.ravel(v))
+
+    # faces to visit: all of them, or those of the requested cells
+    if rows is None:
+        J, I = np.meshgrid(np.arange(n), np.arange(m + 1), indexing="ij")
+        Jr, Ir = J.ravel(), I.ravel()                                      # radial faces
+        J, I = np.meshgrid(np.arange(n), np.arange(1, m + 1), indexing="ij")
+        Jt, It = J.ravel(), I.ravel()                                      # angular faces
+    else:
+        rows = np.asarray(rows, dtype=np.int64)
+        cell = rows[rows > 0] - 1
+        ci, cj = cell % m + 1, cell // m                                   # ring, angle
+        fr = [np.stack([cj, ci - 1]), np.stack([cj, ci])]                  # faces i -+ 1/2
+        if rows[0] == 0:
+            fr.append(np.stack([np.arange(n), np.zeros(n, dtype=np.int64)]))
+        fr = np.unique(np.concatenate(fr, axis=1), axis=1)
+        Jr, Ir = fr[0], fr[1]
+        ft = np.unique(np.concatenate([np.stack([cj, ci]), np.stack([(cj - 1) % n, ci])],
+                                      axis=1), axis=1)                     # faces j -+ 1/2
+        Jt, It = ft[0], ft[1]
 
     # radial faces
-    J, I = np.meshgrid(np.arange(n), np.arange(m + 1), indexing="ij")     # [j, i], i = 0..m
-    D = np.asarray(prob.d_rface, dtype=np.float64).reshape(n, m + 1)
-    v = (np.zeros((n, m + 1)) if prob.v_rface is None
-         else np.asarray(prob.v_rface, dtype=np.float64).reshape(n, m + 1))
-    length = g.w[:, None] * g.rh[None, :]
-    cond = D / g.h[None, :]                                                 # h[i] = h_{i+1}
+    D = np.asarray(prob.d_rface, dtype=np.float64).reshape(n, m + 1)[Jr, Ir]
+    v = (np.zeros_like(D) if prob.v_rface is None
+         else np.asarray(prob.v_rface, dtype=np.float64).reshape(n, m + 1)[Jr, Ir])
+    length = g.w[Jr] * g.rh[Ir]
+    cond = D / g.h[Ir]                                                      # h[i] = h_{i+1}
     c_in = length * (cond + np.maximum(v, 0.0))
     c_out = length * (cond + np.maximum(-v, 0.0))
-    inner = np.where(I == 0, 0, g.idx(np.maximum(I, 1), J))
-    outer_is_bnd = I == m
-    outer = np.where(outer_is_bnd, -1, g.idx(np.minimum(I + 1, m), J))
+    inner = np.where(Ir == 0, 0, g.idx(np.maximum(Ir, 1), Jr))
+    outer_is_bnd = Ir == m
+    outer = np.where(outer_is_bnd, -1, g.idx(np.minimum(Ir + 1, m), Jr))
     V_in = g.V[inner]
     # row of the inner cell: + flux / V_in
     add(inner, inner, c_in / V_in)
     nb = ~outer_is_bnd
     add(inner[nb], outer[nb], -c_out[nb] / V_in[nb])
-    brow.append(inner[outer_is_bnd]); bcol.append(J[outer_is_bnd])
+    brow.append(inner[outer_is_bnd]); bcol.append(Jr[outer_is_bnd])
     bval.append(-c_out[outer_is_bnd] / V_in[outer_is_bnd])
     # row of the outer cell: - flux / V_out
     V_out = g.V[outer[nb]]
@@ -116,31 +136,41 @@ def conservative_operator(prob):
     add(outer[nb], outer[nb], c_out[nb] / V_out)
 
     # angular faces
-    J, I = np.meshgrid(np.arange(n), np.arange(1, m + 1), indexing="ij")  # [j, i-1]
-    D = np.asarray(prob.d_tface, dtype=np.float64).reshape(n, m)
-    wv = (np.zeros((n, m)) if prob.v_tface is None
-          else np.asarray(prob.v_tface, dtype=np.float64).reshape(n, m))
-    ri = g.r[1:m + 1][None, :]
-    mu_next = g.mu[1:n + 1][:, None]                                        # mu_{j+1}
-    length = np.broadcast_to(g.k[None, :], (n, m))
+    D = np.asarray(prob.d_tface, dtype=np.float64).reshape(n, m)[Jt, It - 1]
+    wv = (np.zeros_like(D) if prob.v_tface is None
+          else np.asarray(prob.v_tface, dtype=np.float64).reshape(n, m)[Jt, It - 1])
+    ri = g.r[It]
+    mu_next = g.mu[Jt + 1]                                                  # mu_{j+1}
+    length = g.k[It - 1]
     cond = D / (ri * mu_next)
     c_in = length * (cond + np.maximum(wv, 0.0))
     c_out = length * (cond + np.maximum(-wv, 0.0))
-    left = g.idx(I, J)
-    right = g.idx(I, (J + 1) % n)
+    left = g.idx(It, Jt)
+    right = g.idx(It, (Jt + 1) % n)
     add(left, left, c_in / g.V[left])
     add(left, right, -c_out / g.V[left])
     add(right, left, -c_in / g.V[right])
     add(right, right, c_out / g.V[right])
 
     # reaction
-    b = np.full(N, prob.b_const) if prob.b is None else np.asarray(prob.b, dtype=np.float64)
-    add(np.arange(N), np.arange(N), b)
+    diag = np.arange(N) if rows is None else rows
+    b = (np.full(len(diag), prob.b_const) if prob.b is None
+         else np.asarray(prob.b, dtype=np.float64)[diag])
+    add(diag, diag, b)
 
-    L = sp.coo_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
-                      shape=(N, N)).tocsr()
-    B = sp.coo_matrix((np.concatenate(bval), (np.concatenate(brow), np.concatenate(bcol))),
-                      shape=(N, n)).tocsr()
+    R, C, X = np.concatenate(rows_), np.concatenate(cols), np.concatenate(vals)
+    Rb, Cb, Xb = np.concatenate(brow), np.concatenate(bcol), np.concatenate(bval)
+    nrow = N
+    if rows is not None:   # keep the entries of the requested rows, renumbered 0..len-1
+        pos = np.searchsorted(rows, R).clip(0, len(rows) - 1)
+        keep = rows[pos] == R
+        R, C, X = pos[keep], C[keep], X[keep]
+        pos = np.searchsorted(rows, Rb).clip(0, len(rows) - 1)
+        keep = rows[pos] == Rb
+        Rb, Cb, Xb = pos[keep], Cb[keep], Xb[keep]
+        nrow = len(rows)
+    L = sp.coo_matrix((X, (R, C)), shape=(nrow, N)).tocsr()
+    B = sp.coo_matrix((Xb, (Rb, Cb)), shape=(nrow, n)).tocsr()
     return L, B
 
 
@@ -249,6 +279,37 @@ def step(L, B, U, dt, th, f_old, g_old, f_new, g_new, lu=None, A=None):
         lu = spla.splu(A.tocsc())
     x = lu.solve(e)
     return x + lu.solve(residual_extended(A, x, e))
+
+
+def _matvec_ext(M, x):
+    """M x with products and sums in numpy longdouble (empty rows give 0)."""
+    M = M.tocsr()
+    out = np.zeros(M.shape[0], dtype=np.longdouble)
+    if M.nnz == 0:
+        return out
+    prod = M.data.astype(np.longdouble) * x[M.indices].astype(np.longdouble)
+    full = M.indptr[1:] > M.indptr[:-1]
+    out[full] = np.add.reduceat(prod, M.indptr[:-1][full])
+    return out
+
+
+def step_residual(L, B, U_old, U_new, dt, th, f_old, g_old, f_new, g_new, rows=None):
+    """Jacobi-scaled residual (e - A U_new)_i / A_ii of the theta-step (Eq. 2.11,
+    A = I/dt + th L) for a candidate new level U_new, accumulated in extended precision.
+    With ``rows``, L and B hold only those rows (conservative_operator(prob, rows)) and
+    the residual is returned for them alone; U and f are full vectors either way."""
+    sel = np.arange(L.shape[0]) if rows is None else np.asarray(rows, dtype=np.int64)
+    ld = np.longdouble
+    inv_dt = ld(1.0) / ld(dt)
+    th = ld(th)
+    e = (U_old[sel].astype(ld) * inv_dt
+         - (1 - th) * (_matvec_ext(L, U_old) + _matvec_ext(B, g_old))
+         - th * _matvec_ext(B, g_new)
+         + (1 - th) * f_old[sel].astype(ld) + th * f_new[sel].astype(ld))
+    AU = U_new[sel].astype(ld) * inv_dt + th * _matvec_ext(L, U_new)
+    Lc = L.tocsr()
+    diag = np.asarray(Lc[np.arange(len(sel)), sel]).ravel().astype(ld)
+    return ((e - AU) / (inv_dt + th * diag)).astype(np.float64)
 
 
 def run(prob, nsteps=None, callback=None):

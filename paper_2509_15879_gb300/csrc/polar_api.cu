@@ -13,6 +13,7 @@
 #include <array>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -572,6 +573,15 @@ using TuneKey = std::tuple<int, int, int, int, int>;
 std::mutex g_tune_lock;
 std::map<TuneKey, RingShape> g_tune_cache;
 
+// POLAR_TUNE_LOG=1 in the environment prints every tuned ring launch (shape and time)
+bool tune_log() {
+  static const bool on = [] {
+    const char* v = getenv("POLAR_TUNE_LOG");
+    return v && *v && *v != '0';
+  }();
+  return on;
+}
+
 int bucket(int v) {
   int b = 1;
   while (b < v) b <<= 1;
@@ -638,6 +648,11 @@ int tune_rings(polar_ctx* c) {
           }
         }
         c->tiles[l][mode * 2 + parity] = best;
+        if (tune_log())
+          fprintf(stderr, "polar tune: %s level %d lines %d n %d %s %s -> RW %d TW %d P %d CS %d: "
+                  "%.2f us\n", sizeof(T) == 8 ? "fp64" : "fp32", l, lines, L[l].sh.n,
+                  mode ? "post" : "pre", parity ? "odd" : "even", best.RW, best.TW, best.P,
+                  best.CS, 1e3 * best_ms / 3);
         std::lock_guard<std::mutex> g(g_tune_lock);
         g_tune_cache[key] = best;
       }

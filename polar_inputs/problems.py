@@ -16,6 +16,8 @@ Sources and Dirichlet data are separable in time: f(t) = sum_q w_q(t) S_q and
 g(t) = sum_q w_q(t) G_q with the same weights w_q(t).
 """
 import math
+import os
+from concurrent.futures import ThreadPoolExecutor
 from dataclasses import dataclass, field
 from typing import Callable, List, Optional
 
@@ -258,6 +260,27 @@ class _ContinuityFields:
         return (A, Ax, Ay, lapA), (B, Bx, By, lapB)
 
 
+def _chunked(fn, *arrays, nout=1, chunk=1 << 20):
+    """fn applied to consecutive slices of the (equal-length) arrays on a thread pool
+    (numpy releases the GIL in its loops), outputs concatenated: the same values as one
+    call on the whole arrays, with temporaries bounded by the chunk size."""
+    size = len(arrays[0])
+    if size <= chunk:
+        return fn(*arrays)
+    starts = range(0, size, chunk)
+    outs = [np.empty(size) for _ in range(nout)]
+
+    def run(a):
+        res = fn(*(x[a:a + chunk] for x in arrays))
+        res = (res,) if nout == 1 else res
+        for o, v in zip(outs, res):
+            o[a:a + chunk] = v
+
+    with ThreadPoolExecutor(min(32, os.cpu_count() or 1)) as ex:
+        list(ex.map(run, starts))
+    return outs[0] if nout == 1 else tuple(outs)
+
+
 def continuity_problem(m: int, n: int, K: int, seed: int, theta_w: float = 0.5,
                        two_sided: bool = True, pe_target: float = 10.0, d_amp: float = 1.0,
                        b_const: float = 1.0, delta: float = 0.02, name: str = "continuity",
@@ -277,42 +300,52 @@ def continuity_problem(m: int, n: int, K: int, seed: int, theta_w: float = 0.5,
     # faces
     rr, rth = rface_coords(r, theta)
     tr, tth = tface_coords(r, theta)
-    xr, yr = rr * np.cos(rth), rr * np.sin(rth)
-    xt, yt = tr * np.cos(tth), tr * np.sin(tth)
-    d_r, _, _ = F.D(xr, yr)
-    d_t, _, _ = F.D(xt, yt)
 
-    def face_vel():
-        vx, vy, _ = F.vel(xr, yr)
-        vr = vx * np.cos(rth) + vy * np.sin(rth)
-        vx2, vy2, _ = F.vel(xt, yt)
-        vt = -vx2 * np.sin(tth) + vy2 * np.cos(tth)
-        return vr, vt
+    def face_d(rad, ang):
+        return F.D(rad * np.cos(ang), rad * np.sin(ang))[0]
 
-    vr, vt = face_vel()
+    def face_vr(rad, ang):       # radial component of v at radial faces
+        c, s = np.cos(ang), np.sin(ang)
+        vx, vy, _ = F.vel(rad * c, rad * s)
+        return vx * c + vy * s
+
+    def face_vt(rad, ang):       # angular component of v at angular faces
+        c, s = np.cos(ang), np.sin(ang)
+        vx, vy, _ = F.vel(rad * c, rad * s)
+        return -vx * s + vy * c
+
+    d_r = _chunked(face_d, rr, rth)
+    d_t = _chunked(face_d, tr, tth)
+    vr, vt = _chunked(face_vr, rr, rth), _chunked(face_vt, tr, tth)
     h = np.diff(r)                                        # h_{i+1} for face i+1/2, i = 0..m
     th_next = np.concatenate([theta[1:], [2.0 * math.pi]])
     mu_next = th_next - theta                             # mu_{j+1}
     pe_r = np.abs(vr) * np.tile(h, n) / d_r
     pe_t = np.abs(vt) * tr * np.repeat(mu_next, m) / d_t
     pe = max(pe_r.max(), pe_t.max())
+    del pe_r, pe_t
     if phi_scale is not None:
         F.phi_scale = phi_scale
     else:
         F.phi_scale = pe_target / pe if pe > 0 else 0.0
-    vr, vt = face_vel()
-    # sources
+    vr, vt = _chunked(face_vr, rr, rth), _chunked(face_vt, tr, tth)
+    del rr, rth, tr, tth
+
+    # sources: S1 = -A + Lc(A), S2 = Lc(B), Lc(P) = -div(D grad P) + div(v P) + b P
+    def node_fields(rad, ang):
+        x, y = rad * np.cos(ang), rad * np.sin(ang)
+        Dn, Dx, Dy = F.gradD(x, y)
+        vx, vy, divv = F.vel(x, y)
+        (A, Ax, Ay, lapA), (B, Bx, By, lapB) = F.parts(x, y)
+
+        def Lc(P, Px, Py, lapP):
+            return -(Dx * Px + Dy * Py) - Dn * lapP + P * divv + vx * Px + vy * Py + b_const * P
+
+        return -A + Lc(A, Ax, Ay, lapA), Lc(B, Bx, By, lapB), A, B
+
     R, TH = node_coords(r, theta)
-    x, y = R * np.cos(TH), R * np.sin(TH)
-    Dn, Dx, Dy = F.gradD(x, y)
-    vx, vy, divv = F.vel(x, y)
-    (A, Ax, Ay, lapA), (B, Bx, By, lapB) = F.parts(x, y)
-
-    def Lc(P, Px, Py, lapP):     # -div(D grad P) + div(v P) + b P
-        return -(Dx * Px + Dy * Py) - Dn * lapP + P * divv + vx * Px + vy * Py + b_const * P
-
-    S1 = -A + Lc(A, Ax, Ay, lapA)
-    S2 = Lc(B, Bx, By, lapB)
+    S1, S2, A, B = _chunked(node_fields, R, TH, nout=4)
+    del R, TH
     G1 = 1.0 + 0.5 * np.cos(theta)
     G2 = 1.0 + 0.5 * np.sin(theta)
     return Problem(

@@ -269,3 +269,43 @@ def test_paper_origin_row_matches_control_volume_balance():
     n0, n1 = U[0], U[1:].reshape(n, m)[:, 0].mean()
     balance = 4 * 1.4 * (n1 - n0) / h1 ** 2 - (2 * E[0] / h1) * (n0 + n1) / 2
     assert abs((L @ U)[0] - (-balance + 0.3 * n0)) < 1e-12 * abs(balance)
+
+
+# ------------------------------------------------------------------------------ sampled rows
+def test_sampled_rows_equal_full_assembly():
+    """conservative_operator restricted to a set of rows (origin, first and last rings,
+    random cells) returns exactly those rows of the full assembly."""
+    for p in (_drift_problem(m=17, n=23), pi.config2(m=21, n=30, K=2)):
+        L, B = po.conservative_operator(p)
+        rng = np.random.default_rng(5)
+        for rows in (np.unique(np.concatenate([[0, 1, 2, p.m, p.N - 1],
+                                               rng.integers(0, p.N, 40)])),
+                     np.unique(rng.integers(1, p.N, 25))):
+            Ls, Bs = po.conservative_operator(p, rows)
+            assert (Ls != L[rows]).nnz == 0 and (Bs != B[rows]).nnz == 0
+
+
+def test_step_residual_detects_a_perturbation():
+    """The oracle's own step has a Jacobi-scaled residual at rounding level; moving one
+    value by d shows up as -d in that row and as the coupling ratio in its neighbours."""
+    p = _drift_problem(m=12, n=18, K=2)
+    L, B = po.conservative_operator(p)
+    dt, th = p.t[1] - p.t[0], p.theta_w
+    fo, go = po.source(p, p.t[0])
+    fn, gn = po.source(p, p.t[1])
+    U1 = po.step(L, B, p.u0, dt, th, fo, go, fn, gn)
+    res = po.step_residual(L, B, p.u0, U1, dt, th, fo, go, fn, gn)
+    assert np.max(np.abs(res)) < 1e-15 * np.max(np.abs(U1))
+    q, d = 1 + 5 * p.m + 7, 1e-6
+    U2 = U1.copy()
+    U2[q] += d
+    res2 = po.step_residual(L, B, p.u0, U2, dt, th, fo, go, fn, gn)
+    assert abs(res2[q] + d) < 1e-12
+    A = po.system_matrix(L, dt, th).tocsr()
+    col = A[:, q].toarray().ravel()
+    expect = -col * d / A.diagonal()
+    assert np.allclose(res2, expect, atol=1e-15)
+    rows = np.array([0, q - 1, q, q + 1, p.N - 1])
+    Ls, Bs = po.conservative_operator(p, rows)
+    assert np.allclose(po.step_residual(Ls, Bs, p.u0, U2, dt, th, fo, go, fn, gn, rows),
+                       res2[rows], rtol=0, atol=1e-18)
