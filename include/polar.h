@@ -120,9 +120,12 @@ int polar_get_state(polar_ctx* ctx, double* u, double* t, int32_t memory);
 /* Solver controls (NULL -> defaults).
  *   tol         stop when max_i |r_i| / A_ii <= tol * max_i |U_i|, r = e - A U
  *               (Jacobi-scaled residual of the implicit system); default 1e-14
- *   max_iter    Krylov iterations per solve (FP64) or per inner solve (MIXED); default 4000
- *   max_refine  outer refinement sweeps of the MIXED path; default 12
- *   inner_tol   relative residual reduction of each FP32 inner solve; default 1e-5 */
+ *   max_iter    Krylov iterations per solve (FP64) or per inner solve (MIXED); default 500
+ *   max_refine  outer refinement sweeps (FP64 residual evaluations); default 12
+ *   inner_tol   reduction of the Jacobi-scaled max norm max_i |r_i| / A_ii that each FP32
+ *               inner solve of the MIXED path reaches; default 1e-5.  Every inner solve
+ *               (both paths) also goes at least as far as the outer test still needs:
+ *               a tenth of tol * max_i |U_i| after its correction. */
 typedef struct {
   double tol;
   int32_t max_iter;

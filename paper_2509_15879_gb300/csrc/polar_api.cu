@@ -688,8 +688,9 @@ int bicg_iteration(polar_ctx* c, CondHandle cond) {
   TLAUNCH("bicg_s", 3 * B * nv, launch_bicg_s<T>(nv, k.r, k.v, k.s, c->cs, red));
   TRY(vcycle<T>(c, k.s, k.shat));
   TLAUNCH("stencil_dot", 8 * B * pts, launch_apply_dot<T>(L0, c->par(), k.shat, k.t, k.s, 1, c->cs, red));
-  TLAUNCH("bicg_update", 8 * B * nv,
-          launch_bicg_update<T>(nv, k.d, k.phat, k.shat, k.r, k.s, k.t, k.rhat, c->cs, red));
+  TLAUNCH("bicg_update", 9 * B * nv,
+          launch_bicg_update<T>(nv, k.d, k.phat, k.shat, k.r, k.s, k.t, k.rhat, L0.diag,
+                                L0.sc, c->cs, red));
   TLAUNCH("bicg_p", 4 * B * nv, launch_bicg_p<T>(nv, k.p, k.r, k.v, cond, c->cs, red));
   return POLAR_OK;
 }
@@ -788,18 +789,6 @@ int capture_end(polar_ctx* c, std::vector<cudaGraphNode_t>* sinks) {
   cudaGraph_t out = nullptr;
   CUDA_TRY(cudaStreamEndCapture(c->cap, &out));
   c->cs = c->st;
-  return POLAR_OK;
-}
-
-int add_while(cudaGraph_t g, const std::vector<cudaGraphNode_t>& deps, cudaGraphConditionalHandle h,
-              cudaGraphNode_t* node, cudaGraph_t* body) {
-  cudaGraphNodeParams np{};
-  np.type = cudaGraphNodeTypeConditional;
-  np.conditional.handle = h;
-  np.conditional.type = cudaGraphCondTypeWhile;
-  np.conditional.size = 1;
-  CUDA_TRY(cudaGraphAddNode(node, g, deps.data(), nullptr, deps.size(), &np));
-  *body = np.conditional.phGraph_out[0];
   return POLAR_OK;
 }
 
@@ -936,7 +925,7 @@ int set_step_params(polar_ctx* c, double alpha, double theta, const double* cf, 
     p.cg[q] = cg[q];
   }
   p.tol = o.tol;
-  p.inner_tol = (c->precision == POLAR_FP64) ? std::min(o.inner_tol, 1e-12) : o.inner_tol;
+  p.inner_tol = (c->precision == POLAR_FP64) ? 0.0 : o.inner_tol;
   p.max_iter = o.max_iter;
   p.max_refine = o.max_refine;
   p.do_refresh = (alpha != c->cur_alpha || theta != c->cur_beta) ? 1 : 0;
@@ -964,7 +953,7 @@ int make_params(polar_ctx* c, double t0, double t1, double theta, const double* 
     p.cg[q] = -((1.0 - theta) * w_old[q] + theta * w_new[q]);
   }
   p.tol = o.tol;
-  p.inner_tol = (c->precision == POLAR_FP64) ? std::min(o.inner_tol, 1e-12) : o.inner_tol;
+  p.inner_tol = (c->precision == POLAR_FP64) ? 0.0 : o.inner_tol;
   p.max_iter = o.max_iter;
   p.max_refine = o.max_refine;
   p.do_refresh = (p.alpha != prev_alpha || theta != prev_beta) ? 1 : 0;

@@ -102,6 +102,8 @@ struct KrylovScalars {
   double scaled;   // last Jacobi-scaled residual max |r_i| / S_ii / max |x_i|
   int halt;        // a step of the current schedule failed: the later ones are skipped
   int pad2;
+  double sm_tol;   // inner solve: stop when max_i |r_i| / S_ii of its residual is below
+  double sm;       //   sm_tol (sm: the last value)
 };
 
 // Result of one step of a device-side schedule (graph mode).
@@ -217,7 +219,8 @@ template <typename T>
 int launch_bicg_s(size_t nv, const T* r, const T* v, T* s, cudaStream_t st, Reduce red);
 template <typename T>
 int launch_bicg_update(size_t nv, T* x, const T* phat, const T* shat, T* r, const T* s,
-                       const T* t, const T* rhat, cudaStream_t st, Reduce red);
+                       const T* t, const T* rhat, const T* diag, const double* sc,
+                       cudaStream_t st, Reduce red);
 template <typename T>
 int launch_bicg_p(size_t nv, T* p, const T* r, const T* v, CondHandle cond, cudaStream_t st,
                   Reduce red);

@@ -430,6 +430,14 @@ __global__ void __launch_bounds__(kVT) k_bicg_init(size_t nv, const T* r, T* rha
   ks->rr = tot[0];
   ks->rho = tot[0];
   ks->tol2 = rel_tol * rel_tol * tot[0];
+  // The inner residual is r / rmax with r the FP64 residual, so its Jacobi-scaled max
+  // norm starts at smax / rmax.  The solve stops once that norm has fallen by the
+  // larger of the requested reduction and what the outer test still needs (a tenth of
+  // tol max|x| after the correction): the max norm, like the outer test, so that a few
+  // rows cannot hide behind a small 2-norm of many.
+  const double need = (ks->smax > 0.0) ? 0.1 * sp->tol * ks->xmax / ks->smax : 1.0;
+  ks->sm_tol = fmax(rel_tol, need) * (ks->rmax > 0.0 ? ks->smax / ks->rmax : 0.0);
+  ks->sm = INFINITY;
   ks->alpha = 1.0;
   ks->omega = 1.0;
   ks->beta = 0.0;
@@ -449,33 +457,44 @@ __global__ void __launch_bounds__(kVT) k_bicg_s(size_t nv, const T* r, const T* 
     s[k] = fma(-alpha, v[k], r[k]);
 }
 
+// |r| / d in FP32 (a stopping test needs no more); padding entries have d = 0
+template <typename T>
+__device__ __forceinline__ float scaled_abs(T r, T d) {
+  return d > T(0) ? fabsf((float)r) / (float)d : 0.f;
+}
+
 template <typename T>
 __global__ void __launch_bounds__(kVT) k_bicg_update(size_t nv, T* x, const T* phat,
                                                      const T* shat, T* r, const T* s,
-                                                     const T* t, const T* rhat, Reduce red) {
+                                                     const T* t, const T* rhat, const T* diag,
+                                                     const double* sc, Reduce red) {
   if (red.ks->done) return;
   const T alpha = (T)red.ks->alpha, omega = (T)red.ks->omega;
   double s1 = 0.0, s2 = 0.0;
+  float sm = 0.f;
   for (size_t k = blockIdx.x * (size_t)kVT + threadIdx.x; k < nv; k += (size_t)gridDim.x * kVT) {
     x[k] = fma(omega, shat[k], fma(alpha, phat[k], x[k]));
     const T rn = fma(-omega, t[k], s[k]);
     r[k] = rn;
     s1 = fma((double)rhat[k], (double)rn, s1);
     s2 = fma((double)rn, (double)rn, s2);
+    // the origin's diagonal lives in the level scalars (entry 0 of diag is unused)
+    sm = fmaxf(sm, scaled_abs<T>(rn, k == 0 ? (T)sc[0] : diag[k]));
   }
-  double acc[2] = {s1, s2};
-  block_reduce<2, 2>(acc);
-  if (!publish_and_arrive<2>(acc, red.part, &red.ks->counter)) return;
-  double tot[2];
-  grid_totals<2, 2>(red.part, tot);
+  double acc[3] = {s1, s2, isfinite(sm) ? (double)sm : INFINITY};
+  block_reduce<3, 2>(acc);
+  if (!publish_and_arrive<3>(acc, red.part, &red.ks->counter)) return;
+  double tot[3];
+  grid_totals<3, 2>(red.part, tot);
   if (threadIdx.x != 0) return;
   KrylovScalars* ks = red.ks;
   const double rho_new = tot[0], rr = tot[1];
   ks->rr = rr;
+  ks->sm = tot[2];
   ks->iters += 1;
   if (!isfinite(rr) || !isfinite(rho_new)) {
     ks->done = 3;
-  } else if (rr <= ks->tol2) {
+  } else if (tot[2] <= ks->sm_tol) {
     ks->done = 1;
   } else if (ks->iters >= ks->max_iter) {
     ks->done = 4;
@@ -512,8 +531,10 @@ int launch_bicg_s(size_t nv, const T* r, const T* v, T* s, cudaStream_t st, Redu
 }
 template <typename T>
 int launch_bicg_update(size_t nv, T* x, const T* phat, const T* shat, T* r, const T* s,
-                       const T* t, const T* rhat, cudaStream_t st, Reduce red) {
-  k_bicg_update<T><<<grid_for(nv, kVT), kVT, 0, st>>>(nv, x, phat, shat, r, s, t, rhat, red);
+                       const T* t, const T* rhat, const T* diag, const double* sc,
+                       cudaStream_t st, Reduce red) {
+  k_bicg_update<T><<<grid_for(nv, kVT), kVT, 0, st>>>(nv, x, phat, shat, r, s, t, rhat, diag,
+                                                       sc, red);
   return 1;
 }
 template <typename T>
@@ -726,7 +747,7 @@ int launch_unpack(const Shape& sh, const double* in, const double* div, double* 
                                    CondHandle, cudaStream_t, Reduce);                          \
   template int launch_bicg_s<T>(size_t, const T*, const T*, T*, cudaStream_t, Reduce);         \
   template int launch_bicg_update<T>(size_t, T*, const T*, const T*, T*, const T*, const T*,   \
-                                     const T*, cudaStream_t, Reduce);                          \
+                                     const T*, const T*, const double*, cudaStream_t, Reduce); \
   template int launch_bicg_p<T>(size_t, T*, const T*, const T*, CondHandle, cudaStream_t,      \
                                 Reduce);                                                       \
   template int launch_scale_cast<T>(size_t, const double*, T*, cudaStream_t, Reduce);          \

@@ -58,7 +58,7 @@ struct RefreshLevel {
   void* fz;
   double* ws;  // 3 nv doubles: forward values, pivot reciprocals, q (FP64)
   int coarsest;
-  int ring0;   // first global ring index of this level
+  int ring0;   // first CTA of this level in the refresh grid
 };
 constexpr int kMaxLevels = 20;
 struct RefreshArgs {
@@ -67,8 +67,8 @@ struct RefreshArgs {
   const StepParams* sp;
 };
 
-// One thread per ring of every level.  Ring i of a level is the periodic tridiagonal
-// system  a_j x_{j-1} + b_j x_j + c_j x_{j+1} = d_j  (indices mod n) with
+// Ring i of a level is the periodic tridiagonal system
+//   a_j x_{j-1} + b_j x_j + c_j x_{j+1} = d_j  (indices mod n) with
 //   a_j = beta s_ij,  b_j = alpha vol_ij + beta (rs - w - e - s - nn)_ij,  c_j = beta nn_ij.
 // Sherman-Morrison: with gamma = -b_0, u = (gamma, 0, .., 0, c_{n-1}),
 // v = (1, 0, .., 0, a_0 / gamma), the system is (T' + u v^T) x = d where T' is the
@@ -76,121 +76,219 @@ struct RefreshArgs {
 // b'_{n-1} = b_{n-1} - c_{n-1} a_0 / gamma.  Stored: Doolittle factors of T'
 // (l_j = a_j / u_{j-1}, ui_j = 1 / u_j, cu_j = c_j / u_j), q = T'^{-1} u and, per ring,
 // vf = a_0 / gamma and 1 / (1 + v.q).
+//
+// A CTA factors RF rings of one parity block (threadIdx.x; consecutive rings are
+// adjacent in memory) with TF threads per ring (threadIdx.y), each owning a chunk of
+// consecutive angles.  Every recurrence along the ring is turned into a scan over the
+// chunks:
+//   pivots  u_j = b'_j - a_j c_{j-1} / u_{j-1} is the projective action of the 2 x 2
+//           matrices [[b'_j, -a_j c_{j-1}], [1, 0]] on (u_{j-1}, 1): each chunk composes
+//           its matrices (rescaled by powers of two), an exclusive scan gives every chunk
+//           its incoming pivot, and the chunk replays the recurrence from it;
+//   y = L^{-1} u forward and q = U^{-1} y backward are affine recurrences, scanned the
+//           same way (the backward one with the chunk order reversed).
+// All arithmetic is FP64; only the stored factors take the inner precision T.
+constexpr int RF = 4;     // rings per CTA
+constexpr int TF = 128;   // threads per ring
+
+struct M2 {  // [[a, b], [c, d]]
+  double a, b, c, d;
+};
+struct A2 {  // x -> a x + b
+  double a, b;
+};
+__device__ __forceinline__ M2 comb(const M2& first, const M2& then) {  // then * first
+  return M2{fma(then.a, first.a, then.b * first.c), fma(then.a, first.b, then.b * first.d),
+            fma(then.c, first.a, then.d * first.c), fma(then.c, first.b, then.d * first.d)};
+}
+__device__ __forceinline__ A2 comb(const A2& first, const A2& then) {  // then o first
+  return A2{then.a * first.a, fma(then.a, first.b, then.b)};
+}
+__device__ __forceinline__ M2 shfl_up(const M2& v, int off) {
+  return M2{__shfl_up_sync(0xffffffffu, v.a, off), __shfl_up_sync(0xffffffffu, v.b, off),
+            __shfl_up_sync(0xffffffffu, v.c, off), __shfl_up_sync(0xffffffffu, v.d, off)};
+}
+__device__ __forceinline__ A2 shfl_up(const A2& v, int off) {
+  return A2{__shfl_up_sync(0xffffffffu, v.a, off), __shfl_up_sync(0xffffffffu, v.b, off)};
+}
+// rescales a matrix by a power of two (exact) so that its largest entry is in [1, 2)
+__device__ __forceinline__ M2 renorm(const M2& m) {
+  const double mx = fmax(fmax(fabs(m.a), fabs(m.b)), fmax(fabs(m.c), fabs(m.d)));
+  if (!(mx > 0.0) || !isfinite(mx)) return m;
+  const int e = ilogb(mx);
+  return M2{ldexp(m.a, -e), ldexp(m.b, -e), ldexp(m.c, -e), ldexp(m.d, -e)};
+}
+
+// composition inside the scans: the matrix products are rescaled after every step (their
+// entries hold different powers of the coupling, and unscaled products over a long ring
+// underflow); the affine maps only shrink
+__device__ __forceinline__ M2 scan_comb(const M2& first, const M2& then) {
+  return renorm(comb(first, then));
+}
+__device__ __forceinline__ A2 scan_comb(const A2& first, const A2& then) {
+  return comb(first, then);
+}
+
+// Exclusive scan over the TF chunks of each ring of the CTA (thread (r, c), linear index
+// r + RF c): returns the composition of the maps of chunks 0..c-1 (identity for c = 0).
+template <typename V>
+__device__ V chunk_excl_scan(V v, const V& ident, V* sw) {
+  const int tid = threadIdx.x + RF * threadIdx.y;
+  const int lane = tid & 31, warp = tid >> 5;
+  const int per = 32 / RF, pos = lane / RF, r = threadIdx.x;
+  V inc = v;
+#pragma unroll
+  for (int off = 1; off < per; off <<= 1) {
+    const V o = shfl_up(inc, off * RF);
+    if (pos >= off) inc = scan_comb(o, inc);
+  }
+  V exc = shfl_up(inc, RF);
+  if (pos == 0) exc = ident;
+  if (pos == per - 1) sw[warp * RF + r] = inc;
+  __syncthreads();
+  V pre = ident;
+  for (int w = 0; w < warp; ++w) pre = scan_comb(pre, sw[w * RF + r]);
+  __syncthreads();
+  return scan_comb(pre, exc);
+}
+
 template <typename T>
-__global__ void k_refresh(RefreshArgs A) {
-  const int g = blockIdx.x * blockDim.x + threadIdx.x;
-  int l = 0;
-  while (l + 1 < A.nlev && g >= A.lv[l + 1].ring0) ++l;
-  const RefreshLevel& L = A.lv[l];
-  const int local = g - L.ring0;
-  const Shape sh = L.sh;
-  if (local < 0 || local >= sh.m) return;
+__global__ void __launch_bounds__(RF * TF) k_refresh(RefreshArgs A) {
+  __shared__ M2 sm2[(RF * TF / 32) * RF];
+  __shared__ A2 sa2[(RF * TF / 32) * RF];
+  __shared__ double qend[2][RF];
   if (!A.sp->do_refresh) return;
-  const double alpha = A.sp->alpha, beta = A.sp->beta;
-  // ring order: odd rings (local < no) then even rings
-  const int i = (local < sh.no) ? 2 * local + 1 : 2 * (local - sh.no) + 2;
+  // which level, parity block and group of RF rings this CTA takes
+  int l = 0;
+  while (l + 1 < A.nlev && (int)blockIdx.x >= A.lv[l + 1].ring0) ++l;
+  const RefreshLevel& L = A.lv[l];
+  const Shape sh = L.sh;
+  int g = blockIdx.x - L.ring0;
+  const int godd = (sh.no + RF - 1) / RF;
+  const int parity = g < godd ? 1 : 0;
+  if (!parity) g -= godd;
+  const int nlines = parity ? sh.no : sh.ne;
+  const int r = threadIdx.x, cidx = threadIdx.y;
+  const int k = g * RF + r;
+  const bool valid = k < nlines;
+  const int i = parity ? 2 * (valid ? k : 0) + 1 : 2 * (valid ? k : 0) + 2;
+  const int local = parity ? k : sh.no + k;  // ring slot: odd rings, then even rings
   const int n = sh.n;
+  const size_t ld = parity ? sh.ldo : sh.lde;
+  const size_t q0 = sh.at(i, 0);
+  const double alpha = A.sp->alpha, beta = A.sp->beta;
   T* diag = static_cast<T*>(L.diag);
   T* fl = static_cast<T*>(L.fl);
   T* fui = static_cast<T*>(L.fui);
   T* fcu = static_cast<T*>(L.fcu);
   T* fq = static_cast<T*>(L.fq);
-  T* fring = static_cast<T*>(L.fring);
   double* wy = L.ws;
   double* wu = L.ws + sh.nv;
-  double* wq = L.ws + 2 * sh.nv;
-  auto dg = [&](size_t q) {
+  const int P = (n + TF - 1) / TF;
+  auto bdiag = [&](size_t q) {
     return alpha * L.vol[q] + beta * (L.rs[q] - L.w[q] - L.e[q] - L.s[q] - L.nn[q]);
   };
-  const size_t q0 = sh.at(i, 0), qn = sh.at(i, n - 1);
-  const double a0 = beta * L.s[q0];
-  const double b0 = dg(q0);
-  const double cn1 = beta * L.nn[qn];
+  // corner terms of the periodic system
+  const double b0 = valid ? bdiag(q0) : 1.0;
   const double gamma = -b0;
+  const double a0 = valid ? beta * L.s[q0] : 0.0;
+  const double cn1 = valid ? beta * L.nn[q0 + (size_t)(n - 1) * ld] : 0.0;
   const double vf = a0 / gamma;
-  const size_t ld = (i & 1) ? sh.ldo : sh.lde;
-  // the coefficient loads do not depend on the recurrence: they are issued U angles
-  // ahead so that the division chain, not the memory latency, sets the pace
-  constexpr int U = 8;
-  double uiprev = 1.0, cprev = 0.0, yq = 0.0;
-  for (int jb = 0; jb < n; jb += U) {
-    double cv[U], cr[U], cw[U], ce[U], cs[U], cn[U];
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const int j = jb + u;
-      if (j < n) {
-        const size_t q = q0 + (size_t)j * ld;
-        cv[u] = L.vol[q];
-        cr[u] = L.rs[q];
-        cw[u] = L.w[q];
-        ce[u] = L.e[q];
-        cs[u] = L.s[q];
-        cn[u] = L.nn[q];
-      }
-    }
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const int j = jb + u;
-      if (j >= n) break;
+  auto bmod = [&](int j, double bd) {
+    double bb = bd;
+    if (j == 0) bb -= gamma;
+    if (j == n - 1) bb -= cn1 * vf;
+    return bb;
+  };
+  auto cc = [&](int j) {  // c_j (0 past the end of the non-periodic part)
+    return (j >= 0 && j < n - 1) ? beta * L.nn[q0 + (size_t)j * ld] : 0.0;
+  };
+
+  // ---- pivots: compose this chunk's matrices, scan, replay
+  const int j0 = valid ? min(n, cidx * P) : n, j1 = valid ? min(n, j0 + P) : n;
+  M2 m{1.0, 0.0, 0.0, 1.0};
+  {
+    double cprev = cc(j0 - 1);
+    for (int j = j0; j < j1; ++j) {
       const size_t q = q0 + (size_t)j * ld;
-      const double a = (j > 0) ? beta * cs[u] : 0.0;
-      const double bd = alpha * cv[u] + beta * (cr[u] - cw[u] - ce[u] - cs[u] - cn[u]);
-      diag[q] = (T)bd;
-      if (L.diag64) L.diag64[q] = bd;
-      if (L.rsum) static_cast<T*>(L.rsum)[q] = (T)(alpha * cv[u] + beta * cr[u]);
-      double bb = bd;
-      if (j == 0) bb -= gamma;
-      if (j == n - 1) bb -= cn1 * vf;
-      const double c = (j < n - 1) ? beta * cn[u] : 0.0;
-      const double lj = (j > 0) ? a * uiprev : 0.0;
-      const double uu = bb - lj * cprev;
-      const double ui = 1.0 / uu;
-      fl[q] = (T)lj;
-      fui[q] = (T)ui;
-      fcu[q] = (T)(c * ui);
+      const double a = (j > 0) ? beta * L.s[q] : 0.0;
+      const M2 mj{bmod(j, bdiag(q)), -a * cprev, 1.0, 0.0};
+      m = comb(m, mj);
+      if (((j - j0) & 3) == 3) m = renorm(m);
+      cprev = cc(j);
+    }
+    m = renorm(m);
+  }
+  const M2 pm = chunk_excl_scan(m, M2{1.0, 0.0, 0.0, 1.0}, sm2);
+  // incoming state (u_{j0-1}, 1) ~ pm (1, 0)^T; chunk 0 starts from (1, 0): ui = 0
+  double uiprev = (pm.a != 0.0) ? pm.c / pm.a : 0.0;
+  double cprev = cc(j0 - 1);
+  A2 fy{1.0, 0.0};
+  for (int j = j0; j < j1; ++j) {
+    const size_t q = q0 + (size_t)j * ld;
+    const double bd = bdiag(q);
+    diag[q] = (T)bd;
+    if (L.diag64) L.diag64[q] = bd;
+    if (L.rsum) static_cast<T*>(L.rsum)[q] = (T)(alpha * L.vol[q] + beta * L.rs[q]);
+    const double a = (j > 0) ? beta * L.s[q] : 0.0;
+    const double c = cc(j);
+    const double lj = a * uiprev;
+    const double ui = 1.0 / (bmod(j, bd) - lj * cprev);
+    fl[q] = (T)lj;
+    fui[q] = (T)ui;
+    fcu[q] = (T)(c * ui);
+    wu[q] = ui;
+    // y_j = ur_j - l_j y_{j-1}, ur = (gamma, 0, .., 0, c_{n-1})
+    const double ur = (j == 0) ? gamma : ((j == n - 1) ? cn1 : 0.0);
+    fy = comb(fy, A2{-lj, ur});
+    uiprev = ui;
+    cprev = c;
+  }
+  // ---- y = L^{-1} u
+  const A2 py = chunk_excl_scan(fy, A2{1.0, 0.0}, sa2);
+  {
+    double y = py.b;  // y_{j0-1} (y_{-1} = 0)
+    for (int j = j0; j < j1; ++j) {
+      const size_t q = q0 + (size_t)j * ld;
+      const double lj = (j > 0) ? beta * L.s[q] * wu[q - ld] : 0.0;
       const double ur = (j == 0) ? gamma : ((j == n - 1) ? cn1 : 0.0);
-      yq = ur - lj * yq;
-      wy[q] = yq;
-      wu[q] = ui;
-      uiprev = ui;
-      cprev = c;
+      y = fma(-lj, y, ur);
+      wy[q] = y;
     }
   }
-  double qnext = 0.0, qfirst = 0.0, qlast = 0.0;
-  for (int jb = n - 1; jb >= 0; jb -= U) {
-    double cu[U], cy[U], cn[U];
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const int j = jb - u;
-      if (j >= 0) {
-        const size_t q = q0 + (size_t)j * ld;
-        cu[u] = wu[q];
-        cy[u] = wy[q];
-        cn[u] = L.nn[q];
-      }
-    }
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const int j = jb - u;
-      if (j < 0) break;
+  __syncthreads();
+  // ---- q = U^{-1} y, chunks taken in reverse order (thread c owns chunk TF - 1 - c)
+  const int rc = TF - 1 - cidx;
+  const int k0 = valid ? min(n, rc * P) : n, k1 = valid ? min(n, k0 + P) : n;
+  A2 fq2{1.0, 0.0};
+  for (int j = k1 - 1; j >= k0; --j) {
+    const size_t q = q0 + (size_t)j * ld;
+    const double ui = wu[q];
+    fq2 = comb(fq2, A2{-cc(j) * ui, ui * wy[q]});
+  }
+  const A2 pq = chunk_excl_scan(fq2, A2{1.0, 0.0}, sa2);
+  {
+    double qn = pq.b;  // q_{k1} (q_n = 0)
+    for (int j = k1 - 1; j >= k0; --j) {
       const size_t q = q0 + (size_t)j * ld;
-      const double c = (j < n - 1) ? beta * cn[u] : 0.0;
-      const double qq = cu[u] * (cy[u] - c * qnext);
-      fq[q] = (T)qq;
-      wq[q] = qq;
-      if (j == n - 1) qlast = qq;
-      if (j == 0) qfirst = qq;
-      qnext = qq;
+      const double ui = wu[q];
+      qn = fma(-cc(j) * ui, qn, ui * wy[q]);
+      fq[q] = (T)qn;
+      if (j == 0) qend[0][r] = qn;
+      if (j == n - 1) qend[1][r] = qn;
     }
   }
-  const double inv = 1.0 / (1.0 + qfirst + vf * qlast);
-  fring[2 * local] = (T)vf;
-  fring[2 * local + 1] = (T)inv;
-  if (i == 1) {
-    // origin scalars of this level: diag0 = alpha vol0 + beta (rs0 - sum_j o_j)
-    const double d0 = alpha * L.sc[3] + beta * (L.sc[4] - L.sc[2]);
-    L.sc[0] = d0;
-    L.sc[5] = alpha * L.sc[3] + beta * L.sc[4];
+  __syncthreads();
+  if (valid && cidx == 0) {
+    T* fring = static_cast<T*>(L.fring);
+    fring[2 * local] = (T)vf;
+    fring[2 * local + 1] = (T)(1.0 / (1.0 + qend[0][r] + vf * qend[1][r]));
+    if (i == 1) {
+      // origin scalars of this level: diag0 = alpha vol0 + beta (rs0 - sum_j o_j)
+      const double d0 = alpha * L.sc[3] + beta * (L.sc[4] - L.sc[2]);
+      L.sc[0] = d0;
+      L.sc[5] = alpha * L.sc[3] + beta * L.sc[4];
+    }
   }
 }
 
@@ -229,10 +327,10 @@ int launch_refresh(const LevelView<double>* L64, LevelView<T>* LT, int nlev,
     r.ws = ws + wofs;
     wofs += 3 * d.sh.nv;
     r.coarsest = (l == nlev - 1);
-    r.ring0 = rings;
-    rings += d.sh.m;
+    r.ring0 = rings;  // first CTA of this level (groups of RF rings, odd block first)
+    rings += (d.sh.no + RF - 1) / RF + (d.sh.ne + RF - 1) / RF;
   }
-  k_refresh<T><<<(rings + 31) / 32, 32, 0, st>>>(A);
+  k_refresh<T><<<rings, dim3(RF, TF), 0, st>>>(A);
   return 1 + launch_schur<T>(LT[nlev - 1], sp, st);
 }
 
