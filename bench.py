@@ -256,6 +256,9 @@ def run_native(args):
         launches0 = P.polar_kernel_launches(ctx)
         if timers:
             P.polar_timing_enable(ctx, True)
+            # the per-kernel pass runs the kernels eagerly (ncu cannot see kernels inside
+            # conditional graph nodes); `ncu --profile-from-start off` captures this range
+            torch.cuda.profiler.start()
         barrier()
         wall0 = time.perf_counter()
         for s, k in enumerate(levels):
@@ -270,6 +273,8 @@ def run_native(args):
             if consecutive and not timers and (k + 1) % 100 == 0:
                 checkpoints[k + 1] = P.polar_get_state(ctx)[0]
         barrier()
+        if timers:
+            torch.cuda.profiler.stop()
         wall = time.perf_counter() - wall0
         launches = P.polar_kernel_launches(ctx) - launches0
         kstats = P.polar_timing_query(ctx) if timers else {}
@@ -489,6 +494,40 @@ def run_batch(args):
     return 0
 
 
+# ------------------------------------------------------------------------- profiling
+def run_profile_step(args):
+    """One eager theta-step of a named workload inside a CUDA profiler range, after the
+    autotuner and a warm-up step, with per-kernel CUDA-event times (for
+    `ncu --profile-from-start off`).  Workloads: c2 (the bench workload), c3 (continuity
+    2048 x 4096, 2000-level time stretch), c5 (continuity 8192 x 16384 graded to r = 1,
+    theta = 0.6, 200 levels).  The step is the third level of the schedule."""
+    import torch
+    import polar_inputs as pi
+    import paper_2509_15879_gb300 as P
+    from paper_2509_15879_gb300 import driver
+    prob = {"c2": make_problem, "c3": pi.config3, "c5": pi.config5}[args.workload]()
+    precision = P.POLAR_MIXED if args.precision == "mixed" else P.POLAR_FP64
+    t = np.asarray(prob.t)
+    W = prob.weight_table()
+    ctx = driver.create(prob, precision)
+    P.polar_advance(ctx, t[0:2], prob.theta_w, W[0:2])   # autotuner + graph
+    P.polar_timing_enable(ctx, True)
+    P.polar_advance(ctx, t[1:3], prob.theta_w, W[1:3])
+    torch.cuda.synchronize()
+    torch.cuda.profiler.start()
+    st, _ = P.polar_advance(ctx, t[2:4], prob.theta_w, W[2:4])
+    torch.cuda.synchronize()
+    torch.cuda.profiler.stop()
+    q = P.polar_timing_query(ctx)
+    print(json.dumps({"workload": args.workload, "m": prob.m, "n": prob.n,
+                      "precision": args.precision, "step": st[0],
+                      "kernels": {k: {"launches": v["launches"], "us_per_launch":
+                                      round(1e3 * v["ms"] / max(v["launches"], 1), 2),
+                                      "GBps": round(v["bytes"] / max(v["ms"], 1e-9) / 1e6, 1)}
+                                  for k, v in sorted(q.items(), key=lambda kv: -kv[1]["ms"])}}))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -500,11 +539,19 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--compare", type=int, default=1,
                     help="also time the other precision on the same steps")
-    ap.add_argument("--workload", choices=["c2", "batch"], default="c2")
+    ap.add_argument("--workload", choices=["c2", "batch", "c3", "c5"], default="c2",
+                    help="c2: the timed workload; batch: the 256-instance sweep; c3/c5: only "
+                         "with --profile-step")
+    ap.add_argument("--profile-step", action="store_true",
+                    help="run one eager step of --workload inside a profiler range")
     ap.add_argument("--instances", type=int, default=256)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.profile_step:
+        return run_profile_step(args)
+    if args.workload in ("c3", "c5"):
+        ap.error("--workload c3/c5 needs --profile-step")
     if args.workload == "batch":
         return run_batch(args)
     return run_native(args)

@@ -134,10 +134,13 @@ typedef struct {
 } polar_solver_opts;
 
 typedef struct {
-  int32_t iters;         /* Krylov iterations (all inner solves for MIXED)            */
-  int32_t refinements;   /* outer FP64 residual evaluations (MIXED), 1 for FP64       */
+  int32_t iters;         /* Krylov iterations of all inner solves                     */
+  int32_t refinements;   /* FP64 residual evaluations (one more than the inner solves) */
   int32_t status;        /* POLAR_OK or the error of this step                        */
-  int32_t pad;
+  int32_t fp64_iters;    /* MIXED: of iters, those of FP64 Krylov solves over the FP32
+                            V-cycle, which the step switches to once a sweep of FP32
+                            refinement gains less than a factor 10 (or an FP32 solve
+                            breaks down or hits max_iter); 0 for FP64                 */
   double scaled_resid;   /* final max |r_i| / A_ii / max |U_i|                        */
 } polar_step_stats;
 

@@ -42,11 +42,11 @@ class polar_solver_opts(C.Structure):
 
 class polar_step_stats(C.Structure):
     _fields_ = [("iters", C.c_int32), ("refinements", C.c_int32), ("status", C.c_int32),
-                ("pad", C.c_int32), ("scaled_resid", C.c_double)]
+                ("fp64_iters", C.c_int32), ("scaled_resid", C.c_double)]
 
     def as_dict(self):
         return dict(iters=self.iters, refinements=self.refinements, status=self.status,
-                    scaled_resid=self.scaled_resid)
+                    fp64_iters=self.fp64_iters, scaled_resid=self.scaled_resid)
 
 
 class PolarError(RuntimeError):

@@ -121,11 +121,8 @@ struct polar_ctx {
   cudaGraphExec_t gexec = nullptr;
   bool graph_ok = false;          // gexec matches the current coefficients
   bool use_graph = true;
-  // coarse end of the V-cycle in one CTA (launch_coarse_cycle).  Off: measured on the
-  // 512 x 1024 workload, one CTA took 272 us per V-cycle (FP32) and 611 us (FP64) for the
-  // levels below 32 rings, against about 210 us for their separate launches.
-  bool coarse_fusion = false;
   int64_t graph_kernels_fixed = 0, graph_kernels_sweep = 0, graph_kernels_iter = 0;
+  int64_t graph_kernels_iter64 = 0;  // mixed path: an FP64 Krylov iteration over the FP32 V-cycle
   int64_t generation = 0;         // bumped whenever a captured graph goes stale
   // ring-solve tile shapes per level, [mode * 2 + parity] (autotuned on first use)
   std::vector<std::array<RingShape, 4>> tiles;
@@ -479,20 +476,8 @@ const RingShape* tile(const polar_ctx* c, int l, int mode, int parity) {
   return s.P > 0 ? &s : nullptr;
 }
 
-// first level of the hierarchy that the one-CTA coarse cycle takes (nlev - 1: none)
-template <typename T>
-int coarse_start(const polar_ctx* c) {
-  const std::vector<LevelView<T>>& L = views<T>(c);
-  const int nl = c->nlev();
-  int lc = nl - 1;
-  if (c->coarse_fusion && sizeof(T) == 4)
-    while (lc > 0 && L[lc - 1].sh.no <= coarse_cycle_lines<T>()) --lc;
-  return lc;
-}
-
-// x = M^{-1} b: one V(1,1) cycle of the radial multigrid (polar_mg.cu).  The levels
-// from `lc` down run inside one CTA (launch_coarse_cycle); the ones above it launch one
-// kernel per half-sweep.
+// x = M^{-1} b: one V(1,1) cycle of the radial multigrid (polar_mg.cu), one kernel per
+// half-sweep and level.
 template <typename T>
 int vcycle(polar_ctx* c, const T* b, T* x) {
   const std::vector<LevelView<T>>& L = views<T>(c);
@@ -508,9 +493,7 @@ int vcycle(polar_ctx* c, const T* b, T* x) {
     s = std::string(base) + (l == 0 ? "@L0" : l == 1 ? "@L1" : "@L2+");
     return s.c_str();
   };
-  // one CTA holds the coarse end only in FP32: GB300's FP64 rate per SM (about 2 FMA
-  // per clock) makes a single CTA far slower than the same FP64 work spread over SMs
-  int lc = coarse_start<T>(c);
+  const int lc = nl - 1;
   for (int l = 0; l < lc; ++l) {
     const Shape& s = L[l].sh;
     const double po = (double)s.no * s.n, pe = (double)s.ne * s.n;
@@ -527,28 +510,8 @@ int vcycle(polar_ctx* c, const T* b, T* x) {
             launch_restrict<T>(L[l], L[l + 1], xof(l), static_cast<T*>(c->lv[l + 1].b), par, done,
                                c->cs));
   }
-  bool fused = false;
-  if (lc < nl - 1) {
-    std::vector<T*> bl(nl, nullptr), xl(nl, nullptr);
-    for (int l = 1; l < nl; ++l) {
-      bl[l] = static_cast<T*>(c->lv[l].b);
-      xl[l] = static_cast<T*>(c->lv[l].x);
-    }
-    double words = 0.0;
-    for (int l = lc; l < nl; ++l) words += 40.0 * L[l].sh.m * L[l].sh.n;
-    cudaEvent_t ev_;
-    TRY(timed_begin(c, &ev_));
-    const int k = launch_coarse_cycle<T>(L.data(), lc, nl, bof(lc), xof(lc), bl.data(), xl.data(),
-                                         par, done, c->cs);
-    LAUNCH(k);
-    TRY(timed_end(c, ev_, "coarse_cycle", B * words));
-    fused = k > 0;
-  }
-  if (!fused) {
-    lc = nl - 1;
-    TLAUNCH("coarsest", 8 * B * L[nl - 1].sh.n,
-            launch_coarsest<T>(L[nl - 1], bof(nl - 1), xof(nl - 1), par, done, c->cs));
-  }
+  TLAUNCH("coarsest", 8 * B * L[nl - 1].sh.n,
+          launch_coarsest<T>(L[nl - 1], bof(nl - 1), xof(nl - 1), par, done, c->cs));
   for (int l = lc - 1; l >= 0; --l) {
     const Shape& s = L[l].sh;
     const double po = (double)s.no * s.n, pe = (double)s.ne * s.n;
@@ -595,7 +558,7 @@ template <typename T>
 int tune_rings(polar_ctx* c) {
   const std::vector<LevelView<T>>& L = views<T>(c);
   const int nl = c->nlev();
-  const int lc = coarse_start<T>(c);
+  const int lc = nl - 1;
   c->tiles.assign(nl, std::array<RingShape, 4>{});
   CUDA_TRY(cudaMemsetAsync(&c->ks->done, 0, sizeof(int), c->st));
   cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -695,6 +658,33 @@ int bicg_iteration(polar_ctx* c, CondHandle cond) {
   return POLAR_OK;
 }
 
+// Mixed path fallback: one BiCGStab iteration in FP64 (vectors, matrix, scalars) whose
+// preconditioner is the FP32 V-cycle, entered and left through casts.  The FP32
+// rounding of the preconditioner changes only how fast the iteration converges, not the
+// FP64 residual it converges to.
+int bicg_iteration_x(polar_ctx* c, CondHandle cond) {
+  KVecs<double>& k = c->kv64;
+  KVecs<float>& f = c->kv32;
+  const LevelView<double>& L0 = c->v64[0];
+  const Reduce red = c->red();
+  const size_t nv = c->nv();
+  const double pts = (double)c->m * c->n;
+  TLAUNCH("cast", 12.0 * nv, launch_to_float(nv, k.p, f.r, c->cs));
+  TRY(vcycle<float>(c, f.r, f.phat));
+  TLAUNCH("cast", 12.0 * nv, launch_to_double(nv, f.phat, k.phat, c->cs));
+  TLAUNCH("stencil_dot", 64.0 * pts, launch_apply_dot<double>(L0, c->par(), k.phat, k.v, k.rhat, 0, c->cs, red));
+  TLAUNCH("bicg_s", 24.0 * nv, launch_bicg_s<double>(nv, k.r, k.v, k.s, c->cs, red));
+  TLAUNCH("cast", 12.0 * nv, launch_to_float(nv, k.s, f.r, c->cs));
+  TRY(vcycle<float>(c, f.r, f.shat));
+  TLAUNCH("cast", 12.0 * nv, launch_to_double(nv, f.shat, k.shat, c->cs));
+  TLAUNCH("stencil_dot", 64.0 * pts, launch_apply_dot<double>(L0, c->par(), k.shat, k.t, k.s, 1, c->cs, red));
+  TLAUNCH("bicg_update", 72.0 * nv,
+          launch_bicg_update<double>(nv, k.d, k.phat, k.shat, k.r, k.s, k.t, k.rhat, L0.diag,
+                                     L0.sc, c->cs, red));
+  TLAUNCH("bicg_p", 32.0 * nv, launch_bicg_p<double>(nv, k.p, k.r, k.v, cond, c->cs, red));
+  return POLAR_OK;
+}
+
 template <typename T>
 int bicg_begin(polar_ctx* c, CondHandle cond) {
   KVecs<T>& k = kvecs<T>(c);
@@ -737,7 +727,14 @@ int step_eager(polar_ctx* c, polar_step_stats& stats) {
   CUDA_TRY(cudaMemcpyAsync(c->X, c->U, c->nv() * sizeof(double), cudaMemcpyDeviceToDevice, c->st));
   stats.iters = 0;
   stats.refinements = 0;
+  stats.fp64_iters = 0;
   const StepParams& o = *c->sp_host;
+  // the same switch as k_refine_decide: a sweep that gained less than a factor 10, or an
+  // inner solve that broke down or hit its iteration limit, moves the mixed path to the
+  // FP64 Krylov solve for the rest of the step
+  bool use64 = false;
+  int inner_done = 0;
+  double prev = INFINITY;
   for (int sweep = 0;; ++sweep) {
     TRY(resid(c));
     TRY(read_scalars(c));
@@ -751,17 +748,36 @@ int step_eager(polar_ctx* c, polar_step_stats& stats) {
     if (sweep >= o.max_refine)
       return fail(POLAR_ENOCONV, "refinement did not reach the tolerance (scaled residual " +
                                      std::to_string(scaled) + ")");
-    TRY(bicg_begin<T>(c, 0));
+    if (sweep > 0 && (scaled > 0.1 * prev || inner_done == 2 || inner_done == 4)) use64 = true;
+    prev = scaled;
+    const bool x64 = use64 && sizeof(T) == 4;
+    if (x64) {
+      TRY(bicg_begin<double>(c, 0));
+    } else {
+      TRY(bicg_begin<T>(c, 0));
+    }
     int batch = 2;
     for (;;) {
-      for (int it = 0; it < batch; ++it) TRY(bicg_iteration<T>(c, 0));
+      for (int it = 0; it < batch; ++it) {
+        if (x64) {
+          TRY(bicg_iteration_x(c, 0));
+        } else {
+          TRY(bicg_iteration<T>(c, 0));
+        }
+      }
       TRY(read_scalars(c));
       if (c->ks_host->done != 0) break;
       batch = std::min(batch * 2, 8);
     }
     stats.iters += c->ks_host->iters;
+    if (x64) stats.fp64_iters += c->ks_host->iters;
+    inner_done = c->ks_host->done;
     if (c->ks_host->done == 3) return fail(POLAR_ENONFINITE, "non-finite value in the Krylov solve");
-    TRY(correct<T>(c));
+    if (x64) {
+      TRY(correct<double>(c));
+    } else {
+      TRY(correct<T>(c));
+    }
   }
   std::swap(c->U, c->X);
   c->graph_ok = false;  // the graph was captured with the previous U and X
@@ -805,6 +821,47 @@ int add_cond(cudaGraph_t g, const std::vector<cudaGraphNode_t>& deps,
   return POLAR_OK;
 }
 
+// Appends one inner solve to graph g after `deps`: scaled cast and BiCGStab set-up,
+// WHILE (iterate) { iteration }, bookkeeping and correction of X; *sinks receives its
+// last node and *iter_kernels the kernels of one iteration.  x64 selects the mixed path's
+// FP64 Krylov solve over the FP32 V-cycle.
+template <typename T>
+int append_inner(polar_ctx* c, cudaGraph_t g, const std::vector<cudaGraphNode_t>& deps,
+                 bool x64, std::vector<cudaGraphNode_t>* sinks, int64_t* iter_kernels) {
+  cudaGraphConditionalHandle hin;
+  CUDA_TRY(cudaGraphConditionalHandleCreate(&hin, g, 0, 0));
+  TRY(capture_begin(c, g, deps.empty() ? nullptr : deps.data(), deps.size()));
+  if (x64) {
+    TRY(bicg_begin<double>(c, (CondHandle)hin));
+  } else {
+    TRY(bicg_begin<T>(c, (CondHandle)hin));
+  }
+  std::vector<cudaGraphNode_t> s1;
+  TRY(capture_end(c, &s1));
+  cudaGraphNode_t nin;
+  cudaGraph_t bin;
+  TRY(add_cond(g, s1, hin, cudaGraphCondTypeWhile, &nin, &bin));
+  const int64_t a = c->launches;
+  TRY(capture_begin(c, bin, nullptr, 0));
+  if (x64) {
+    TRY(bicg_iteration_x(c, (CondHandle)hin));
+  } else {
+    TRY(bicg_iteration<T>(c, (CondHandle)hin));
+  }
+  TRY(capture_end(c, nullptr));
+  *iter_kernels = c->launches - a;
+  c->launches = a;
+  TRY(capture_begin(c, g, &nin, 1));
+  LAUNCH(launch_after_inner(c->cs, c->red()));
+  if (x64) {
+    TRY(correct<double>(c));
+  } else {
+    TRY(correct<T>(c));
+  }
+  TRY(capture_end(c, sinks));
+  return POLAR_OK;
+}
+
 // Appends one schedule-driven theta-step of this context to graph g (no dependencies on
 // the graph's other nodes):
 //   load step *kstep of the schedule -> IF (no earlier failure) {
@@ -816,14 +873,14 @@ template <typename T>
 int append_step(polar_ctx* c, cudaGraph_t g) {
   if (!c->cap) CUDA_TRY(cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking));
   const int64_t l0 = c->launches;
-  cudaGraphConditionalHandle hif, hout, hin;
+  cudaGraphConditionalHandle hif, hout;
   CUDA_TRY(cudaGraphConditionalHandleCreate(&hif, g, 0, 0));
   std::vector<cudaGraphNode_t> sinks;
   TRY(capture_begin(c, g, nullptr, 0));
   LAUNCH(launch_sched_begin(c->sched, c->kstep, c->sp, c->dout, (CondHandle)hif, c->cs, c->red()));
   TRY(capture_end(c, &sinks));
-  cudaGraphNode_t nif, nout, nin;
-  cudaGraph_t bif, bout, bin;
+  cudaGraphNode_t nif, nout;
+  cudaGraph_t bif, bout;
   TRY(add_cond(g, sinks, hif, cudaGraphCondTypeIf, &nif, &bif));
   const int64_t l1 = c->launches;
   CUDA_TRY(cudaGraphConditionalHandleCreate(&hout, bif, 0, 0));
@@ -836,23 +893,34 @@ int append_step(polar_ctx* c, cudaGraph_t g) {
   TRY(capture_end(c, &sinks));
   const int64_t l2 = c->launches;
   TRY(add_cond(bif, sinks, hout, cudaGraphCondTypeWhile, &nout, &bout));
-  CUDA_TRY(cudaGraphConditionalHandleCreate(&hin, bout, 0, 0));
-  TRY(capture_begin(c, bout, nullptr, 0));
-  TRY(bicg_begin<T>(c, (CondHandle)hin));
-  TRY(capture_end(c, &sinks));
-  TRY(add_cond(bout, sinks, hin, cudaGraphCondTypeWhile, &nin, &bin));
-  const int64_t l3 = c->launches;
-  TRY(capture_begin(c, bin, nullptr, 0));
-  TRY(bicg_iteration<T>(c, (CondHandle)hin));
-  TRY(capture_end(c, nullptr));
-  const int64_t l4 = c->launches;
-  TRY(capture_begin(c, bout, &nin, 1));
-  LAUNCH(launch_after_inner(c->cs, c->red()));
-  TRY(correct<T>(c));
+  int64_t iter_k = 0, iter64_k = 0;
+  std::vector<cudaGraphNode_t> body;
+  if (sizeof(T) == 8) {
+    TRY(append_inner<T>(c, bout, body, false, &body, &iter_k));
+  } else {
+    // mixed path: IF (FP32 refinement) { FP32 Krylov solve } then
+    //             IF (stalled) { FP64 Krylov solve over the FP32 V-cycle }
+    cudaGraphConditionalHandle h32, h64;
+    CUDA_TRY(cudaGraphConditionalHandleCreate(&h32, bout, 0, 0));
+    CUDA_TRY(cudaGraphConditionalHandleCreate(&h64, bout, 0, 0));
+    TRY(capture_begin(c, bout, nullptr, 0));
+    LAUNCH(launch_choose_inner((CondHandle)h32, (CondHandle)h64, c->cs, c->red()));
+    TRY(capture_end(c, &sinks));
+    cudaGraphNode_t n32, n64;
+    cudaGraph_t b32, b64;
+    TRY(add_cond(bout, sinks, h32, cudaGraphCondTypeIf, &n32, &b32));
+    std::vector<cudaGraphNode_t> none, tail;
+    TRY(append_inner<T>(c, b32, none, false, &tail, &iter_k));
+    TRY(add_cond(bout, std::vector<cudaGraphNode_t>{n32}, h64, cudaGraphCondTypeIf, &n64, &b64));
+    TRY(append_inner<T>(c, b64, none, true, &tail, &iter64_k));
+    body.assign(1, n64);
+  }
+  const int64_t l3 = c->launches, l4 = l3 + iter_k + iter64_k;
+  TRY(capture_begin(c, bout, body.data(), body.size()));
   TRY(resid(c));
   LAUNCH(launch_refine_decide(c->sp, (CondHandle)hout, c->cs, c->red()));
   TRY(capture_end(c, nullptr));
-  const int64_t l5 = c->launches;
+  const int64_t l5 = c->launches + iter_k + iter64_k;
   TRY(capture_begin(c, bif, &nout, 1));
   LAUNCH(launch_commit(c->nv(), c->U, c->X, c->cs, c->red()));
   LAUNCH(launch_sched_end(c->kstep, c->dout, c->cs, c->red()));
@@ -863,9 +931,11 @@ int append_step(polar_ctx* c, cudaGraph_t g) {
   TRY(capture_end(c, nullptr));
   const int64_t l7 = c->launches;
   // kernels per executed step: fixed ones, per refinement sweep, per Krylov iteration
+  // (a sweep runs one of the inner solves: the FP64 one's set-up kernels are as many)
   c->graph_kernels_fixed = (l1 - l0) + (l2 - l1) + (l6 - l5) + (l7 - l6);
-  c->graph_kernels_sweep = (l3 - l2) + (l5 - l4);
-  c->graph_kernels_iter = l4 - l3;
+  c->graph_kernels_sweep = (l3 - l2) + (l5 - l4) - (sizeof(T) == 8 ? 0 : 4);
+  c->graph_kernels_iter = iter_k;
+  c->graph_kernels_iter64 = iter64_k;
   c->launches = l0;  // captured launches run only when the graph is launched
   return POLAR_OK;
 }
@@ -1021,11 +1091,13 @@ int finish_schedule(polar_ctx* c, int32_t K, const double* t, polar_step_stats* 
       stats[k].iters = r.iters;
       stats[k].refinements = r.sweeps;
       stats[k].status = r.status;
+      stats[k].fp64_iters = r.iters64;
       stats[k].scaled_resid = r.scaled;
     }
     if (r.status != POLAR_ESTATE) {
       c->launches += 2 + c->graph_kernels_fixed + (int64_t)std::max(r.sweeps - 1, 0) * c->graph_kernels_sweep +
-                     (int64_t)r.iters * c->graph_kernels_iter;
+                     (int64_t)(r.iters - r.iters64) * c->graph_kernels_iter +
+                     (int64_t)r.iters64 * c->graph_kernels_iter64;
       c->cur_alpha = c->sched_host[k].alpha;  // the refresh state follows every executed step
       c->cur_beta = c->sched_host[k].beta;
     } else {
@@ -1178,11 +1250,10 @@ int polar_mesh_create(const polar_mesh_desc* d, polar_ctx** out) {
     chk(dalloc(c, &c->r64, nv));
     chk(dalloc(c, &c->io, c->N()));
     chk(dalloc(c, &c->sp, 1));
-    if (c->precision == POLAR_FP64) {
-      chk(alloc_kvecs(c, c->kv64));
-    } else {
-      chk(alloc_kvecs(c, c->kv32));
-    }
+    // FP64 Krylov vectors in both paths: the mixed path falls back to an FP64 Krylov
+    // solve over its FP32 V-cycle when its FP32 refinement stalls
+    chk(alloc_kvecs(c, c->kv64));
+    if (c->precision == POLAR_MIXED) chk(alloc_kvecs(c, c->kv32));
     chk(dalloc(c, &c->part, (size_t)kMaxBlocks * 4));
     chk(dalloc(c, &c->ks, 1));
   }

@@ -104,6 +104,14 @@ struct KrylovScalars {
   int pad2;
   double sm_tol;   // inner solve: stop when max_i |r_i| / S_ii of its residual is below
   double sm;       //   sm_tol (sm: the last value)
+  // mixed path: the FP32 refinement stalls where the FP32 operator cannot resolve the
+  // correction (stiff rings); the rest of the step then takes FP64 Krylov solves over
+  // the FP32 V-cycle
+  int use64;       // 1: the remaining sweeps of this step use the FP64 Krylov solve
+  int inner_done;  // `done` of the last inner solve
+  double prev_scaled;
+  int iters64;     // Krylov iterations of this step spent in FP64 Krylov solves
+  int pad3;
 };
 
 // Result of one step of a device-side schedule (graph mode).
@@ -111,7 +119,7 @@ struct StepOut {
   int iters;       // Krylov iterations of all inner solves
   int sweeps;      // FP64 residual evaluations
   int status;      // POLAR_OK, the step's error, or POLAR_ESTATE if skipped
-  int pad;
+  int iters64;     // of iters: FP64 Krylov iterations of the mixed path's fallback
   double scaled;   // final Jacobi-scaled residual
 };
 
@@ -201,15 +209,6 @@ int launch_restrict(const LevelView<T>& L, const LevelView<T>& C, const T* x, T*
 template <typename T>
 int launch_coarsest(const LevelView<T>& L, const T* b, T* x, Params p, const int* done,
                     cudaStream_t st);
-// the V-cycle restricted to levels l0..nlev-1 (the coarse end of the hierarchy) in a
-// single CTA; level l0 takes b0/x0, deeper levels bl[l]/xl[l].  Returns 0 when the levels
-// are too large for it (nothing launched).
-template <typename T>
-int launch_coarse_cycle(const LevelView<T>* L, int l0, int nlev, const T* b0, T* x0,
-                        T* const* bl, T* const* xl, Params p, const int* done, cudaStream_t st);
-// lines of one parity per level up to which the coarse cycle applies
-template <typename T>
-int coarse_cycle_lines();
 
 // ---- BiCGStab vector kernels
 template <typename T>
@@ -217,6 +216,8 @@ int launch_bicg_init(size_t nv, const T* r, T* rhat, T* p, T* v, T* x, const Ste
                      CondHandle cond, cudaStream_t st, Reduce red);
 template <typename T>
 int launch_bicg_s(size_t nv, const T* r, const T* v, T* s, cudaStream_t st, Reduce red);
+int launch_to_double(size_t n, const float* a, double* b, cudaStream_t st);
+int launch_choose_inner(CondHandle c32, CondHandle c64, cudaStream_t st, Reduce red);
 template <typename T>
 int launch_bicg_update(size_t nv, T* x, const T* phat, const T* shat, T* r, const T* s,
                        const T* t, const T* rhat, const T* diag, const double* sc,

@@ -457,10 +457,14 @@ __global__ void __launch_bounds__(kVT) k_bicg_s(size_t nv, const T* r, const T* 
     s[k] = fma(-alpha, v[k], r[k]);
 }
 
-// |r| / d in FP32 (a stopping test needs no more); padding entries have d = 0
+// |r| / d in FP32 (a stopping test needs no more), in FP64 when d is outside the FP32
+// range; padding entries have d = 0
 template <typename T>
 __device__ __forceinline__ float scaled_abs(T r, T d) {
-  return d > T(0) ? fabsf((float)r) / (float)d : 0.f;
+  if (!(d > T(0))) return 0.f;
+  const float df = (float)d;
+  if (df >= 1e-30f && df <= 1e30f) return fabsf((float)r) / df;
+  return (float)fmin(fabs((double)r) / (double)d, 3.0e38);
 }
 
 template <typename T>
@@ -547,6 +551,10 @@ int launch_bicg_p(size_t nv, T* p, const T* r, const T* v, CondHandle cond, cuda
 // ------------------------------------------------------------------ step control
 __global__ void k_step_begin(KrylovScalars* ks) {
   ks->failed = 0;
+  ks->use64 = 0;
+  ks->inner_done = 0;
+  ks->prev_scaled = INFINITY;
+  ks->iters64 = 0;
   ks->sweeps = 0;
   ks->iters_total = 0;
   ks->converged = 0;
@@ -569,6 +577,10 @@ __global__ void k_sched_begin(const StepParams* sched, const int* kstep, StepPar
   }
   *sp = sched[k];
   ks->failed = 0;
+  ks->use64 = 0;
+  ks->inner_done = 0;
+  ks->prev_scaled = INFINITY;
+  ks->iters64 = 0;
   ks->sweeps = 0;
   ks->iters_total = 0;
   ks->converged = 0;
@@ -584,7 +596,7 @@ int launch_sched_begin(const StepParams* sched, const int* kstep, StepParams* sp
 }
 
 __global__ void k_sched_end(const int* kstep, StepOut* out, KrylovScalars* ks) {
-  out[*kstep] = StepOut{ks->iters_total, ks->sweeps, ks->failed, 0, ks->scaled};
+  out[*kstep] = StepOut{ks->iters_total, ks->sweeps, ks->failed, ks->iters64, ks->scaled};
   if (ks->failed) ks->halt = 1;
 }
 int launch_sched_end(const int* kstep, StepOut* out, cudaStream_t st, Reduce red) {
@@ -615,9 +627,25 @@ __global__ void k_refine_decide(const StepParams* sp, CondHandle cond, KrylovSca
       ks->failed = -4;  // POLAR_ENOCONV
     } else {
       more = true;
+      // a correction that gained less than a factor 10, or an inner solve that broke
+      // down or ran out of iterations, switches the step to the FP64 Krylov solve
+      if (ks->sweeps > 1 && (scaled > 0.1 * ks->prev_scaled || ks->inner_done == 2 ||
+                             ks->inner_done == 4))
+        ks->use64 = 1;
     }
+    ks->prev_scaled = scaled;
   }
   set_cond(cond, more);
+}
+
+// Selects the inner solve of the next refinement sweep (mixed path).
+__global__ void k_choose_inner(CondHandle c32, CondHandle c64, const KrylovScalars* ks) {
+  set_cond(c32, ks->use64 == 0);
+  set_cond(c64, ks->use64 != 0);
+}
+int launch_choose_inner(CondHandle c32, CondHandle c64, cudaStream_t st, Reduce red) {
+  k_choose_inner<<<1, 1, 0, st>>>(c32, c64, red.ks);
+  return 1;
 }
 int launch_refine_decide(const StepParams* sp, CondHandle cond, cudaStream_t st, Reduce red) {
   k_refine_decide<<<1, 1, 0, st>>>(sp, cond, red.ks);
@@ -626,6 +654,8 @@ int launch_refine_decide(const StepParams* sp, CondHandle cond, cudaStream_t st,
 
 __global__ void k_after_inner(KrylovScalars* ks) {
   ks->iters_total += ks->iters;
+  if (ks->use64) ks->iters64 += ks->iters;
+  ks->inner_done = ks->done;
   if (ks->done == 3 && ks->failed == 0) ks->failed = -5;  // POLAR_ENONFINITE
 }
 int launch_after_inner(cudaStream_t st, Reduce red) {
@@ -673,6 +703,16 @@ int launch_scale_cast(size_t nv, const double* r, T* rs, cudaStream_t st, Reduce
 template <typename T>
 int launch_correct(size_t nv, double* x, const T* d, cudaStream_t st, Reduce red) {
   k_correct<T><<<grid_for(nv, kVT), kVT, 0, st>>>(nv, x, d, red.ks);
+  return 1;
+}
+
+__global__ void k_to_double(size_t n, const float* a, double* b) {
+  for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n;
+       k += (size_t)gridDim.x * blockDim.x)
+    b[k] = (double)a[k];
+}
+int launch_to_double(size_t n, const float* a, double* b, cudaStream_t st) {
+  k_to_double<<<grid_for(n, 256), 256, 0, st>>>(n, a, b);
   return 1;
 }
 

@@ -854,59 +854,6 @@ __global__ void __launch_bounds__(512) k_schur(LevelView<T> L, const StepParams*
   }
 }
 
-// The levels below a size bound, V-cycle and all, in one CTA: every phase of those levels
-// (zebra half-sweeps, restriction, coarsest solve, correction sweeps) runs between
-// __syncthreads() barriers instead of separate launches.  Level vectors stay in L2.
-template <typename T>
-struct CoarseCycleArgs {
-  LevelView<T> L[kMaxLevels];
-  T* b[kMaxLevels];  // b[0] is only read (it may be the caller's vector)
-  T* x[kMaxLevels];
-  int nlev;
-  Params par;
-  const int* done;
-};
-
-template <typename T, int P>
-__global__ void __launch_bounds__(512) k_coarse_cycle(CoarseCycleArgs<T> a) {
-  if (a.done && *a.done) return;
-  const T beta = (T)a.par[1];
-  const int RW = blockDim.x;
-  auto sweep = [&](int l, int parity, int mode) {
-    RingArgs<T> r{};
-    r.L = a.L[l];
-    r.C = a.L[l + 1];
-    r.b = a.b[l];
-    r.x = a.x[l];
-    r.X = (mode == RING_POST) ? a.x[l + 1] : nullptr;
-    r.par = a.par;
-    r.parity = parity;
-    r.mode = mode;
-    const int nl = parity ? r.L.sh.no : r.L.sh.ne;
-    for (int kb = 0; kb < nl; kb += RW) {
-      ring_body<T, P>(r, beta, kb);
-      __syncthreads();
-    }
-    if (parity == 0) {
-      relax_origin(r, beta);
-      __syncthreads();
-    }
-  };
-  for (int l = 0; l + 1 < a.nlev; ++l) {
-    sweep(l, 1, RING_PRE);
-    sweep(l, 0, RING_PRE);
-    RestrictArgs<T> ra{a.L[l], a.L[l + 1], a.x[l], a.b[l + 1], a.par, nullptr};
-    restrict_body(ra, beta, threadIdx.x + (size_t)RW * threadIdx.y, (size_t)RW * blockDim.y, true);
-    __syncthreads();
-  }
-  coarsest_body<T, P>(a.L[a.nlev - 1], a.b[a.nlev - 1], a.x[a.nlev - 1], beta);
-  __syncthreads();
-  for (int l = a.nlev - 2; l >= 0; --l) {
-    sweep(l, 0, RING_POST);
-    sweep(l, 1, RING_POST);
-  }
-}
-
 // ---------------------------------------------------------------------------------
 // launch configuration of the ring solves
 
@@ -1050,45 +997,6 @@ int launch_coarsest(const LevelView<T>& L, const T* b, T* x, Params p, const int
   return 1;
 }
 
-// Levels l0..nlev-1 of L (bl/xl indexed by level; level l0 uses b0/x0) in one CTA.
-// Returns 0 (nothing launched) when the levels are too large for one CTA.
-template <typename T>
-int launch_coarse_cycle(const LevelView<T>* L, int l0, int nlev, const T* b0, T* x0,
-                        T* const* bl, T* const* xl, Params p, const int* done, cudaStream_t st) {
-  CoarseCycleArgs<T> a{};
-  a.nlev = nlev - l0;
-  if (a.nlev < 1 || a.nlev > kMaxLevels) return 0;
-  for (int l = l0; l < nlev; ++l) {
-    a.L[l - l0] = L[l];
-    a.b[l - l0] = (l == l0) ? const_cast<T*>(b0) : bl[l];
-    a.x[l - l0] = (l == l0) ? x0 : xl[l];
-  }
-  a.par = p;
-  a.done = done;
-  const int n = L[l0].sh.n;
-  RingShape s;
-  s.RW = (sizeof(T) == 8) ? 4 : 8;
-  const int maxTW = 512 / s.RW;
-  s.P = 8;
-  if ((n + s.P - 1) / s.P > maxTW) s.P = 16;
-  if ((n + s.P - 1) / s.P > maxTW) return 0;
-  s.TW = 32;
-  while (s.TW < (n + s.P - 1) / s.P) s.TW <<= 1;
-  const size_t smem = ring_smem<T>(s);
-  if (s.P == 8) {
-    k_coarse_cycle<T, 8><<<1, dim3(s.RW, s.TW), smem, st>>>(a);
-  } else {
-    k_coarse_cycle<T, 16><<<1, dim3(s.RW, s.TW), smem, st>>>(a);
-  }
-  return 1;
-}
-
-// largest number of lines of one parity that the one-CTA coarse cycle takes per level
-template <typename T>
-int coarse_cycle_lines() {
-  return 2 * ((sizeof(T) == 8) ? 4 : 8);
-}
-
 template <typename T>
 static int launch_schur(const LevelView<T>& L, const StepParams* sp, cudaStream_t st) {
   RingShape s;
@@ -1120,10 +1028,7 @@ static int launch_schur(const LevelView<T>& L, const StepParams* sp, cudaStream_
   template int launch_restrict<T>(const LevelView<T>&, const LevelView<T>&, const T*, T*,      \
                                   Params, const int*, cudaStream_t);                          \
   template int launch_coarsest<T>(const LevelView<T>&, const T*, T*, Params, const int*,       \
-                                  cudaStream_t);                                              \
-  template int launch_coarse_cycle<T>(const LevelView<T>*, int, int, const T*, T*, T* const*,  \
-                                      T* const*, Params, const int*, cudaStream_t);           \
-  template int coarse_cycle_lines<T>();
+                                  cudaStream_t);
 
 POLAR_MG_INST(float)
 POLAR_MG_INST(double)

@@ -97,19 +97,49 @@ def test_steps_match_oracle(name, make, K, precision, tol):
         assert _rel(U, refs[k]) < tol, (name, k, _rel(U, refs[k]))
 
 
-def test_graph_step_equals_eager_step():
+def _stiff_rings():
+    """7 rings, the first at r = 1e-4, 16384 angles, one Crank-Nicolson step of dt = 0.2:
+    on ring 1 the angular couplings exceed the row sums by many orders more than 1 / eps32,
+    so the FP32 refinement cannot reach the FP64 tolerance there."""
+    r = np.concatenate([[0.0, 1e-4], np.linspace(1e-4, 1.0, 8)[1:]])
+    return pi.parabolic_problem(r, meshes.uniform_theta(16384), np.array([0.0, 0.2]), 0.5,
+                                name="stiff_rings")
+
+
+@pytest.mark.parametrize("precision,make", [(0, lambda: _small_continuity(37, 61, K=6)),
+                                            (1, lambda: _small_continuity(37, 61, K=6)),
+                                            (1, _stiff_rings)])
+def test_graph_step_equals_eager_step(precision, make):
     """A step run as one CUDA graph (device-side refinement and Krylov loops) and the same
-    step driven from the host (kernel timing on) execute the same kernels in the same order."""
-    prob = _small_continuity(37, 61, K=6)
+    step driven from the host (kernel timing on) execute the same kernels in the same order
+    (for the mixed path also when it falls back to the FP64 Krylov solve)."""
+    prob = make()
+    K = len(prob.t) - 1
     out = []
     for eager in (False, True):
-        ctx = driver.create(prob, P.POLAR_FP64)
+        ctx = driver.create(prob, precision)
         if eager:
             P.polar_timing_enable(ctx, True)
-        stats = driver.advance(ctx, prob, 0, 6)
+        stats = driver.advance(ctx, prob, 0, K)
         out.append((P.polar_get_state(ctx)[0], stats))
     assert np.array_equal(out[0][0], out[1][0])
     assert [s["iters"] for s in out[0][1]] == [s["iters"] for s in out[1][1]]
+    assert [s["fp64_iters"] for s in out[0][1]] == [s["fp64_iters"] for s in out[1][1]]
+
+
+def test_mixed_fallback_reaches_fp64_tolerance():
+    """Where FP32 refinement stalls, the mixed path finishes the step with FP64 Krylov
+    solves over its FP32 V-cycle (fp64_iters > 0) and meets the FP64 tolerance; the result
+    agrees with the oracle to max(1e-9, 20 kappa eps)."""
+    prob = _stiff_rings()
+    ref = po.run(prob, 1)
+    ctx = driver.create(prob, P.POLAR_MIXED)
+    st = driver.advance(ctx, prob, 0, 1)
+    assert st[0]["status"] == 0 and st[0]["scaled_resid"] <= 1e-14
+    assert st[0]["fp64_iters"] > 0, st[0]
+    U, _ = P.polar_get_state(ctx)
+    tol = max(1e-9, 20 * _kappa(prob, 0) * np.finfo(float).eps)
+    assert _rel(U, ref) < tol, (_rel(U, ref), tol)
 
 
 @pytest.mark.parametrize("timing", [False, True])
