@@ -123,6 +123,7 @@ struct polar_ctx {
   bool use_graph = true;
   int64_t graph_kernels_fixed = 0, graph_kernels_sweep = 0, graph_kernels_iter = 0;
   int64_t graph_kernels_iter64 = 0;  // mixed path: an FP64 Krylov iteration over the FP32 V-cycle
+  bool symmetric = false;  // S is symmetric (no drift): CG instead of BiCGStab
   int64_t generation = 0;         // bumped whenever a captured graph goes stale
   // ring-solve tile shapes per level, [mode * 2 + parity] (autotuned on first use)
   std::vector<std::array<RingShape, 4>> tiles;
@@ -658,6 +659,32 @@ int bicg_iteration(polar_ctx* c, CondHandle cond) {
   return POLAR_OK;
 }
 
+// One preconditioned CG iteration (symmetric S): z = M r, rho = r.z, p = z + beta p,
+// q = S p with alpha = rho / p.q, x += alpha p, r -= alpha q and the stopping test.  One
+// V-cycle per iteration where BiCGStab takes two.
+template <typename T>
+int cg_iteration(polar_ctx* c, CondHandle cond) {
+  KVecs<T>& k = kvecs<T>(c);
+  const LevelView<T>& L0 = views<T>(c)[0];
+  const Reduce red = c->red();
+  const size_t nv = c->nv();
+  const double B = sizeof(T), pts = (double)c->m * c->n;
+  TRY(vcycle<T>(c, k.r, k.phat));
+  TLAUNCH("cg_rho", 2 * B * nv, launch_cg_rho<T>(nv, k.r, k.phat, c->cs, red));
+  TLAUNCH("cg_p", 3 * B * nv, launch_cg_p<T>(nv, k.p, k.phat, c->cs, red));
+  // stencil with dot: reads p, diag, 4 couplings; writes q (7 words per point)
+  TLAUNCH("stencil_dot", 7 * B * pts, launch_apply_dot<T>(L0, c->par(), k.p, k.v, k.p, 0, c->cs, red));
+  TLAUNCH("cg_update", 7 * B * nv,
+          launch_cg_update<T>(nv, k.d, k.p, k.r, k.v, L0.diag, L0.sc, cond, c->cs, red));
+  return POLAR_OK;
+}
+
+// The inner Krylov iteration: CG when S is symmetric, BiCGStab otherwise.
+template <typename T>
+int krylov_iteration(polar_ctx* c, CondHandle cond) {
+  return c->symmetric ? cg_iteration<T>(c, cond) : bicg_iteration<T>(c, cond);
+}
+
 // Mixed path fallback: one BiCGStab iteration in FP64 (vectors, matrix, scalars) whose
 // preconditioner is the FP32 V-cycle, entered and left through casts.  The FP32
 // rounding of the preconditioner changes only how fast the iteration converges, not the
@@ -762,7 +789,7 @@ int step_eager(polar_ctx* c, polar_step_stats& stats) {
         if (x64) {
           TRY(bicg_iteration_x(c, 0));
         } else {
-          TRY(bicg_iteration<T>(c, 0));
+          TRY(krylov_iteration<T>(c, 0));
         }
       }
       TRY(read_scalars(c));
@@ -846,7 +873,7 @@ int append_inner(polar_ctx* c, cudaGraph_t g, const std::vector<cudaGraphNode_t>
   if (x64) {
     TRY(bicg_iteration_x(c, (CondHandle)hin));
   } else {
-    TRY(bicg_iteration<T>(c, (CondHandle)hin));
+    TRY(krylov_iteration<T>(c, (CondHandle)hin));
   }
   TRY(capture_end(c, nullptr));
   *iter_kernels = c->launches - a;
@@ -1188,6 +1215,22 @@ int advance(polar_ctx* c, int32_t K, const double* t, double theta, const double
   return finish_schedule(c, K, t, stats);
 }
 
+// Whether V L (hence S = alpha V + beta V L) is symmetric: every coupling equals its mirror
+// (radial faces, angular faces with the wrap, the origin's faces).  The conservative
+// scheme without drift stores one conductance per face on both sides, so the test is exact.
+bool is_symmetric(const HLevel& L) {
+  const int m = L.m, n = L.n;
+  for (int j = 0; j < n; ++j) {
+    if (L.o[j] != L.w[L.q(1, j)]) return false;
+    const int jm = (j == 0) ? n - 1 : j - 1;
+    for (int i = 1; i <= m; ++i) {
+      if (i > 1 && L.w[L.q(i, j)] != L.e[L.q(i - 1, j)]) return false;
+      if (L.s[L.q(i, j)] != L.nn[L.q(i, jm)]) return false;
+    }
+  }
+  return true;
+}
+
 }  // namespace
 
 namespace polar {
@@ -1323,6 +1366,7 @@ int polar_set_coeffs(polar_ctx* c, const polar_coeffs* k) {
   } else {
     assemble_paper(c->r, c->theta, K, H[0]);
   }
+  c->symmetric = is_symmetric(H[0]);
   for (int l = 0; l + 1 < c->nlev(); ++l) coarsen(H[l], H[l + 1]);
   for (int l = 0; l < c->nlev(); ++l) TRY(upload_level(c, l, H[l]));
   // sources in the split layout, scaled by the control volumes

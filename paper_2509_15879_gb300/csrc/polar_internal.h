@@ -216,6 +216,14 @@ int launch_bicg_init(size_t nv, const T* r, T* rhat, T* p, T* v, T* x, const Ste
                      CondHandle cond, cudaStream_t st, Reduce red);
 template <typename T>
 int launch_bicg_s(size_t nv, const T* r, const T* v, T* s, cudaStream_t st, Reduce red);
+// ---- conjugate gradients (symmetric systems)
+template <typename T>
+int launch_cg_rho(size_t nv, const T* r, const T* z, cudaStream_t st, Reduce red);
+template <typename T>
+int launch_cg_p(size_t nv, T* p, const T* z, cudaStream_t st, Reduce red);
+template <typename T>
+int launch_cg_update(size_t nv, T* x, const T* p, T* r, const T* q, const T* diag,
+                     const double* sc, CondHandle cond, cudaStream_t st, Reduce red);
 int launch_to_double(size_t n, const float* a, double* b, cudaStream_t st);
 int launch_choose_inner(CondHandle c32, CondHandle c64, cudaStream_t st, Reduce red);
 template <typename T>

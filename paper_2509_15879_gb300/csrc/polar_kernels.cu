@@ -548,6 +548,99 @@ int launch_bicg_p(size_t nv, T* p, const T* r, const T* v, CondHandle cond, cuda
   return 1;
 }
 
+// ------------------------------------------------------------------ conjugate gradients
+// Preconditioned CG for symmetric systems (no drift: S = alpha V + beta V L is symmetric
+// positive definite and the V(1,1) cycle with its zebra smoother in mirrored order is a
+// symmetric preconditioner).  One iteration: z = M r (V-cycle), rho = r.z and
+// beta = rho / rho_prev (k_cg_rho), p = z + beta p (k_cg_p), q = S p with
+// alpha = rho / p.q (the stencil's DOTV mode with d1 = p), then x += alpha p,
+// r -= alpha q and the stopping test (k_cg_update).  Set-up is k_bicg_init (x = 0, the
+// stopping threshold; its p = r is scaled by beta = 0 in the first iteration).
+template <typename T>
+__global__ void __launch_bounds__(kVT) k_cg_rho(size_t nv, const T* r, const T* z, Reduce red) {
+  if (red.ks->done) return;
+  double acc[1] = {0.0};
+  for (size_t k = blockIdx.x * (size_t)kVT + threadIdx.x; k < nv; k += (size_t)gridDim.x * kVT)
+    acc[0] = fma((double)r[k], (double)z[k], acc[0]);
+  block_reduce<1, 1>(acc);
+  if (!publish_and_arrive<1>(acc, red.part, &red.ks->counter)) return;
+  double tot[1];
+  grid_totals<1, 1>(red.part, tot);
+  if (threadIdx.x != 0) return;
+  KrylovScalars* ks = red.ks;
+  const double rho = tot[0];
+  if (!isfinite(rho)) {
+    ks->done = 3;
+  } else if (rho == 0.0) {
+    ks->done = 2;
+  } else {
+    ks->beta = (ks->iters == 0) ? 0.0 : rho / ks->rho;
+    ks->rho = rho;
+  }
+  ks->counter = 0;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kVT) k_cg_p(size_t nv, T* p, const T* z, const KrylovScalars* ks) {
+  if (ks->done) return;
+  const T beta = (T)ks->beta;
+  for (size_t k = blockIdx.x * (size_t)kVT + threadIdx.x; k < nv; k += (size_t)gridDim.x * kVT)
+    p[k] = fma(beta, p[k], z[k]);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kVT) k_cg_update(size_t nv, T* x, const T* p, T* r, const T* q,
+                                                   const T* diag, const double* sc, Reduce red,
+                                                   CondHandle cond) {
+  if (red.ks->done) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) set_cond(cond, false);
+    return;
+  }
+  const T alpha = (T)red.ks->alpha;
+  float sm = 0.f;
+  for (size_t k = blockIdx.x * (size_t)kVT + threadIdx.x; k < nv; k += (size_t)gridDim.x * kVT) {
+    x[k] = fma(alpha, p[k], x[k]);
+    const T rn = fma(-alpha, q[k], r[k]);
+    r[k] = rn;
+    sm = fmaxf(sm, scaled_abs<T>(rn, k == 0 ? (T)sc[0] : diag[k]));
+  }
+  double acc[1] = {isfinite(sm) ? (double)sm : INFINITY};
+  block_reduce<1, 0>(acc);
+  if (!publish_and_arrive<1>(acc, red.part, &red.ks->counter)) return;
+  double tot[1];
+  grid_totals<1, 0>(red.part, tot);
+  if (threadIdx.x != 0) return;
+  KrylovScalars* ks = red.ks;
+  ks->sm = tot[0];
+  ks->iters += 1;
+  if (!isfinite(tot[0])) {
+    ks->done = 3;
+  } else if (tot[0] <= ks->sm_tol) {
+    ks->done = 1;
+  } else if (ks->iters >= ks->max_iter) {
+    ks->done = 4;
+  }
+  ks->counter = 0;
+  set_cond(cond, ks->done == 0);
+}
+
+template <typename T>
+int launch_cg_rho(size_t nv, const T* r, const T* z, cudaStream_t st, Reduce red) {
+  k_cg_rho<T><<<grid_for(nv, kVT), kVT, 0, st>>>(nv, r, z, red);
+  return 1;
+}
+template <typename T>
+int launch_cg_p(size_t nv, T* p, const T* z, cudaStream_t st, Reduce red) {
+  k_cg_p<T><<<grid_for(nv, kVT), kVT, 0, st>>>(nv, p, z, red.ks);
+  return 1;
+}
+template <typename T>
+int launch_cg_update(size_t nv, T* x, const T* p, T* r, const T* q, const T* diag,
+                     const double* sc, CondHandle cond, cudaStream_t st, Reduce red) {
+  k_cg_update<T><<<grid_for(nv, kVT), kVT, 0, st>>>(nv, x, p, r, q, diag, sc, red, cond);
+  return 1;
+}
+
 // ------------------------------------------------------------------ step control
 __global__ void k_step_begin(KrylovScalars* ks) {
   ks->failed = 0;
@@ -790,6 +883,10 @@ int launch_unpack(const Shape& sh, const double* in, const double* div, double* 
                                      const T*, const T*, const double*, cudaStream_t, Reduce); \
   template int launch_bicg_p<T>(size_t, T*, const T*, const T*, CondHandle, cudaStream_t,      \
                                 Reduce);                                                       \
+  template int launch_cg_rho<T>(size_t, const T*, const T*, cudaStream_t, Reduce);            \
+  template int launch_cg_p<T>(size_t, T*, const T*, cudaStream_t, Reduce);                      \
+  template int launch_cg_update<T>(size_t, T*, const T*, T*, const T*, const T*, const double*, \
+                                   CondHandle, cudaStream_t, Reduce);                          \
   template int launch_scale_cast<T>(size_t, const double*, T*, cudaStream_t, Reduce);          \
   template int launch_correct<T>(size_t, double*, const T*, cudaStream_t, Reduce);
 
