@@ -13,7 +13,9 @@ its level (set outside the timed region); with K >= 1000 the schedule runs
 consecutively.  L2 is flushed (a 512 MB write) before every timed step.
 
 value  = grid-point updates (N per step) / device time of the K steps, summed over ranks
-         (replicas: every rank advances its own copy; no collective on the data path)
+         (replicas: every rank advances its own copy; no collective on the data path);
+         the headline path is the mixed one (FP32 inner solves, FP64 residual and update,
+         same FP64 tolerance), the FP64 path is timed beside it on the same steps
 e2e    = the same through the C ABI with the state copied in from pinned host memory
          and out to pinned host memory inside every timed step
 roofline: the dominant kernel class's algorithmic bytes / its event-timed duration
@@ -534,7 +536,8 @@ def main():
     ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["native", "reference"], default="native")
-    ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64")
+    ap.add_argument("--precision", choices=["fp64", "mixed"], default="mixed",
+                    help="headline path; --compare 1 also times the other one")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--compare", type=int, default=1,

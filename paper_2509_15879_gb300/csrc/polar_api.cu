@@ -483,7 +483,11 @@ template <typename T>
 int vcycle(polar_ctx* c, const T* b, T* x) {
   const std::vector<LevelView<T>>& L = views<T>(c);
   const int nl = c->nlev();
-  const int* done = &c->ks->done;
+  // Driven from the host, iterations run in batches past convergence, and the V-cycle's
+  // kernels test the solve's `done` flag.  In a captured graph the loop stops exactly at
+  // convergence, so they skip that dependent load (a cycle that follows a breakdown only
+  // writes scratch vectors that the next solve overwrites).
+  const int* done = (c->cs == c->st) ? &c->ks->done : nullptr;
   const double B = sizeof(T);
   const Params par = c->par();
   auto bof = [&](int l) { return l == 0 ? b : static_cast<const T*>(c->lv[l].b); };

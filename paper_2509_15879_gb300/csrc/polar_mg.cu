@@ -550,7 +550,10 @@ __device__ void solve_lines(int n, bool valid, Rhs rhs, Fac fac, T vf, T inv, Ou
   const int crank = (int)cl.block_rank();
   const int gc = crank * TW + c;
   const int j0 = gc * P;
-  T v[P], fl[P], fu[P], fc[P];
+  // the Sherman-Morrison vector is loaded with the rest when registers allow (short
+  // chunks), so that the final correction waits on no memory access
+  constexpr bool kPrefetchQ = (P * sizeof(T) <= 32);
+  T v[P], fl[P], fu[P], fc[P], fqv[kPrefetchQ ? P : 1];
 #pragma unroll
   for (int p = 0; p < P; ++p) {
     const int j = j0 + p;
@@ -559,6 +562,7 @@ __device__ void solve_lines(int n, bool valid, Rhs rhs, Fac fac, T vf, T inv, Ou
     fl[p] = in ? fac.l(j) : T(0);
     fu[p] = in ? fac.ui(j) : T(0);
     fc[p] = in ? fac.cu(j) : T(0);
+    if constexpr (kPrefetchQ) fqv[p] = in ? fac.q(j) : T(0);
   }
   // forward substitution y_j = d_j - l_j y_{j-1}  (padding: l = 0, d = 0 -> identity-like)
   T A = T(1), B = T(0);
@@ -645,7 +649,15 @@ __device__ void solve_lines(int n, bool valid, Rhs rhs, Fac fac, T vf, T inv, Ou
 #pragma unroll
   for (int p = 0; p < P; ++p) {
     const int j = j0 + p;
-    if (valid && j < n) out(j, fma(-sigma, fac.q(j), v[p]));
+    if (valid && j < n) {
+      T qj;
+      if constexpr (kPrefetchQ) {
+        qj = fqv[p];
+      } else {
+        qj = fac.q(j);
+      }
+      out(j, fma(-sigma, qj, v[p]));
+    }
   }
   if (CS > 1) cl.sync();  // no CTA leaves while another may still read its shared memory
 }
