@@ -1091,6 +1091,10 @@ int load_schedule(polar_ctx* c, int32_t K, const double* t, double theta, const 
     CUDA_TRY(cudaMallocHost((void**)&c->sched_host, (size_t)cap * sizeof(StepParams)));
     CUDA_TRY(cudaMallocHost((void**)&c->out_host, (size_t)cap * sizeof(StepOut)));
     c->sched_cap = cap;
+    // step graphs (this context's and any batch graph holding it) captured the old
+    // schedule and result arrays: they must be captured again
+    c->graph_ok = false;
+    c->generation += 1;
   }
   const int Q = c->nsrc;
   double pa = c->cur_alpha, pb = c->cur_beta;

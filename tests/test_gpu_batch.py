@@ -57,3 +57,20 @@ def test_batch_failure_is_per_instance():
         assert row[0]["status"] == P.POLAR_ENOCONV
         assert row[1]["status"] == P.POLAR_ESTATE
         assert P.polar_get_state(c)[1] == p.t[2]
+
+
+def test_batch_longer_schedule_after_a_short_one():
+    """The batch graph is captured again when a longer schedule grows the instances'
+    schedule arrays (it holds their device addresses)."""
+    probs = _instances()[:3]
+    ctxs = [driver.create(p, P.POLAR_MIXED) for p in probs]
+    batch = P.polar_batch_create(ctxs)
+    driver.batch_advance(batch, probs, 0, 1)
+    stats, rc = driver.batch_advance(batch, probs, 1, 5)
+    assert rc == 0
+    assert all(s["status"] == 0 and s["iters"] > 0 for row in stats for s in row)
+    for p, c in zip(probs, ctxs):
+        U, t = P.polar_get_state(c)
+        assert t == p.t[5]
+        ref = po.run(p, 5)
+        assert np.max(np.abs(U - ref)) / np.max(np.abs(ref)) < 1e-9

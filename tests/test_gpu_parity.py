@@ -189,3 +189,19 @@ def test_long_rings(precision, m, n):
         driver.advance(ctx, prob, k, k + 1)
         U, _ = P.polar_get_state(ctx)
         assert _rel(U, refs[k]) < tol, (m, n, k, _rel(U, refs[k]))
+
+
+def test_longer_schedule_after_a_short_one():
+    """A schedule longer than any before grows the device schedule arrays; the step graph
+    captured for the shorter one must not be reused with the old arrays."""
+    prob = _small_continuity(24, 40, K=12)
+    refs = _oracle_levels(prob, 12)
+    ctx = driver.create(prob, P.POLAR_FP64)
+    driver.advance(ctx, prob, 0, 1)
+    driver.advance(ctx, prob, 1, 3)
+    stats = driver.advance(ctx, prob, 3, 12)
+    assert [s["status"] for s in stats] == [0] * 9
+    assert all(s["iters"] > 0 for s in stats)
+    U, t = P.polar_get_state(ctx)
+    assert t == prob.t[12]
+    assert _rel(U, refs[11]) < 1e-12
