@@ -753,6 +753,7 @@ int rhs(polar_ctx* c) {
 template <typename T>
 int step_eager(polar_ctx* c, polar_step_stats& stats) {
   c->cs = c->st;
+  LAUNCH(launch_step_begin(c->cs, c->red()));  // step flags a graph run may have left set
   TRY(rhs(c));
   if (c->sp_host->do_refresh) TRY(launch_refresh_all<T>(c));
   CUDA_TRY(cudaMemcpyAsync(c->X, c->U, c->nv() * sizeof(double), cudaMemcpyDeviceToDevice, c->st));
@@ -779,7 +780,7 @@ int step_eager(polar_ctx* c, polar_step_stats& stats) {
     if (sweep >= o.max_refine)
       return fail(POLAR_ENOCONV, "refinement did not reach the tolerance (scaled residual " +
                                      std::to_string(scaled) + ")");
-    if (sweep > 0 && (scaled > 0.1 * prev || inner_done == 2 || inner_done == 4)) use64 = true;
+    if (sweep > 0 && (scaled > 0.1 * prev || inner_done >= 2)) use64 = true;
     prev = scaled;
     const bool x64 = use64 && sizeof(T) == 4;
     if (x64) {
@@ -803,11 +804,16 @@ int step_eager(polar_ctx* c, polar_step_stats& stats) {
     stats.iters += c->ks_host->iters;
     if (x64) stats.fp64_iters += c->ks_host->iters;
     inner_done = c->ks_host->done;
-    if (c->ks_host->done == 3) return fail(POLAR_ENONFINITE, "non-finite value in the Krylov solve");
-    if (x64) {
-      TRY(correct<double>(c));
-    } else {
-      TRY(correct<T>(c));
+    // as k_after_inner / k_correct: a non-finite FP32 solve of the mixed path is dropped
+    // and the step moves to the FP64 Krylov solve; a non-finite FP64 solve fails
+    if (c->ks_host->done == 3 && (x64 || sizeof(T) == 8))
+      return fail(POLAR_ENONFINITE, "non-finite value in the Krylov solve");
+    if (c->ks_host->done != 3) {
+      if (x64) {
+        TRY(correct<double>(c));
+      } else {
+        TRY(correct<T>(c));
+      }
     }
   }
   std::swap(c->U, c->X);
@@ -883,7 +889,7 @@ int append_inner(polar_ctx* c, cudaGraph_t g, const std::vector<cudaGraphNode_t>
   *iter_kernels = c->launches - a;
   c->launches = a;
   TRY(capture_begin(c, g, &nin, 1));
-  LAUNCH(launch_after_inner(c->cs, c->red()));
+  LAUNCH(launch_after_inner(sizeof(T) == 4 && !x64, c->cs, c->red()));
   if (x64) {
     TRY(correct<double>(c));
   } else {

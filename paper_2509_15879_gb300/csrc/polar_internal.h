@@ -248,7 +248,7 @@ int launch_sched_next(int* kstep, cudaStream_t st);
 // after an FP64 residual: converged / failed / continue; sets `cond` to continue
 int launch_refine_decide(const StepParams* sp, CondHandle cond, cudaStream_t st, Reduce red);
 // after an inner solve: count its iterations, fail on a non-finite value
-int launch_after_inner(cudaStream_t st, Reduce red);
+int launch_after_inner(int tolerant, cudaStream_t st, Reduce red);
 // U = X when the step converged
 int launch_commit(size_t nv, double* U, const double* X, cudaStream_t st, Reduce red);
 

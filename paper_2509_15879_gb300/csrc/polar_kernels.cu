@@ -722,8 +722,7 @@ __global__ void k_refine_decide(const StepParams* sp, CondHandle cond, KrylovSca
       more = true;
       // a correction that gained less than a factor 10, or an inner solve that broke
       // down or ran out of iterations, switches the step to the FP64 Krylov solve
-      if (ks->sweeps > 1 && (scaled > 0.1 * ks->prev_scaled || ks->inner_done == 2 ||
-                             ks->inner_done == 4))
+      if (ks->sweeps > 1 && (scaled > 0.1 * ks->prev_scaled || ks->inner_done >= 2))
         ks->use64 = 1;
     }
     ks->prev_scaled = scaled;
@@ -745,14 +744,17 @@ int launch_refine_decide(const StepParams* sp, CondHandle cond, cudaStream_t st,
   return 1;
 }
 
-__global__ void k_after_inner(KrylovScalars* ks) {
+// tolerant: the solve was the mixed path's FP32 one, whose non-finite end (FP32 overflow
+// on a near-singular ring) only discards its correction and moves the step to the FP64
+// Krylov solve; a non-finite FP64 solve fails the step.
+__global__ void k_after_inner(KrylovScalars* ks, int tolerant) {
   ks->iters_total += ks->iters;
   if (ks->use64) ks->iters64 += ks->iters;
   ks->inner_done = ks->done;
-  if (ks->done == 3 && ks->failed == 0) ks->failed = -5;  // POLAR_ENONFINITE
+  if (ks->done == 3 && !tolerant && ks->failed == 0) ks->failed = -5;  // POLAR_ENONFINITE
 }
-int launch_after_inner(cudaStream_t st, Reduce red) {
-  k_after_inner<<<1, 1, 0, st>>>(red.ks);
+int launch_after_inner(int tolerant, cudaStream_t st, Reduce red) {
+  k_after_inner<<<1, 1, 0, st>>>(red.ks, tolerant);
   return 1;
 }
 
@@ -783,7 +785,7 @@ __global__ void __launch_bounds__(kVT) k_scale_cast(size_t nv, const double* r, 
 template <typename T>
 __global__ void __launch_bounds__(kVT) k_correct(size_t nv, double* x, const T* d,
                                                  const KrylovScalars* ks) {
-  if (ks->failed) return;
+  if (ks->failed || ks->inner_done == 3) return;  // no non-finite correction reaches x
   const double s = ks->rmax;
   for (size_t k = blockIdx.x * (size_t)kVT + threadIdx.x; k < nv; k += (size_t)gridDim.x * kVT)
     x[k] = fma(s, (double)d[k], x[k]);

@@ -188,8 +188,20 @@ __global__ void __launch_bounds__(RF * TF) k_refresh(RefreshArgs A) {
   auto bdiag = [&](size_t q) {
     return alpha * L.vol[q] + beta * (L.rs[q] - L.w[q] - L.e[q] - L.s[q] - L.nn[q]);
   };
+  // Diagonal the ring is factored with.  FP64 factors: the ring's own.  FP32 factors (the
+  // mixed path's smoother): where the upwinded drift diverges, a ring's diagonal can fall
+  // to or below the sum of its two angular couplings (no longer diagonally dominant), and
+  // an FP32 solve of that ring -- then the whole V-cycle -- goes wild; such a diagonal is
+  // raised to (1 + 1e-7) times the couplings.  The operator itself is untouched: only the
+  // smoother's rings are shifted, and diagonally dominant rings keep their own diagonal.
+  auto bfac = [&](size_t q) {
+    const double bd = bdiag(q);
+    if (sizeof(T) == 8) return bd;
+    const double off = beta * (fabs(L.s[q]) + fabs(L.nn[q]));
+    return bd > off ? bd : (1.0 + 1e-7) * off;
+  };
   // corner terms of the periodic system
-  const double b0 = valid ? bdiag(q0) : 1.0;
+  const double b0 = valid ? bfac(q0) : 1.0;
   const double gamma = -b0;
   const double a0 = valid ? beta * L.s[q0] : 0.0;
   const double cn1 = valid ? beta * L.nn[q0 + (size_t)(n - 1) * ld] : 0.0;
@@ -212,7 +224,7 @@ __global__ void __launch_bounds__(RF * TF) k_refresh(RefreshArgs A) {
     for (int j = j0; j < j1; ++j) {
       const size_t q = q0 + (size_t)j * ld;
       const double a = (j > 0) ? beta * L.s[q] : 0.0;
-      const M2 mj{bmod(j, bdiag(q)), -a * cprev, 1.0, 0.0};
+      const M2 mj{bmod(j, bfac(q)), -a * cprev, 1.0, 0.0};
       m = comb(m, mj);
       if (((j - j0) & 3) == 3) m = renorm(m);
       cprev = cc(j);
@@ -233,7 +245,7 @@ __global__ void __launch_bounds__(RF * TF) k_refresh(RefreshArgs A) {
     const double a = (j > 0) ? beta * L.s[q] : 0.0;
     const double c = cc(j);
     const double lj = a * uiprev;
-    const double ui = 1.0 / (bmod(j, bd) - lj * cprev);
+    const double ui = 1.0 / (bmod(j, bfac(q)) - lj * cprev);
     fl[q] = (T)lj;
     fui[q] = (T)ui;
     fcu[q] = (T)(c * ui);
