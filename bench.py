@@ -59,6 +59,33 @@ def env_int(name, default):
         return default
 
 
+# ------------------------------------------------------------------------- replicas
+# With N ranks every rank advances its own replica (or its share of independent
+# instances); nothing crosses ranks on the data path, only these scalar reductions of the
+# timing and the update counts.
+def shard(count, rank, world):
+    """Independent instances of this rank: rank, rank + world, rank + 2 world, ..."""
+    return list(range(rank, count, world))
+
+
+def _reduce(dist, vals, op):
+    import torch
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(v) for v in vals], device=dev, dtype=torch.float64)
+    dist.all_reduce(t, op=op)
+    return [float(x) for x in t.tolist()]
+
+
+def max_over_ranks(dist, v):
+    """The slowest rank's time (v itself on one rank)."""
+    return v if dist is None else _reduce(dist, [v], dist.ReduceOp.MAX)[0]
+
+
+def sum_over_ranks(dist, vals):
+    """Whole-job totals of per-rank counts."""
+    return list(vals) if dist is None else _reduce(dist, vals, dist.ReduceOp.SUM)
+
+
 def measured_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -281,12 +308,8 @@ def run_native(args):
         launches = P.polar_kernel_launches(ctx) - launches0
         kstats = P.polar_timing_query(ctx) if timers else {}
         P.polar_timing_enable(ctx, False)
-        dev_ms = sum(a.elapsed_time(b) for a, b in ev)
+        dev_ms = max_over_ranks(dist, sum(a.elapsed_time(b) for a, b in ev))
         U_last, t_last = P.polar_get_state(ctx)
-        if dist is not None:
-            tt = torch.tensor([dev_ms], device="cuda", dtype=torch.float64)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            dev_ms = float(tt.item())
         return dict(ctx=ctx, dev_ms=dev_ms, wall=wall, launches=launches, kstats=kstats,
                     iters=float(np.mean(iters)), refs=float(np.mean(refs)), U=U_last, t=t_last,
                     set_level=set_level, checkpoints=checkpoints)
@@ -344,10 +367,7 @@ def run_native(args):
         e1.record(stream)
         e1.synchronize()
         e_ms += e0.elapsed_time(e1)
-    if dist is not None:
-        tt = torch.tensor([e_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e_ms = float(tt.item())
+    e_ms = max_over_ranks(dist, e_ms)
     e2e_value = prob.N * len(ke) * world / (e_ms * 1e-3)
 
     # ---- roofline of the dominant kernel class
@@ -424,7 +444,7 @@ def run_batch(args):
     K_sched = 500
     count = args.instances
     # replicas: rank r takes instances r, r + world, ... (independent instances, no collective)
-    mine = list(range(rank, count, world))
+    mine = shard(count, rank, world)
     t0 = time.perf_counter()
     probs = [pi.config4_instance(i, K=K_sched) for i in mine]
     gen_s = time.perf_counter() - t0
@@ -451,11 +471,7 @@ def run_batch(args):
         e1.record(stream)
         torch.cuda.synchronize()
         clk = clocks.stop()
-        ms = e0.elapsed_time(e1)
-        if dist is not None:
-            tt = torch.tensor([ms], device="cuda", dtype=torch.float64)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            ms = float(tt.item())
+        ms = max_over_ranks(dist, e0.elapsed_time(e1))
         states = [P.polar_get_state(c)[0] for c in ctxs]
         done = [sum(1 for s in row if s["status"] == 0) for row in stats]
         failed = [mine[i] for i, row in enumerate(stats) if any(s["status"] != 0 for s in row)]
@@ -463,16 +479,12 @@ def run_batch(args):
         iters = float(np.mean([s["iters"] for s in ok])) if ok else 0.0
         # only the steps an instance completed count as updates (a failed step halts the
         # rest of that instance's schedule; its state stays at the last committed level)
-        updates = float(sum(p.N * d for p, d in zip(probs, done)))
+        updates = sum_over_ranks(dist, [sum(p.N * d for p, d in zip(probs, done))])[0]
         launches = sum(P.polar_kernel_launches(c) for c in ctxs) - launches0
         return ms, K, states, iters, clk, launches, updates, failed
 
     ms, K, st_main, iters, clk, launches, updates, failed = run(precision)
-    pts = sum(p.N for p in probs)
-    if dist is not None:
-        tt = torch.tensor([float(pts), updates], device="cuda", dtype=torch.float64)
-        dist.all_reduce(tt)
-        pts, updates = float(tt[0].item()), float(tt[1].item())
+    pts = sum_over_ranks(dist, [sum(p.N for p in probs)])[0]
     value = updates / (ms * 1e-3)
     compare = None
     if args.compare:
