@@ -117,7 +117,21 @@ int polar_set_coeffs(polar_ctx* ctx, const polar_coeffs* coeffs);
 int polar_set_state(polar_ctx* ctx, const double* u, double t, int32_t memory);
 int polar_get_state(polar_ctx* ctx, double* u, double* t, int32_t memory);
 
-/* Solver controls (NULL -> defaults).
+/* How a step is solved.  The new level X starts from U; the FP64 residual of the implicit
+ * system is formed, and while its Jacobi-scaled max norm exceeds tol the residual (scaled
+ * by its max norm) is handed to an inner Krylov solve whose correction is added to X in
+ * FP64.  The inner solve is preconditioned by one V-cycle of a multigrid that coarsens
+ * the radius only, smooths whole rings (periodic tridiagonal solves) and eliminates the
+ * odd rings' radial couplings exactly.  It is conjugate gradients when the assembled
+ * operator is symmetric (the conservative scheme without drift), BiCGStab otherwise.
+ * POLAR_FP64 runs everything in FP64 (one inner solve normally suffices); POLAR_MIXED
+ * runs the inner solve (vectors, operator, V-cycle) in FP32 and the residual and update
+ * in FP64, and after a sweep that gains less than a factor 10 (FP32 cannot resolve rows
+ * whose couplings exceed their row sums by about 1/eps32, e.g. long rings next to the
+ * origin) finishes the step with FP64 BiCGStab preconditioned by the FP32 V-cycle.
+ * Both paths stop at the same FP64 tolerance.
+ *
+ * Solver controls (NULL -> defaults).
  *   tol         stop when max_i |r_i| / A_ii <= tol * max_i |U_i|, r = e - A U
  *               (Jacobi-scaled residual of the implicit system); default 1e-14
  *   max_iter    Krylov iterations per solve (FP64) or per inner solve (MIXED); default 500
