@@ -350,7 +350,7 @@ int alloc_levels(polar_ctx* c) {
         d.x = x;
       }
     }
-    wsz += 3 * nv;
+    wsz += 2 * nv;  // refresh workspace: y and the pivot reciprocals
   }
   TRY(dalloc(c, &c->ws, wsz));
   c->v64.resize(c->nlev());

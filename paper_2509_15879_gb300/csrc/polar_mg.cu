@@ -56,8 +56,7 @@ struct RefreshLevel {
   void* fq;
   void* fring;
   void* fz;
-  double* ws;  // 3 nv doubles: forward values, pivot reciprocals, q (FP64)
-  int coarsest;
+  double* ws;  // 2 nv doubles: forward values y and pivot reciprocals (FP64)
   int ring0;   // first CTA of this level in the refresh grid
 };
 constexpr int kMaxLevels = 20;
@@ -337,8 +336,7 @@ int launch_refresh(const LevelView<double>* L64, LevelView<T>* LT, int nlev,
     r.fring = LT[l].fring;
     r.fz = LT[l].fz;
     r.ws = ws + wofs;
-    wofs += 3 * d.sh.nv;
-    r.coarsest = (l == nlev - 1);
+    wofs += 2 * d.sh.nv;
     r.ring0 = rings;  // first CTA of this level (groups of RF rings, odd block first)
     rings += (d.sh.no + RF - 1) / RF + (d.sh.ne + RF - 1) / RF;
   }
