@@ -919,7 +919,6 @@ int append_step(polar_ctx* c, cudaGraph_t g) {
   cudaGraphNode_t nif, nout;
   cudaGraph_t bif, bout;
   TRY(add_cond(g, sinks, hif, cudaGraphCondTypeIf, &nif, &bif));
-  const int64_t l1 = c->launches;
   CUDA_TRY(cudaGraphConditionalHandleCreate(&hout, bif, 0, 0));
   TRY(capture_begin(c, bif, nullptr, 0));
   TRY(rhs(c));
@@ -952,25 +951,24 @@ int append_step(polar_ctx* c, cudaGraph_t g) {
     TRY(append_inner<T>(c, b64, none, true, &tail, &iter64_k));
     body.assign(1, n64);
   }
-  const int64_t l3 = c->launches, l4 = l3 + iter_k + iter64_k;
   TRY(capture_begin(c, bout, body.data(), body.size()));
   TRY(resid(c));
   LAUNCH(launch_refine_decide(c->sp, (CondHandle)hout, c->cs, c->red()));
   TRY(capture_end(c, nullptr));
-  const int64_t l5 = c->launches + iter_k + iter64_k;
+  const int64_t l3 = c->launches;  // (append_inner leaves the iteration kernels out)
   TRY(capture_begin(c, bif, &nout, 1));
   LAUNCH(launch_commit(c->nv(), c->U, c->X, c->cs, c->red()));
   LAUNCH(launch_sched_end(c->kstep, c->dout, c->cs, c->red()));
   TRY(capture_end(c, nullptr));
-  const int64_t l6 = c->launches;
   TRY(capture_begin(c, g, &nif, 1));
   LAUNCH(launch_sched_next(c->kstep, c->cs));
   TRY(capture_end(c, nullptr));
   const int64_t l7 = c->launches;
   // kernels per executed step: fixed ones, per refinement sweep, per Krylov iteration
-  // (a sweep runs one of the inner solves: the FP64 one's set-up kernels are as many)
-  c->graph_kernels_fixed = (l1 - l0) + (l2 - l1) + (l6 - l5) + (l7 - l6);
-  c->graph_kernels_sweep = (l3 - l2) + (l5 - l4) - (sizeof(T) == 8 ? 0 : 4);
+  // (a mixed sweep runs one of its two inner solves, whose set-up and correction kernels
+  // are 4 each)
+  c->graph_kernels_fixed = (l2 - l0) + (l7 - l3);
+  c->graph_kernels_sweep = (l3 - l2) - (sizeof(T) == 8 ? 0 : 4);
   c->graph_kernels_iter = iter_k;
   c->graph_kernels_iter64 = iter64_k;
   c->launches = l0;  // captured launches run only when the graph is launched
