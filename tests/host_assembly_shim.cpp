@@ -50,3 +50,44 @@ extern "C" int assemble_level0(int scheme, int m, int n, const double* r, const 
   scal[1] = L.rs0;
   return 0;
 }
+
+// The same assembly followed by one radial coarsening: outputs the next coarser level
+// (mc = m / 2 rings: vol, rs, w, e, s, nn, o, scal) and the fine odd rings' interpolation
+// weights ia, ib (m*n, zero on even rings).
+extern "C" int coarsen_level0(int scheme, int m, int n, const double* r, const double* th,
+                              const double* dr, const double* dt, const double* vr,
+                              const double* vt, const double* en, const double* b,
+                              double d_const, double d0, double* vol, double* rs, double* w,
+                              double* e, double* s, double* nn, double* o, double* scal,
+                              double* ia, double* ib) {
+  polar::HostCoeffs K;
+  const size_t N = (size_t)m * n + 1, nf = (size_t)(m + 1) * n, nt = (size_t)m * n;
+  K.dr = take(dr, nf);
+  K.dt = take(dt, nt);
+  K.vr = take(vr, nf);
+  K.vt = take(vt, nt);
+  K.en = take(en, N);
+  K.b = take(b, N);
+  K.d_const = d_const;
+  K.d0 = d0;
+  const std::vector<double> rv(r, r + m + 2), tv(th, th + n);
+  polar::HLevel L, Lc;
+  if (scheme == 0) {
+    polar::assemble_conservative(rv, tv, K, L);
+  } else {
+    polar::assemble_paper(rv, tv, K, L);
+  }
+  polar::coarsen(L, Lc);
+  put(Lc.vol, vol);
+  put(Lc.rs, rs);
+  put(Lc.w, w);
+  put(Lc.e, e);
+  put(Lc.s, s);
+  put(Lc.nn, nn);
+  put(Lc.o, o);
+  scal[0] = Lc.vol0;
+  scal[1] = Lc.rs0;
+  put(L.ia, ia);
+  put(L.ib, ib);
+  return 0;
+}

@@ -114,3 +114,63 @@ def test_conservative_assembly_parabolic_graded(shim):
 def test_paper_assembly(shim):
     for prob in (pi.paper_continuity_e3(7), pi.paper_parabolic_e1(6)):
         _check(prob, _assemble(shim, prob))
+
+
+def _coarsen(lib, prob):
+    m, n = prob.m, prob.n
+    mc = m // 2
+    outs = ([np.zeros(mc * n) for _ in range(6)] + [np.zeros(n), np.zeros(2)] +
+            [np.zeros(m * n), np.zeros(m * n)])
+    rc = lib.coarsen_level0(
+        C.c_int(prob.scheme), C.c_int(m), C.c_int(n), _ptr(prob.r), _ptr(prob.theta),
+        _ptr(prob.d_rface), _ptr(prob.d_tface), None, None, None,
+        _ptr(np.full(prob.N, prob.b_const)), C.c_double(1.0), C.c_double(prob.d0),
+        *[o.ctypes.data_as(C.c_void_p) for o in outs])
+    assert rc == 0
+    _ptr.keep.clear()
+    return outs
+
+
+@pytest.mark.parametrize("m", [12, 13])
+def test_radial_coarsening_is_cyclic_reduction(shim, m):
+    """Without angular coupling, reaction or drift, the coarse level is exactly the Schur
+    complement of V L after eliminating the odd rings (one step of cyclic reduction of every
+    radial line, the origin included), computed here densely from the oracle's L and B."""
+    n = 7
+    prob = pi.config2(m=m, n=n, K=2)
+    rng = np.random.default_rng(m)
+    prob.d_rface = rng.uniform(0.5, 2.0, (m + 1) * n)     # radial D varies along the line
+    prob.d_tface = np.zeros(m * n)                          # no angular coupling
+    vol, rs, w, e, s, nn, o, scal, ia, ib = _coarsen(shim, prob)
+    L, B = po.operator(prob)
+    g = po.Geometry(prob.r, prob.theta)
+    A = (np.diag(g.V) @ L.toarray())
+    Bd = np.diag(g.V) @ B.toarray()
+    ring = np.zeros(prob.N, dtype=int)
+    ring[1:] = np.tile(np.arange(1, m + 1), n)
+    Eset = np.where(ring % 2 == 0)[0]                        # origin and even rings
+    Oset = np.where(ring % 2 == 1)[0]
+    Aoo = A[np.ix_(Oset, Oset)]
+    assert np.count_nonzero(Aoo - np.diag(np.diag(Aoo))) == 0   # odd rings decoupled
+    inv = 1.0 / np.diag(Aoo)
+    Cm = A[np.ix_(Eset, Eset)] - A[np.ix_(Eset, Oset)] @ (inv[:, None] * A[np.ix_(Oset, Eset)])
+    CB = Bd[Eset] - A[np.ix_(Eset, Oset)] @ (inv[:, None] * Bd[Oset])
+    pos = {int(p): k for k, p in enumerate(Eset)}
+    mc = m // 2
+    idx = lambda i, j: 1 + j * m + (i - 1)
+    for j in range(n):
+        for I in range(1, mc + 1):
+            qc = j * mc + (I - 1)
+            row = pos[idx(2 * I, j)]
+            scale = np.abs(Cm[row]).sum() + np.abs(CB[row]).sum()
+            west = pos[0] if I == 1 else pos[idx(2 * I - 2, j)]
+            assert abs(Cm[row, west] - w[qc]) <= 1e-12 * scale, ("w", I, j)
+            if 2 * I + 2 <= m:
+                east = Cm[row, pos[idx(2 * I + 2, j)]]
+            else:
+                east = CB[row, j]                           # into the Dirichlet ring
+            assert abs(east - e[qc]) <= 1e-12 * scale, ("e", I, j)
+            assert abs(Cm[row, row] - (rs[qc] - w[qc] - e[qc])) <= 1e-12 * scale, ("diag", I, j)
+            assert s[qc] == 0.0 and nn[qc] == 0.0
+        assert abs(Cm[pos[0], pos[idx(2, j)]] - o[j]) <= 1e-12 * np.abs(Cm[pos[0]]).sum()
+    assert abs(Cm[pos[0], pos[0]] - (scal[1] - o.sum())) <= 1e-12 * np.abs(Cm[pos[0]]).sum()
