@@ -262,8 +262,10 @@ class _ContinuityFields:
 
 def _chunked(fn, *arrays, nout=1, chunk=1 << 20):
     """fn applied to consecutive slices of the (equal-length) arrays on a thread pool
-    (numpy releases the GIL in its loops), outputs concatenated: the same values as one
-    call on the whole arrays, with temporaries bounded by the chunk size."""
+    (numpy releases the GIL in its loops), outputs concatenated: one call on the whole
+    arrays up to the summation order of the BLAS products inside fn, with temporaries
+    bounded by the chunk size.  The chunking is fixed, so a workload's arrays are
+    reproducible."""
     size = len(arrays[0])
     if size <= chunk:
         return fn(*arrays)

@@ -104,3 +104,20 @@ def test_manufactured_sources_satisfy_pde_numerically():
     L = lambda P, Px, Py, lP: -(Dx * Px + Dy * Py) - Dn * lP + P * divv + vx * Px + vy * Py + P
     f = math.exp(-t) * (-A + L(A, Ax, Ay, lA)) + L(B, Bx, By, lB)
     assert np.allclose(f, f_expected, rtol=1e-5, atol=1e-5)
+
+
+def test_chunked_field_evaluation_matches_whole_arrays():
+    """Large workloads evaluate their fields in chunks on a thread pool; the values agree with
+    one evaluation over the whole arrays to the rounding of the 8-term mode sums (the BLAS
+    products may order them differently), ragged last chunk included."""
+    from polar_inputs.problems import _chunked, _ContinuityFields
+    F = _ContinuityFields(15879002, 1.3, 0.05)
+    rng = np.random.default_rng(3)
+    x, y = rng.uniform(-1, 1, 1001), rng.uniform(-1, 1, 1001)
+    whole = F.D(x, y)[0]
+    assert np.allclose(_chunked(lambda a, b: F.D(a, b)[0], x, y, chunk=64), whole,
+                       rtol=1e-14, atol=0)
+    vx, vy, dv = F.vel(x, y)
+    got = _chunked(lambda a, b: F.vel(a, b), x, y, nout=3, chunk=100)
+    for g_, w_ in zip(got, (vx, vy, dv)):
+        assert np.allclose(g_, w_, rtol=1e-13, atol=1e-13 * np.max(np.abs(w_)))
