@@ -58,22 +58,41 @@ enum { POLAR_HOST = 0, POLAR_DEVICE = 1 };  /* where a caller's pointer lives   
 
 typedef struct polar_ctx polar_ctx;
 
+/* Device-memory hooks (memory management of the library; the paper has no counterpart).
+ * alloc returns a device pointer to at least `bytes` bytes on the current device, aligned
+ * to 256 bytes and usable by work on `stream` (the cudaStream_t of the context), or NULL
+ * when it cannot; free gives back a pointer alloc returned, after every use of it on
+ * `stream` has been enqueued.  `user` is the alloc_user of the mesh descriptor.  A binding
+ * passes its framework's allocator here (e.g. the PyTorch caching allocator), so the
+ * library's buffers come out of the framework's memory pool. */
+typedef void* (*polar_alloc_fn)(size_t bytes, void* stream, void* user);
+typedef void (*polar_free_fn)(void* ptr, void* stream, void* user);
+
 /* Mesh of Sections 2.1 / 3.1.  The caller owns r and theta; they are copied. */
 typedef struct {
   int32_t nr;            /* m >= 2 unknown rings r_1..r_m                              */
-  int32_t ntheta;        /* n >= 4 angles theta_0..theta_{n-1}                          */
+  int32_t ntheta;        /* 4 <= n <= 16384 angles theta_0..theta_{n-1}                 */
   const double* r;       /* host, m+2 values, r[0] = 0 < r[1] < ... < r[m+1] = 1        */
   const double* theta;   /* host, n values, 0 <= theta[0] < ... < theta[n-1] < theta[0] + 2 pi */
   int32_t scheme;        /* POLAR_SCHEME_*                                              */
   int32_t precision;     /* POLAR_FP64 or POLAR_MIXED                                   */
   void* stream;          /* cudaStream_t for all work (NULL = legacy default stream)    */
+  polar_alloc_fn alloc;  /* device allocations of the context; NULL: cudaMalloc         */
+  polar_free_fn free;    /* required when alloc is set; NULL with alloc NULL: cudaFree  */
+  void* alloc_user;      /* passed to alloc and free                                    */
 } polar_mesh_desc;
 
 /* polar_mesh_create: validates the mesh (strictly increasing r with r[0] = 0 and
- * r[m+1] = 1; strictly increasing theta spanning less than 2 pi; m >= 2; n >= 4)
- * and allocates every device buffer of the context on the current device.
- * Errors: POLAR_EINVAL (bad mesh, nothing allocated), POLAR_ENOMEM, POLAR_ECUDA.
- * On success *out owns the buffers until polar_mesh_destroy. */
+ * r[m+1] = 1; strictly increasing theta spanning less than 2 pi; m >= 2; 4 <= n <= 16384,
+ * the longest ring the line solves handle: up to 16 CTAs of a thread-block cluster per
+ * ring; m n <= 2^31) and allocates every device buffer of the context on the current
+ * device through desc->alloc (cudaMalloc when NULL), the multigrid levels included.
+ * Later calls allocate through the same hook: polar_set_coeffs (source fields, on first
+ * use) and polar_advance / polar_batch_advance (a schedule longer than any before it).
+ * polar_mesh_destroy returns every buffer through desc->free (cudaFree when NULL).
+ * Errors: POLAR_EINVAL (bad mesh or alloc without free, nothing allocated),
+ * POLAR_ENOMEM (an allocation failed or was not 256-byte aligned; what was allocated is
+ * freed), POLAR_ECUDA.  On success *out owns the buffers until polar_mesh_destroy. */
 int polar_mesh_create(const polar_mesh_desc* desc, polar_ctx** out);
 int polar_mesh_destroy(polar_ctx* ctx);
 
@@ -202,9 +221,10 @@ int polar_apply_operator(polar_ctx* ctx, double alpha, double beta, const double
                          double* y, int32_t memory);
 
 /* polar_apply_rows_noalloc: y = alpha x + beta L x for a 5-point polar operator given row
- * by row, for callers that cannot allocate device memory -- code that runs while a CUDA
- * stream is being captured into a graph (where cudaMalloc is not permitted) or embedders
- * whose device memory is budgeted up front.  It needs no context and allocates nothing.
+ * by row, for callers that cannot allocate device memory -- embedders whose device memory
+ * is a fixed budget they hand out themselves, or pipelines that must not call cudaMalloc /
+ * cudaFree between kernels (both may synchronise the device).  It needs no context and
+ * allocates nothing.
  * The paper has no counterpart: this is a memory-management variant of
  * polar_apply_operator for operators the caller holds itself.
  *   m >= 2, 4 <= n <= 16384 (larger n: POLAR_EINVAL).
@@ -215,15 +235,17 @@ int polar_apply_operator(polar_ctx* ctx, double alpha, double beta, const double
  *     with x_{0,j} = x_0 (the origin), x_{m+1,j} = 0 and j periodic; entry 0 of W, E, S, N
  *     is not read.
  *   o: device array of n doubles; the origin row is R[0] x_0 + sum_j o_j (x_{1,j} - x_0).
- *   x, y: device arrays of m n + 1 doubles; they must not overlap.
+ *   x, y: device arrays of m n + 1 doubles; their ranges must not overlap (POLAR_EINVAL).
  *   stream: the cudaStream_t to enqueue on (NULL: legacy default stream).
  * Asynchronous: it returns once the work is enqueued (launch errors are reported).
  * Its only scratch is a fixed 128 KB array in device memory that the library reserves on
  * every device it is loaded on, until the process exits: the origin row's sum over the n
  * angles is staged there.  Every call shares that array, so calls that may overlap on the
- * GPU (different streams, or several host threads) race; serialise them.  The first call on
- * a device looks up the array's address on that device; make that first call before any
- * stream capture begins. */
+ * GPU (different streams, or several host threads) race; serialise them.  Each call looks
+ * up the array's address on the current device (the first call on a device is its set-up);
+ * make that first call before any stream capture begins: a call while `stream` is being
+ * captured reuses the address found by the device's last call, and returns POLAR_ESTATE if
+ * there was none. */
 int polar_apply_rows_noalloc(int32_t m, int32_t n, const double* R, const double* W,
                              const double* E, const double* S, const double* N,
                              const double* o, double alpha, double beta, const double* x,

@@ -7,6 +7,7 @@ The library has no CPU fallback: loading fails loudly if libpolar.so is missing.
 """
 import ctypes as C
 import os
+import sys
 
 import numpy as np
 
@@ -22,9 +23,15 @@ POLAR_HOST, POLAR_DEVICE = 0, 1
 _dp = C.POINTER(C.c_double)
 
 
+# device-memory hooks of polar_mesh_desc: alloc(bytes, stream, user) -> ptr, free(ptr, stream, user)
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p, C.c_void_p)
+
+
 class polar_mesh_desc(C.Structure):
     _fields_ = [("nr", C.c_int32), ("ntheta", C.c_int32), ("r", _dp), ("theta", _dp),
-                ("scheme", C.c_int32), ("precision", C.c_int32), ("stream", C.c_void_p)]
+                ("scheme", C.c_int32), ("precision", C.c_int32), ("stream", C.c_void_p),
+                ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_user", C.c_void_p)]
 
 
 class polar_coeffs(C.Structure):
@@ -110,48 +117,110 @@ def _f64(a):
 
 
 class _Arr:
-    """Holds a pointer to caller data and keeps the owner alive."""
+    """Holds a pointer to caller data and keeps the owner alive.
 
-    def __init__(self, a):
+    ``count`` is the number of doubles the C call reads or writes through the pointer:
+    every array must be float64, contiguous and hold at least that many.  CUDA tensors must
+    live on the current device.  ``out`` marks an array the call writes: it is used in
+    place, so a numpy array that would need a converted copy is rejected instead of being
+    copied (the result would land in the copy).  Violations raise ValueError before the
+    library is called."""
+
+    def __init__(self, a, count, name="array", out=False):
+        self.ptr, self.keep, self.device = None, None, None
         if a is None:
-            self.ptr, self.keep, self.device = None, None, None
-        elif hasattr(a, "data_ptr") and getattr(a, "is_cuda", False):
-            self.ptr, self.keep, self.device = a.data_ptr(), a, True
-        elif hasattr(a, "data_ptr") and hasattr(a, "is_contiguous"):
-            # host torch tensor (e.g. pinned): used in place, never copied
-            if str(a.dtype) != "torch.float64" or not a.is_contiguous():
-                raise ValueError("host tensors must be contiguous float64")
-            self.ptr, self.keep, self.device = a.data_ptr(), a, False
+            return
+        if hasattr(a, "data_ptr") and hasattr(a, "is_contiguous"):   # torch tensor
+            if str(a.dtype) != "torch.float64":
+                raise ValueError(f"{name}: tensors must be float64, got {a.dtype}")
+            if not a.is_contiguous():
+                raise ValueError(f"{name}: tensors must be contiguous")
+            if a.numel() < count:
+                raise ValueError(f"{name}: needs {count} values, the tensor holds {a.numel()}")
+            if getattr(a, "is_cuda", False):
+                import torch
+                if a.device.index != torch.cuda.current_device():
+                    raise ValueError(f"{name}: tensor on cuda:{a.device.index}, but the "
+                                     f"current device is cuda:{torch.cuda.current_device()}")
+                self.device = True
+            else:
+                self.device = False          # host tensor (e.g. pinned): used in place
+            self.ptr, self.keep = a.data_ptr(), a
+            return
+        if out:
+            if not (isinstance(a, np.ndarray) and a.dtype == np.float64 and
+                    a.flags.c_contiguous and a.flags.writeable):
+                raise ValueError(f"{name}: outputs must be writable contiguous float64 arrays")
+            arr = a
         else:
             arr = _f64(a)
-            self.ptr, self.keep, self.device = arr.ctypes.data, arr, False
+        if arr.size < count:
+            raise ValueError(f"{name}: needs {count} values, the array holds {arr.size}")
+        self.ptr, self.keep, self.device = arr.ctypes.data, arr, False
 
 
 class Ctx:
-    """Handle of a polar_ctx; destroyed with the object or by polar_mesh_destroy."""
+    """Handle of a polar_ctx; destroyed with the object or by polar_mesh_destroy.  It keeps
+    the allocator hooks the context was created with alive as long as the context."""
 
-    def __init__(self, handle, m, n):
-        self.handle, self.m, self.n = handle, m, n
+    def __init__(self, handle, m, n, hooks=None):
+        self.handle, self.m, self.n, self.hooks = handle, m, n, hooks
 
     @property
     def N(self):
         return self.m * self.n + 1
 
     def __del__(self):
-        if getattr(self, "handle", None) and _lib is not None:
+        # at interpreter exit the allocator behind the hooks may already be gone: the
+        # process ends and its device memory with it
+        if getattr(self, "handle", None) and _lib is not None and not sys.is_finalizing():
             _lib.polar_mesh_destroy(self.handle)
             self.handle = None
 
 
+class TorchAllocator:
+    """Device memory of a context from PyTorch's caching allocator (the library's buffers
+    join torch's memory pool; torch keeps freed blocks cached for reuse)."""
+
+    def alloc(self, nbytes, stream):
+        import torch
+        return torch.cuda.caching_allocator_alloc(int(nbytes), torch.cuda.current_device(),
+                                                  int(stream or 0))
+
+    def free(self, ptr, stream):
+        import torch
+        torch.cuda.caching_allocator_delete(int(ptr))
+
+
+def _hooks(allocator):
+    """(alloc, free) ctypes callbacks of an allocator object with alloc(nbytes, stream) ->
+    int pointer and free(ptr, stream); null callbacks for None (the library's cudaMalloc)."""
+    if allocator is None:
+        return ALLOC_FN(), FREE_FN()
+
+    def a(nbytes, stream, user):
+        return int(allocator.alloc(nbytes, stream)) or None
+
+    def f(ptr, stream, user):
+        allocator.free(ptr, stream)
+
+    return ALLOC_FN(a), FREE_FN(f)
+
+
 def polar_mesh_create(r, theta, scheme=POLAR_SCHEME_CONSERVATIVE, precision=POLAR_FP64,
-                      stream=None) -> Ctx:
+                      stream=None, allocator=None) -> Ctx:
+    """``allocator``: None (the library allocates with cudaMalloc), "torch" (PyTorch's
+    caching allocator) or an object with alloc(nbytes, stream) and free(ptr, stream)."""
     lib = load()
     r, theta = _f64(r), _f64(theta)
+    if allocator == "torch":
+        allocator = TorchAllocator()
+    fa, ff = _hooks(allocator)
     d = polar_mesh_desc(len(r) - 2, len(theta), r.ctypes.data_as(_dp), theta.ctypes.data_as(_dp),
-                        scheme, precision, stream)
+                        scheme, precision, stream, fa, ff, None)
     h = C.c_void_p()
     _check(lib.polar_mesh_create(C.byref(d), C.byref(h)))
-    return Ctx(h, len(r) - 2, len(theta))
+    return Ctx(h, len(r) - 2, len(theta), (fa, ff, allocator))
 
 
 def polar_mesh_destroy(ctx: Ctx):
@@ -162,9 +231,15 @@ def polar_mesh_destroy(ctx: Ctx):
 
 def polar_set_coeffs(ctx: Ctx, d_rface=None, d_tface=None, v_rface=None, v_tface=None,
                      e_node=None, b=None, d_const=1.0, b_const=0.0, d0=1.0, src=(), bnd=()):
-    arrs = [_Arr(x) for x in (d_rface, d_tface, v_rface, v_tface, e_node, b)]
-    srcs = [_Arr(x) for x in src]
-    bnds = [_Arr(x) for x in bnd]
+    m, n, N = ctx.m, ctx.n, ctx.N
+    if len(src) != len(bnd) or len(src) > 4:
+        raise ValueError("src and bnd must have the same length, at most 4")
+    sizes = ((m + 1) * n, m * n, (m + 1) * n, m * n, N, N)
+    names = ("d_rface", "d_tface", "v_rface", "v_tface", "e_node", "b")
+    arrs = [_Arr(x, c, nm) for x, c, nm in zip((d_rface, d_tface, v_rface, v_tface, e_node, b),
+                                                sizes, names)]
+    srcs = [_Arr(x, N, f"src[{q}]") for q, x in enumerate(src)]
+    bnds = [_Arr(x, n, f"bnd[{q}]") for q, x in enumerate(bnd)]
     kinds = {a.device for a in arrs + srcs + bnds if a.ptr is not None}
     if len(kinds) > 1:
         raise ValueError("all coefficient arrays must live in the same memory")
@@ -181,7 +256,7 @@ def polar_set_coeffs(ctx: Ctx, d_rface=None, d_tface=None, v_rface=None, v_tface
 
 
 def polar_set_state(ctx: Ctx, u, t: float):
-    a = _Arr(u)
+    a = _Arr(u, ctx.N, "u")
     _check(load().polar_set_state(ctx.handle, a.ptr, float(t),
                                   POLAR_DEVICE if a.device else POLAR_HOST))
 
@@ -190,7 +265,7 @@ def polar_get_state(ctx: Ctx, out=None):
     """Returns (u, t); u is a new numpy array unless ``out`` (host or device) is given."""
     if out is None:
         out = np.empty(ctx.N, dtype=np.float64)
-    a = _Arr(out)
+    a = _Arr(out, ctx.N, "out", out=True)
     t = C.c_double()
     _check(load().polar_get_state(ctx.handle, a.ptr, C.byref(t),
                                   POLAR_DEVICE if a.device else POLAR_HOST))
@@ -229,7 +304,7 @@ def polar_advance(ctx: Ctx, t, theta, w=None, opts=None, check=True):
 def polar_apply_operator(ctx: Ctx, alpha, beta, x, out=None):
     if out is None:
         out = np.empty(ctx.N, dtype=np.float64)
-    ax, ay = _Arr(x), _Arr(out)
+    ax, ay = _Arr(x, ctx.N, "x"), _Arr(out, ctx.N, "out", out=True)
     if ax.device != ay.device:
         raise ValueError("x and y must live in the same memory")
     _check(load().polar_apply_operator(ctx.handle, float(alpha), float(beta), ax.ptr, ay.ptr,
@@ -240,7 +315,11 @@ def polar_apply_operator(ctx: Ctx, alpha, beta, x, out=None):
 def polar_apply_rows_noalloc(m, n, R, W, E, S, N, o, alpha, beta, x, y, stream=None):
     """y = alpha x + beta L x from caller-held device rows (torch CUDA tensors); allocates
     nothing on the device."""
-    arrs = [_Arr(a) for a in (R, W, E, S, N, o, x, y)]
+    m, n = int(m), int(n)
+    Np = m * n + 1
+    arrs = [_Arr(a, c, nm, out=(nm == "y")) for a, c, nm in
+            zip((R, W, E, S, N, o, x, y), (Np,) * 5 + (n, Np, Np),
+                ("R", "W", "E", "S", "N", "o", "x", "y"))]
     if not all(a.device for a in arrs):
         raise ValueError("polar_apply_rows_noalloc takes device arrays only")
     _check(load().polar_apply_rows_noalloc(int(m), int(n), *[a.ptr for a in arrs[:6]],

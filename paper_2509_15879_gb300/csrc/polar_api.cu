@@ -97,7 +97,11 @@ struct polar_ctx {
   cudaStream_t st = nullptr;
   int device = 0;
   std::vector<double> r, theta;
-  std::vector<void*> allocs;
+  std::vector<void*> allocs;      // every device buffer of the context
+  polar_alloc_fn alloc = nullptr; // caller's allocator (null: cudaMalloc / cudaFree)
+  polar_free_fn free_fn = nullptr;
+  void* alloc_user = nullptr;
+  size_t alloc_bytes = 0;         // bytes held in `allocs`
   std::vector<DevLevel> lv;
   std::vector<LevelView<double>> v64;
   std::vector<LevelView<float>> v32;
@@ -157,16 +161,29 @@ struct polar_ctx {
 
 namespace {
 
+// One zeroed device buffer of the context, from the caller's allocator when one was given
+// (zeroed on the context's stream, the stream the allocator hands the memory out for).
 template <typename T>
 int dalloc(polar_ctx* c, T** p, size_t count) {
+  const size_t bytes = std::max<size_t>(count, 1) * sizeof(T);
   void* q = nullptr;
-  cudaError_t e = cudaMalloc(&q, std::max<size_t>(count, 1) * sizeof(T));
-  if (e != cudaSuccess) {
-    (void)cudaGetLastError();
-    return fail(POLAR_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+  if (c->alloc) {
+    q = c->alloc(bytes, c->st, c->alloc_user);
+    if (!q) return fail(POLAR_ENOMEM, "the caller's allocator returned NULL");
+    if (reinterpret_cast<uintptr_t>(q) % 256 != 0) {
+      c->free_fn(q, c->st, c->alloc_user);
+      return fail(POLAR_ENOMEM, "the caller's allocator returned memory not aligned to 256 bytes");
+    }
+  } else {
+    cudaError_t e = cudaMalloc(&q, bytes);
+    if (e != cudaSuccess) {
+      (void)cudaGetLastError();
+      return fail(POLAR_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    }
   }
   c->allocs.push_back(q);
-  e = cudaMemset(q, 0, std::max<size_t>(count, 1) * sizeof(T));
+  c->alloc_bytes += bytes;
+  cudaError_t e = cudaMemsetAsync(q, 0, bytes, c->st);
   if (e != cudaSuccess) return fail(POLAR_ECUDA, cudaGetErrorString(e));
   *p = static_cast<T*>(q);
   return POLAR_OK;
@@ -259,8 +276,15 @@ void release(polar_ctx* c) {
   c->pending.clear();
   for (cudaEvent_t e : c->ev_free) cudaEventDestroy(e);
   c->ev_free.clear();
-  for (void* p : c->allocs) cudaFree(p);
+  for (void* p : c->allocs) {
+    if (c->free_fn) {
+      c->free_fn(p, c->st, c->alloc_user);
+    } else {
+      cudaFree(p);
+    }
+  }
   c->allocs.clear();
+  c->alloc_bytes = 0;
   if (c->ks_host) cudaFreeHost(c->ks_host);
   c->ks_host = nullptr;
   if (c->sp_host) cudaFreeHost(c->sp_host);
@@ -1266,6 +1290,8 @@ int polar_mesh_create(const polar_mesh_desc* d, polar_ctx** out) {
     return fail(POLAR_EINVAL, "unknown scheme");
   if (d->precision != POLAR_FP64 && d->precision != POLAR_MIXED)
     return fail(POLAR_EINVAL, "unknown precision");
+  if ((d->alloc != nullptr) != (d->free != nullptr))
+    return fail(POLAR_EINVAL, "alloc and free hooks go together");
   if ((size_t)m * (size_t)n > (size_t)1 << 31) return fail(POLAR_EINVAL, "mesh too large");
   if (d->r[0] != 0.0 || d->r[m + 1] != 1.0) return fail(POLAR_EINVAL, "r must run from 0 to 1");
   for (int i = 1; i <= m + 1; ++i)
@@ -1290,6 +1316,9 @@ int polar_mesh_create(const polar_mesh_desc* d, polar_ctx** out) {
   c->precision = d->precision;
   c->st = static_cast<cudaStream_t>(d->stream);
   c->cs = c->st;
+  c->alloc = d->alloc;
+  c->free_fn = d->free;
+  c->alloc_user = d->alloc_user;
   cudaGetDevice(&c->device);
   c->r.assign(d->r, d->r + m + 2);
   c->theta.assign(d->theta, d->theta + n);
@@ -1320,7 +1349,12 @@ int polar_mesh_create(const polar_mesh_desc* d, polar_ctx** out) {
     (void)cudaGetLastError();
     rc = fail(POLAR_ENOMEM, "cudaMallocHost failed");
   }
+  if (rc == POLAR_OK && cudaStreamSynchronize(c->st) != cudaSuccess) {
+    (void)cudaGetLastError();
+    rc = fail(POLAR_ECUDA, "stream synchronisation after the allocations failed");
+  }
   if (rc != POLAR_OK) {
+    cudaStreamSynchronize(c->st);
     release(c);
     delete c;
     return rc;
@@ -1386,6 +1420,7 @@ int polar_set_coeffs(polar_ctx* c, const polar_coeffs* k) {
     if (!c->vsrc[q]) {  // allocated on first use, reused by later set_coeffs calls
       TRY(dalloc(c, &c->vsrc[q], c->nv()));
       TRY(dalloc(c, &c->bnd[q], (size_t)n));
+      CUDA_TRY(cudaStreamSynchronize(c->st));  // zeroed before the copies below
     }
     CUDA_TRY(cudaMemcpy(c->io, srcs[q].data(), N * sizeof(double), cudaMemcpyHostToDevice));
     LAUNCH(launch_pack(c->sh0(), c->io, c->lv[0].vol, c->vsrc[q], c->st));

@@ -1,5 +1,6 @@
 // polar_apply_rows_noalloc: the 5-point polar operator applied from caller-supplied rows,
-// for callers that cannot allocate device memory.  See include/polar.h.
+// for callers that cannot allocate device memory (a fixed device-memory budget they own,
+// or a pipeline where an allocation call would stall the device).  See include/polar.h.
 //
 // Its only scratch is the file-scope array below: the origin row needs the sum over all
 // angles of o_j (x_{1,j} - x_0); every thread on ring 1 stores its term at slot j, and the
@@ -80,18 +81,28 @@ __global__ void __launch_bounds__(kThreads)
   }
 }
 
-// Device address of g_scratch, looked up once per device with that device current.
+// Device address of g_scratch on the current device.  In host code the name g_scratch
+// is a host-side stand-in, not a device address, so the address is looked up with the
+// device current.  The lookup is repeated on every call made while `st` is not being
+// captured (a device reset or a new primary context can move the module); a call made
+// during stream capture reuses the address of the last call on that device, and fails if
+// there was none.
 std::mutex g_lock;
 double* g_addr[kMaxDevices] = {};
 
-int scratch_address(double** out) {
+int scratch_address(cudaStream_t st, double** out) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
     (void)cudaGetLastError();
     return fail(POLAR_ECUDA, "no usable CUDA device");
   }
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cap) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return fail(POLAR_ECUDA, "cudaStreamIsCapturing failed on the given stream");
+  }
   std::lock_guard<std::mutex> guard(g_lock);
-  if (!g_addr[dev]) {
+  if (cap == cudaStreamCaptureStatusNone) {
     void* p = nullptr;
     const cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
     if (e != cudaSuccess) {
@@ -99,6 +110,8 @@ int scratch_address(double** out) {
       return fail(POLAR_ECUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
     }
     g_addr[dev] = static_cast<double*>(p);
+  } else if (!g_addr[dev]) {
+    return fail(POLAR_ESTATE, "the first call on a device must come before any stream capture");
   }
   *out = g_addr[dev];
   return POLAR_OK;
@@ -117,11 +130,14 @@ int polar_apply_rows_noalloc(int32_t m, int32_t n, const double* R, const double
     return fail(POLAR_EINVAL, "n above 16384: the origin row's scratch holds 16384 angles");
   if ((size_t)m * (size_t)n > ((size_t)1 << 31)) return fail(POLAR_EINVAL, "mesh too large");
   if (!R || !W || !E || !S || !N || !o || !x || !y) return fail(POLAR_EINVAL, "null argument");
-  if (x == y) return fail(POLAR_EINVAL, "x and y must not overlap");
-  double* scratch = nullptr;
-  const int rc = scratch_address(&scratch);
-  if (rc != POLAR_OK) return rc;
+  const size_t Np = (size_t)m * n + 1;
+  const uintptr_t xa = reinterpret_cast<uintptr_t>(x), ya = reinterpret_cast<uintptr_t>(y);
+  if (xa < ya + Np * sizeof(double) && ya < xa + Np * sizeof(double))
+    return fail(POLAR_EINVAL, "x and y must not overlap");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
+  double* scratch = nullptr;
+  const int rc = scratch_address(st, &scratch);
+  if (rc != POLAR_OK) return rc;
   // the arrival counter must start at zero (a failed earlier launch may have left it set)
   cudaError_t e = cudaMemsetAsync(scratch + kCounterSlot, 0, sizeof(double), st);
   if (e != cudaSuccess) return fail(POLAR_ECUDA, std::string("cudaMemsetAsync: ") + cudaGetErrorString(e));

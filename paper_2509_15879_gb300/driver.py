@@ -18,8 +18,21 @@ def _const(a):
     return float(a.flat[0]) if a.size and np.all(a == a.flat[0]) else None
 
 
-def create(problem, precision=P.POLAR_FP64, stream=None, compact_d=True):
-    ctx = P.polar_mesh_create(problem.r, problem.theta, problem.scheme, precision, stream)
+def default_allocator():
+    """PyTorch's caching allocator when torch sees a GPU (the library then takes its
+    device memory from torch's pool), else None (the library's own cudaMalloc)."""
+    try:
+        import torch
+        return "torch" if torch.cuda.is_available() else None
+    except ImportError:
+        return None
+
+
+def create(problem, precision=P.POLAR_FP64, stream=None, compact_d=True, allocator="auto"):
+    if allocator == "auto":
+        allocator = default_allocator()
+    ctx = P.polar_mesh_create(problem.r, problem.theta, problem.scheme, precision, stream,
+                              allocator)
     load_coeffs(ctx, problem, compact_d=compact_d)
     P.polar_set_state(ctx, problem.u0, problem.t[0])
     return ctx

@@ -109,3 +109,64 @@ def test_valid_mesh_without_gpu_reports_cuda_error(lib):
     h = C.c_void_p()
     assert lib.polar_mesh_create(C.byref(d), C.byref(h)) == P.POLAR_ECUDA
     assert not h.value
+
+
+def test_noalloc_rejects_bad_sizes_and_overlap_before_gpu_work(lib):
+    """polar_apply_rows_noalloc checks n against its fixed scratch and the x / y ranges
+    before it touches the GPU (the pointers here are never dereferenced)."""
+    from paper_2509_15879_gb300 import _native as P
+    fake = [C.c_void_p(4096 * (k + 1)) for k in range(6)]
+    m, n = 4, 8
+    N = m * n + 1
+    x = C.c_void_p(1 << 20)
+    for y in (x, C.c_void_p((1 << 20) + 8 * (N - 1)), C.c_void_p((1 << 20) - 8 * (N - 1))):
+        rc = lib.polar_apply_rows_noalloc(m, n, *fake, 1.0, 1.0, x, y, None)
+        assert rc == P.POLAR_EINVAL
+    rc = lib.polar_apply_rows_noalloc(m, 16385, *fake, 1.0, 1.0, x, C.c_void_p(1 << 30), None)
+    assert rc == P.POLAR_EINVAL
+    assert b"16384" in lib.polar_last_error()
+
+
+def test_mesh_create_rejects_half_an_allocator(lib):
+    from paper_2509_15879_gb300 import _native as P
+    d, keep = _desc(P, 8, 16)
+    d.alloc = P.ALLOC_FN(lambda nbytes, stream, user: None)
+    h = C.c_void_p()
+    assert lib.polar_mesh_create(C.byref(d), C.byref(h)) == P.POLAR_EINVAL
+    assert not h.value
+
+
+# ------------------------------------------------------------------ binding validation
+def test_binding_rejects_wrong_arrays_before_calling_the_library():
+    """Arrays the C calls read or write must be float64, contiguous and long enough; an
+    output that would need a converted copy is refused (nothing reaches the library)."""
+    import torch
+    from paper_2509_15879_gb300 import _native as P
+    P._Arr(np.zeros(6), 6)                                         # fine
+    with pytest.raises(ValueError):
+        P._Arr(np.zeros(5), 6, "x")                                # too short
+    with pytest.raises(ValueError):
+        P._Arr(np.zeros(6, dtype=np.float32), 6, "y", out=True)    # output needs a copy
+    with pytest.raises(ValueError):
+        P._Arr(np.zeros((6, 2))[:, 0], 6, "y", out=True)           # strided output
+    with pytest.raises(ValueError):
+        P._Arr(torch.zeros(6, dtype=torch.float32), 6, "u")        # wrong dtype tensor
+    with pytest.raises(ValueError):
+        P._Arr(torch.zeros(12, dtype=torch.float64)[::2], 6, "u")  # strided tensor
+    with pytest.raises(ValueError):
+        P._Arr(torch.zeros(5, dtype=torch.float64), 6, "u")        # short tensor
+    ctx = P.Ctx(None, 4, 8)                                        # never reaches the library
+    N = ctx.N
+    with pytest.raises(ValueError):
+        P.polar_set_coeffs(ctx, d_rface=np.ones(5 * 8 - 1))
+    with pytest.raises(ValueError):
+        P.polar_set_coeffs(ctx, src=[np.ones(N)], bnd=[np.ones(7)])
+    with pytest.raises(ValueError):
+        P.polar_set_state(ctx, np.ones(N - 1), 0.0)
+    with pytest.raises(ValueError):
+        P.polar_get_state(ctx, np.empty(N - 1))
+    with pytest.raises(ValueError):
+        P.polar_apply_operator(ctx, 1.0, 1.0, np.ones(N), np.empty(N, dtype=np.float32))
+    with pytest.raises(ValueError):
+        P.polar_apply_rows_noalloc(4, 8, *[np.ones(N)] * 5, np.ones(8), 1.0, 1.0,
+                                   np.ones(N), np.empty(N))
