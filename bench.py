@@ -1,31 +1,39 @@
 """Throughput of the implicit theta-step on the adaptive polar mesh (one GB300 per rank).
 
-Workload: the singular parabolic equation on the unit disk on the adaptive mesh --
-m = 512 rings graded geometrically (ratio 1.03) toward r = 0 and r = 1, n = 1024
-angles with node density 1 + 0.5 cos(theta - theta0), Crank-Nicolson, variable
-dt_k = 1e-4 * 1.01^k over a 1000-level schedule (T ~ 209.6); manufactured solution
-u = e^{-t}(1 - r^2)(1 + r cos theta).  Inputs are synthetic and seeded.
+Default workload (the largest single-GPU configuration of the benchmark): the continuity
+(drift-diffusion) equation n_t = div(D grad n - v n) + G - n on the unit disk, m = 8192
+rings graded geometrically (ratio 1.03, capped) toward r = 1, n = 16384 angles with node
+density 1 + 0.5 cos(theta - theta0) (N = 134,217,729 unknowns, 1.07 GB per FP64 field),
+D = exp(ln 2 * 8 seeded Fourier modes) in [0.5, 2], v = -grad(phi) scaled to cell Peclet 10,
+manufactured solution with a sharp layer at r = 1, theta = 0.6 over the 200-level time
+stretch t_k = sin((k/200)^1.5 pi/2).  Inputs are synthetic and seeded.  Other workloads
+(--workload): c3 (continuity 2048 x 4096, Crank-Nicolson, 2000 levels), c2 (parabolic
+512 x 1024, dt_k = 1e-4 * 1.01^k, 1000 levels), batch (the 256-instance sweep).
 
-A bench step is one implicit theta-step (right-hand side, line factors, Krylov solve
-to the FP64 tolerance, time-level update) of that schedule.  With K < 1000 the K steps
-are spread evenly over the schedule, each starting from the manufactured solution at
-its level (set outside the timed region); with K >= 1000 the schedule runs
-consecutively.  L2 is flushed (a 512 MB write) before every timed step.
+A bench step is one implicit theta-step (right-hand side, line factors, Krylov solves to
+the FP64 tolerance, time-level update) at a level of the schedule; the K timed steps are
+spread evenly over the schedule, each starting from the manufactured solution at its level
+(set outside the timed region).  c2 with K >= 1000 runs the schedule consecutively.
 
 value  = grid-point updates (N per step) / device time of the K steps, summed over ranks
          (replicas: every rank advances its own copy; no collective on the data path);
          the headline path is the mixed one (FP32 inner solves, FP64 residual and update,
          same FP64 tolerance), the FP64 path is timed beside it on the same steps
-e2e    = the same through the C ABI with the state copied in from pinned host memory
-         and out to pinned host memory inside every timed step
+e2e    = the same through the C ABI with the state copied in from pinned host memory and
+         out to pinned host memory inside every timed step
+err_vs_oracle: per precision, against the FP64 CPU oracle on the same steps (element by
+         element where the oracle can solve the workload's step, else the oracle's
+         step equation on sampled rows)
 roofline: the dominant kernel class's algorithmic bytes / its event-timed duration
-cpu_baseline: the FP64 CPU oracle on a bounded sample of the same workload
+cpu_baseline: the FP64 CPU oracle on a bounded sample of the same workload, on every
+         host core (independent steps in parallel) and on one core
 
 --impl reference times the CPU oracle itself (the reference arm of this workload).
 """
 import argparse
 import json
 import math
+import multiprocessing as mp
 import os
 import statistics
 import subprocess
@@ -41,14 +49,30 @@ if ROOT not in sys.path:
 
 METRIC = "grid-point-updates/s and HBM GB/s vs peak, mixed vs FP64 GPU at stated error"
 UNIT = "grid-point-updates/s"
-M_RINGS, N_ANGLES, K_SCHEDULE = 512, 1024, 1000
-WORKLOAD = ("parabolic u_t = Lap u + f, adaptive polar mesh 512 x 1024 (r graded 1.03 "
-            "to both ends, theta density 1 + 0.5 cos), Crank-Nicolson, dt_k = 1e-4 * 1.01^k, "
-            "1000-level schedule")
 FALLBACK_HBM_GBS = 6800.0
 
-# ncu dram bytes (read + write) per launch of the dominant kernel class, from the
-# capture summarised under profiles/; None until a capture of the current kernel exists
+# Workloads: generator (polar_inputs), schedule length, description, the mesh of the
+# oracle's bounded sample, and how the oracle checks the GPU's steps ("full": the oracle
+# solves the same step; "rows": the oracle's step equation on sampled rows).
+WORKLOADS = {
+    "c5": dict(gen="config5", K=200, sample=(256, 512), check="rows",
+               desc="continuity n_t = div(D grad n - v n) + G - n, adaptive polar mesh "
+                    "8192 x 16384 (r graded 1.03 toward r = 1, theta density 1 + 0.5 cos), "
+                    "D in [0.5, 2] (8 Fourier modes), cell Peclet 10, theta = 0.6, "
+                    "200-level time stretch"),
+    "c3": dict(gen="config3", K=2000, sample=(256, 512), check="rows",
+               desc="continuity, adaptive polar mesh 2048 x 4096 (r graded 1.03 to both "
+                    "ends), D in [0.5, 2], cell Peclet 10, Crank-Nicolson, 2000-level time "
+                    "stretch"),
+    "c2": dict(gen="config2", K=1000, sample=(256, 512), check="full",
+               desc="parabolic u_t = Lap u + f, adaptive polar mesh 512 x 1024 (r graded "
+                    "1.03 to both ends, theta density 1 + 0.5 cos), Crank-Nicolson, "
+                    "dt_k = 1e-4 * 1.01^k, 1000-level schedule"),
+}
+
+# ncu dram bytes (read + write) per launch of the dominant kernel class, from the capture
+# summarised under profiles/, keyed by (workload, kernel class); absent until a capture of
+# the current kernel exists
 NCU_TRAFFIC = {}
 
 
@@ -149,90 +173,165 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def make_problem(m=M_RINGS, n=N_ANGLES, K=K_SCHEDULE):
+def make_problem(workload, m=None, n=None):
+    """The workload's problem (full size, or the same recipe on an m x n mesh)."""
     import polar_inputs as pi
-    return pi.config2(m=m, n=n, K=K)
+    w = WORKLOADS[workload]
+    gen = getattr(pi, w["gen"])
+    return gen() if m is None else gen(m=m, n=n, K=w["K"])
 
 
-def step_levels(K):
-    """Schedule levels at which the K timed steps start."""
-    if K >= K_SCHEDULE:
-        return [k % K_SCHEDULE for k in range(K)], True
-    return [int(math.floor(s * K_SCHEDULE / K)) for s in range(K)], False
+def step_levels(K_sched, K):
+    """Schedule levels at which K steps start (spread evenly), and whether they run the
+    schedule consecutively (K >= the schedule length)."""
+    if K >= K_sched:
+        return [k % K_sched for k in range(K)], True
+    return [int(math.floor(s * K_sched / K)) for s in range(K)], False
+
+
+def rel_max(a, b):
+    return float(np.max(np.abs(a - b)) / max(float(np.max(np.abs(b))), 1e-300))
 
 
 # ------------------------------------------------------------------------- CPU oracle
-def oracle_sample(budget_s=20.0, prob=None):
-    """Times the FP64 CPU oracle on whole theta-steps of the workload (full mesh, steps
-    spread over the schedule, each from the manufactured solution at its level) until
-    about budget_s of CPU time has passed.  Returns (updates/s, steps, seconds)."""
+# The oracle runs in worker processes started with `spawn` (never forked from a process
+# that holds a CUDA context).  A worker builds the sample problem and its operator once
+# (initializer) and then times whole theta-steps: right-hand side, sparse LU of the step's
+# matrix, solve and the extended-precision refinement.
+_W = {}
+
+
+def _oracle_init(workload, m, n):
+    os.environ.setdefault("OMP_NUM_THREADS", "1")
     from oracle import polar_oracle as po
-    prob = prob or make_problem()
-    L, B = po.operator(prob)
-    levels = [0, 500, 250, 750, 125, 625, 375, 875]
-    done, t_used, upd = 0, 0.0, 0
-    for k in levels:
-        if done and t_used >= budget_s:
-            break
-        U = prob.exact(prob.t[k])
-        dt = prob.t[k + 1] - prob.t[k]
-        t0 = time.perf_counter()
-        fo, go = po.source(prob, prob.t[k])
-        fn, gn = po.source(prob, prob.t[k + 1])
-        po.step(L, B, U, dt, prob.theta_w, fo, go, fn, gn)
-        t_used += time.perf_counter() - t0
-        upd += prob.N
-        done += 1
-    return upd / t_used, done, t_used
+    prob = make_problem(workload, m, n) if m else make_problem(workload)
+    _W.update(prob=prob, po=po, op=po.operator(prob))
+
+
+def _oracle_step(k):
+    """One oracle theta-step from the manufactured state at level k; returns
+    (unknowns, seconds, new state or None)."""
+    prob, po = _W["prob"], _W["po"]
+    L, B = _W["op"]
+    U = prob.exact(prob.t[k])
+    dt = prob.t[k + 1] - prob.t[k]
+    t0 = time.perf_counter()
+    fo, go = po.source(prob, prob.t[k])
+    fn, gn = po.source(prob, prob.t[k + 1])
+    Un = po.step(L, B, U, dt, prob.theta_w, fo, go, fn, gn)
+    return prob.N, time.perf_counter() - t0, Un
+
+
+def _oracle_step_timing(k):
+    N, sec, _ = _oracle_step(k)
+    return N, sec
+
+
+def _noop(_):
+    return os.getpid()
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def oracle_pool(workload, m, n, cores):
+    """A spawn pool of `cores` single-threaded oracle workers on the m x n sample
+    (m = None: the full workload), initialised before it is returned."""
+    ctx = mp.get_context("spawn")
+    pool = ctx.Pool(cores, initializer=_oracle_init, initargs=(workload, m, n))
+    pool.map(_noop, range(4 * cores), chunksize=1)
+    return pool
+
+
+def oracle_sample(pool, cores, K_sched, budget_s, min_rounds=1):
+    """Rounds of `cores` independent oracle steps (levels spread over the schedule), one
+    per core, until about budget_s of wall time has passed.  Returns the all-cores rate,
+    the single-core rate (updates / summed per-step seconds), the steps and the wall."""
+    levels, _ = step_levels(K_sched, 8 * cores)
+    done, upd, busy = 0, 0, 0.0
+    t0 = time.perf_counter()
+    rounds = 0
+    while rounds < min_rounds or time.perf_counter() - t0 < budget_s:
+        batch = [levels[(done + i) % len(levels)] for i in range(cores)]
+        for N, sec in pool.map(_oracle_step_timing, batch, chunksize=1):
+            upd += N
+            busy += sec
+        done += cores
+        rounds += 1
+    wall = time.perf_counter() - t0
+    return upd / wall, upd / busy, done, wall
 
 
 def run_reference(args):
     rank = env_int("RANK", 0)
     if rank != 0:
         return 0
-    prob = make_problem()
-    total = args.warmup + args.steps
-    # each reference step is one oracle theta-step on a sample mesh whose size keeps
-    # the whole run within about three minutes (one full-size step takes ~10-15 s)
-    per_step = 150.0 / max(total, 1)
-    scale = 1
-    while scale < 8 and 13.0 / (scale * scale) > per_step:
-        scale *= 2
-    sample = make_problem(M_RINGS // scale, N_ANGLES // scale) if scale > 1 else prob
-    from oracle import polar_oracle as po
-    L, B = po.operator(sample)
-    levels, _ = step_levels(args.steps)
-    wl, _ = step_levels(max(args.warmup, 1))
-
-    def one(k):
-        U = sample.exact(sample.t[k])
-        dt = sample.t[k + 1] - sample.t[k]
-        fo, go = po.source(sample, sample.t[k])
-        fn, gn = po.source(sample, sample.t[k + 1])
-        po.step(L, B, U, dt, sample.theta_w, fo, go, fn, gn)
-
-    for k in wl[:args.warmup]:
-        one(k)
-    t0 = time.perf_counter()
-    for k in levels:
-        one(k)
-    el = time.perf_counter() - t0
-    value = sample.N * len(levels) / el
-    desc = (f"one FP64 oracle theta-step (sparse LU + one extended-precision refinement) per "
-            f"bench step on the {sample.m} x {sample.n} version of the workload mesh, "
-            f"levels spread over the schedule")
+    if args.workload not in WORKLOADS:
+        print(json.dumps({"impl": "reference", "unavailable":
+                          f"no oracle sample is defined for --workload {args.workload}"}))
+        return 0
+    w = WORKLOADS[args.workload]
+    cores = host_cores()
+    m, n = w["sample"]
+    pool = oracle_pool(args.workload, m, n, cores)
+    levels, _ = step_levels(w["K"], 8 * cores)
+    # one bench step = one oracle theta-step on every host core (levels spread over the
+    # schedule) on the m x n sample of the workload
+    rounds = args.warmup + args.steps
+    t_steps, upd = [], 0
+    for r in range(rounds):
+        batch = [levels[(r * cores + i) % len(levels)] for i in range(cores)]
+        t0 = time.perf_counter()
+        res = pool.map(_oracle_step_timing, batch, chunksize=1)
+        if r >= args.warmup:
+            t_steps.append(time.perf_counter() - t0)
+            upd += sum(N for N, _ in res)
+    pool.close()
+    pool.join()
+    el = sum(t_steps)
+    value = upd / el
+    desc = (f"per bench step, one FP64 oracle theta-step (sparse LU + one extended-precision "
+            f"refinement) on each of the {cores} host cores, on the {m} x {n} version of the "
+            f"workload's mesh, levels spread over the schedule")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / len(levels),
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD, "m": sample.m, "n": sample.n, "N": sample.N,
-                       "sample_of": f"{M_RINGS} x {N_ANGLES}"},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "config": {"workload": w["desc"], "m": m, "n": n, "N": m * n + 1,
+                       "sample_of": args.workload},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": desc},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
+
+
+def sample_rows(prob, count=20000, seed=15879):
+    """The origin, rings 1, 2, m-1 and m at 64 spread angles, and random cells."""
+    m, n = prob.m, prob.n
+    rng = np.random.default_rng(seed)
+    js = np.linspace(0, n - 1, 64).astype(np.int64)
+    special = [0]
+    for i in (1, 2, m - 1, m):
+        special.extend(1 + js * m + (i - 1))
+    return np.unique(np.concatenate([special, rng.integers(1, prob.N, count)]))
+
+
+def step_residual_rows(prob, rows, k, U_old, U_new):
+    """max_i |(e - A U_new)_i| / A_ii / max|U_new| over `rows`, A and e of the oracle
+    (its rows built from those cells' faces alone; extended-precision products)."""
+    from oracle import polar_oracle as po
+    L, B = po.conservative_operator(prob, rows)
+    fo, go = po.source(prob, prob.t[k])
+    fn, gn = po.source(prob, prob.t[k + 1])
+    res = po.step_residual(L, B, U_old, U_new, prob.t[k + 1] - prob.t[k], prob.theta_w,
+                           fo, go, fn, gn, rows)
+    return float(np.max(np.abs(res)) / np.max(np.abs(U_new)))
 
 
 # ------------------------------------------------------------------------- GPU arm
@@ -244,6 +343,14 @@ def run_native(args):
     world = env_int("WORLD_SIZE", 1)
     rank = env_int("RANK", 0)
     local = env_int("LOCAL_RANK", 0)
+    w = WORKLOADS[args.workload]
+    K_sched = w["K"]
+    # the oracle's workers start (spawn) before this process touches the GPU
+    cores = host_cores()
+    pool = None
+    want_cpu = rank == 0 and world == 1 and not args.no_cpu_baseline
+    if want_cpu:
+        pool = oracle_pool(args.workload, *w["sample"], cores)
     if not torch.cuda.is_available():
         raise RuntimeError("bench.py needs a CUDA GPU (the library has no CPU path)")
     torch.cuda.set_device(local)
@@ -257,111 +364,149 @@ def run_native(args):
             dist.barrier()
         torch.cuda.synchronize()
 
-    prob = make_problem()
+    t_setup = time.perf_counter()
+    prob = make_problem(args.workload)
+    setup_s = time.perf_counter() - t_setup
     stream = torch.cuda.current_stream()
     t_all = np.asarray(prob.t)
     W = prob.weight_table()
-    exact = {}
-    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
-    levels, consecutive = step_levels(args.steps)
+    levels, consecutive = step_levels(K_sched, args.steps)
+    big = prob.N * 8 > 256 * 1024 * 1024      # one FP64 field alone is larger than L2
+    flush = None if big else torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32,
+                                         device="cuda")
+    host_u = torch.empty(prob.N, dtype=torch.float64).pin_memory()
 
-    def timed_run(precision, timers):
-        """Warm-up, then the K timed steps; returns the measurements of this precision."""
+    def exact_into(k, out):
+        np.copyto(out.numpy(), prob.exact(t_all[k]))
+        return out
+
+    def timed_run(precision, timers, steps=None):
+        """Warm-up, then the timed steps; returns the measurements of this precision."""
         ctx = driver.create(prob, precision, stream=stream.cuda_stream)
 
         def set_level(k):
-            if k not in exact:
-                exact[k] = np.ascontiguousarray(prob.exact(t_all[k]))
-            P.polar_set_state(ctx, exact[k], t_all[k])
+            P.polar_set_state(ctx, exact_into(k, host_u), t_all[k])
 
-        wl, _ = step_levels(max(args.warmup, 1))
+        lv = levels if steps is None else levels[:steps]
+        wl, _ = step_levels(K_sched, max(args.warmup, 1))
         for k in wl[:args.warmup]:
             set_level(k)
             P.polar_advance(ctx, t_all[k:k + 2], prob.theta_w, W[k:k + 2])
         torch.cuda.synchronize()
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-              for _ in levels]
-        iters, refs, checkpoints = [], [], {}
+              for _ in lv]
+        stats = []
         launches0 = P.polar_kernel_launches(ctx)
         if timers:
             P.polar_timing_enable(ctx, True)
-            # the per-kernel pass runs the kernels eagerly (ncu cannot see kernels inside
-            # conditional graph nodes); `ncu --profile-from-start off` captures this range
-            torch.cuda.profiler.start()
         barrier()
         wall0 = time.perf_counter()
-        for s, k in enumerate(levels):
+        for s, k in enumerate(lv):
             if not consecutive or k == 0:
                 set_level(k)
-            flush.fill_(float(s))
+            if flush is not None:
+                flush.fill_(float(s))
             ev[s][0].record(stream)
             st, _ = P.polar_advance(ctx, t_all[k:k + 2], prob.theta_w, W[k:k + 2])
             ev[s][1].record(stream)
-            iters.append(st[0]["iters"])
-            refs.append(st[0]["refinements"])
-            if consecutive and not timers and (k + 1) % 100 == 0:
-                checkpoints[k + 1] = P.polar_get_state(ctx)[0]
+            stats.append(st[0])
         barrier()
-        if timers:
-            torch.cuda.profiler.stop()
         wall = time.perf_counter() - wall0
         launches = P.polar_kernel_launches(ctx) - launches0
         kstats = P.polar_timing_query(ctx) if timers else {}
         P.polar_timing_enable(ctx, False)
         dev_ms = max_over_ranks(dist, sum(a.elapsed_time(b) for a, b in ev))
-        U_last, t_last = P.polar_get_state(ctx)
         return dict(ctx=ctx, dev_ms=dev_ms, wall=wall, launches=launches, kstats=kstats,
-                    iters=float(np.mean(iters)), refs=float(np.mean(refs)), U=U_last, t=t_last,
-                    set_level=set_level, checkpoints=checkpoints)
+                    stats=stats, steps=len(lv), set_level=set_level)
+
+    def mean(stats, key):
+        return float(np.mean([s[key] for s in stats]))
+
+    def accuracy_states(run, acc_levels):
+        """The state after one step from each accuracy level (host copies)."""
+        out = {}
+        for k in acc_levels:
+            run["set_level"](k)
+            st, _ = P.polar_advance(run["ctx"], t_all[k:k + 2], prob.theta_w, W[k:k + 2])
+            assert st[0]["status"] == 0, st[0]
+            out[k] = P.polar_get_state(run["ctx"])[0]
+        return out
 
     precision = P.POLAR_MIXED if args.precision == "mixed" else P.POLAR_FP64
     other = P.POLAR_FP64 if precision == P.POLAR_MIXED else P.POLAR_MIXED
+    name_of = {P.POLAR_MIXED: "mixed", P.POLAR_FP64: "fp64"}
+    acc_levels = sorted(set(levels[:1] + levels[len(levels) // 2:len(levels) // 2 + 1]))
+    # the oracle's full-size steps at the accuracy levels run on the host cores meanwhile
+    full_oracle = None
+    if w["check"] == "full" and want_cpu:
+        pool_full = mp.get_context("spawn").Pool(len(acc_levels), initializer=_oracle_init,
+                                                 initargs=(args.workload, None, None))
+        full_oracle = (pool_full, pool_full.map_async(_oracle_step, acc_levels, chunksize=1))
+
     clocks = ClockSampler(local)
     clocks.start()
     main = timed_run(precision, False)
     clk = clocks.stop()
-    # per-kernel CUDA events on a second pass over the same steps (kept out of the
+    acc = {name_of[precision]: accuracy_states(main, acc_levels)}
+    # per-kernel CUDA events on a pass of its own over the first steps (kept out of the
     # headline run, whose launch rate the event records would perturb)
-    prof = timed_run(precision, True)
-    comp = timed_run(other, False) if args.compare else None
+    prof = timed_run(precision, True, steps=min(len(levels), 4))
+    del prof["ctx"]
+    comp = None
+    if args.compare:
+        comp = timed_run(other, False)
+        acc[name_of[other]] = accuracy_states(comp, acc_levels)
+        del comp["ctx"]
     ctx, dev_ms = main["ctx"], main["dev_ms"]
     kstats = prof["kstats"]
-    set_level = main["set_level"]
-    U_last, t_last = main["U"], main["t"]
-    launches, wall = main["launches"], main["wall"]
-    iters, refs = [main["iters"]], [main["refs"]]
-    err_exact = float(np.max(np.abs(U_last - prob.exact(t_last))) /
-                      np.max(np.abs(prob.exact(t_last))))
-    err_cp = {k: float(np.max(np.abs(U - prob.exact(t_all[k]))) / np.max(np.abs(prob.exact(t_all[k]))))
-              for k, U in sorted(main["checkpoints"].items())}
     updates = prob.N * len(levels) * world
     value = updates / (dev_ms * 1e-3)
     compare = None
     if comp is not None:
-        diff = float(np.max(np.abs(main["U"] - comp["U"])) / np.max(np.abs(comp["U"])))
-        # relative max-norm difference at the checkpoints t_100, t_200, ... (consecutive runs)
-        cp = {k: float(np.max(np.abs(main["checkpoints"][k] - comp["checkpoints"][k])) /
-                       np.max(np.abs(comp["checkpoints"][k])))
-              for k in sorted(main["checkpoints"]) if k in comp["checkpoints"]}
-        compare = {"precision": "fp64" if other == P.POLAR_FP64 else "mixed",
-                   "value": updates / (comp["dev_ms"] * 1e-3), "ms_per_step": comp["dev_ms"] / len(levels),
-                   "krylov_iters_per_step": comp["iters"], "refinements_per_step": comp["refs"],
+        compare = {"precision": name_of[other],
+                   "value": updates / (comp["dev_ms"] * 1e-3),
+                   "ms_per_step": comp["dev_ms"] / len(levels),
+                   "krylov_iters_per_step": mean(comp["stats"], "iters"),
+                   "refinements_per_step": mean(comp["stats"], "refinements"),
                    "speedup_of_headline": comp["dev_ms"] / dev_ms,
-                   "rel_max_diff_final_state": diff,
-                   "rel_max_diff_at_checkpoints": cp}
+                   "rel_max_diff_mixed_vs_fp64": {
+                       str(k): rel_max(acc["mixed"][k], acc["fp64"][k]) for k in acc_levels}}
+
+    # ---- accuracy against the oracle, per precision, on the steps from acc_levels
+    err = {"levels": acc_levels}
+    if w["check"] == "full" and full_oracle is not None:
+        pool_full, res = full_oracle
+        ref = {k: r[2] for k, r in zip(acc_levels, res.get())}
+        pool_full.close()
+        pool_full.join()
+        err["kind"] = ("relative max-norm difference from the oracle's step (sparse LU + "
+                       "extended-precision refinement) from the same state")
+        for nm, states in acc.items():
+            err[nm] = {str(k): rel_max(states[k], ref[k]) for k in acc_levels}
+    elif w["check"] == "rows":
+        rows = sample_rows(prob)
+        err["kind"] = (f"Jacobi-scaled residual max|(e - A U)_i| / A_ii / max|U| of the GPU's "
+                       f"new level in the oracle's step equation, on {len(rows)} sampled rows "
+                       f"(origin, rings 1, 2, m-1, m, random cells); bar 3e-14")
+        for nm, states in acc.items():
+            err[nm] = {str(k): step_residual_rows(prob, rows, k, prob.exact(t_all[k]), states[k])
+                       for k in acc_levels}
 
     # ---- end to end: pinned host state in, pinned host state out, every step
-    ke = sorted(set(levels))[:: max(1, len(set(levels)) // 20)][:20]
-    host_in = {k: torch.from_numpy(np.ascontiguousarray(prob.exact(t_all[k]))).pin_memory()
-               for k in ke}
+    ke = levels[:min(len(levels), 8)]
     host_out = torch.empty(prob.N, dtype=torch.float64).pin_memory()
+    host_in = [exact_into(k, torch.empty(prob.N, dtype=torch.float64).pin_memory())
+               for k in ke[:2]]
     barrier()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e_ms = 0.0
-    for k in ke:
-        flush.fill_(1.0)
+    for s, k in enumerate(ke):
+        if s >= 2:
+            exact_into(k, host_in[s % 2])
+        if flush is not None:
+            flush.fill_(1.0)
         e0.record(stream)
-        P.polar_set_state(ctx, host_in[k], t_all[k])
+        P.polar_set_state(ctx, host_in[s % 2] if s >= 2 else host_in[s], t_all[k])
         P.polar_advance(ctx, t_all[k:k + 2], prob.theta_w, W[k:k + 2])
         P.polar_get_state(ctx, host_out)
         e1.record(stream)
@@ -379,30 +524,37 @@ def run_native(args):
         achieved = d["bytes"] / (d["ms"] * 1e-3) / 1e9
         per_launch = d["bytes"] / max(d["launches"], 1)
         roof = {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": peak,
-                "peak_source": peak_src, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": NCU_TRAFFIC.get(name), "algorithmic_bytes_per_launch": per_launch,
+                "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)" if peak_src ==
+                "measured" else peak_src, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": NCU_TRAFFIC.get((args.workload, name)),
+                "algorithmic_bytes_per_launch": per_launch,
                 "avg_launch_us": 1e3 * d["ms"] / max(d["launches"], 1),
                 "share_of_step": d["ms"] / prof["dev_ms"],
-                "timing": "CUDA events around every launch, second pass over the same steps"}
+                "timing": "CUDA events around every launch on the context's stream, eager "
+                          "pass over the first timed steps"}
 
+    stats = main["stats"]
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dev_ms / len(levels),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64" if precision == P.POLAR_FP64 else "f32+f64",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD, "m": prob.m, "n": prob.n, "N": prob.N,
+            "config": {"workload": w["desc"], "m": prob.m, "n": prob.n, "N": prob.N,
                        "precision": args.precision,
                        "levels": "consecutive" if consecutive else
-                                 f"{len(levels)} steps spread over the 1000-level schedule",
-                       "l2": "flushed (512 MB write) before every timed step",
+                                 f"{len(levels)} steps spread over the {K_sched}-level schedule, "
+                                 f"each from the manufactured state at its level",
+                       "l2": ("inputs larger than L2 (1.07 GB per FP64 field)" if big else
+                              "flushed (512 MB write) before every timed step"),
                        "parallelism": f"replicas x{world}"},
-            "krylov_iters_per_step": float(np.mean(iters)),
-            "refinements_per_step": float(np.mean(refs)),
-            "rel_err_vs_manufactured_last_step": err_exact,
-            "rel_err_vs_manufactured_at_checkpoints": err_cp,
+            "krylov_iters_per_step": mean(stats, "iters"),
+            "fp64_krylov_iters_per_step": mean(stats, "fp64_iters"),
+            "refinements_per_step": mean(stats, "refinements"),
             "compare": compare,
-            "wall_s": wall,
-            "gpu_launches": int(launches),
+            "err_vs_oracle": err,
+            "wall_s": main["wall"],
+            "setup_s": setup_s,
+            "gpu_launches": int(main["launches"]),
             "clocks": clk,
             "roofline": roof,
             "kernels": {k: {"launches": v["launches"], "ms": round(v["ms"], 3),
@@ -410,12 +562,19 @@ def run_native(args):
                         for k, v in sorted(kstats.items(), key=lambda kv: -kv[1]["ms"])},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": prob.N * 8,
                     "d2h_bytes_per_step": prob.N * 8, "steps": len(ke)}}
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        v, nsteps, secs = oracle_sample(args.cpu_budget, prob)
+    if pool is not None:
+        v_all, v_one, nsteps, secs = oracle_sample(pool, cores, K_sched, args.cpu_budget)
+        pool.close()
+        pool.join()
+        m_s, n_s = w["sample"]
         line["cpu_baseline"] = {
-            "value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{nsteps} full-size theta-steps of the workload ({secs:.1f} s; sparse LU "
-                      f"+ one extended-precision refinement, single-threaded SuperLU)"}
+            "value": v_all, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "single_core_value": v_one,
+            "sample": f"{nsteps} FP64 oracle theta-steps (sparse LU + one extended-precision "
+                      f"refinement each) on the {m_s} x {n_s} version of the workload's mesh, "
+                      f"levels spread over the schedule, {cores} single-threaded workers in "
+                      f"parallel for {secs:.1f} s; single_core_value = updates / summed "
+                      f"per-step seconds"}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist is not None:
@@ -522,14 +681,12 @@ def run_batch(args):
 def run_profile_step(args):
     """One eager theta-step of a named workload inside a CUDA profiler range, after the
     autotuner and a warm-up step, with per-kernel CUDA-event times (for
-    `ncu --profile-from-start off`).  Workloads: c2 (the bench workload), c3 (continuity
-    2048 x 4096, 2000-level time stretch), c5 (continuity 8192 x 16384 graded to r = 1,
-    theta = 0.6, 200 levels).  The step is the third level of the schedule."""
+    `ncu --profile-from-start off`) of one of WORKLOADS, at full size or, with --mesh
+    M N, on the same recipe's M x N mesh.  The step is the third level of the schedule."""
     import torch
-    import polar_inputs as pi
     import paper_2509_15879_gb300 as P
     from paper_2509_15879_gb300 import driver
-    prob = {"c2": make_problem, "c3": pi.config3, "c5": pi.config5}[args.workload]()
+    prob = make_problem(args.workload, *(args.mesh or (None, None)))
     precision = P.POLAR_MIXED if args.precision == "mixed" else P.POLAR_FP64
     t = np.asarray(prob.t)
     W = prob.weight_table()
@@ -555,7 +712,7 @@ def run_profile_step(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["native", "reference"], default="native")
     ap.add_argument("--precision", choices=["fp64", "mixed"], default="mixed",
@@ -564,19 +721,19 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--compare", type=int, default=1,
                     help="also time the other precision on the same steps")
-    ap.add_argument("--workload", choices=["c2", "batch", "c3", "c5"], default="c2",
-                    help="c2: the timed workload; batch: the 256-instance sweep; c3/c5: only "
-                         "with --profile-step")
+    ap.add_argument("--workload", choices=["c5", "c3", "c2", "batch"], default="c5",
+                    help="c5 (default): continuity 8192 x 16384; c3: continuity 2048 x 4096; "
+                         "c2: parabolic 512 x 1024; batch: the 256-instance sweep")
     ap.add_argument("--profile-step", action="store_true",
                     help="run one eager step of --workload inside a profiler range")
+    ap.add_argument("--mesh", type=int, nargs=2, metavar=("M", "N"),
+                    help="with --profile-step: the workload's recipe on an M x N mesh")
     ap.add_argument("--instances", type=int, default=256)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
     if args.profile_step:
         return run_profile_step(args)
-    if args.workload in ("c3", "c5"):
-        ap.error("--workload c3/c5 needs --profile-step")
     if args.workload == "batch":
         return run_batch(args)
     return run_native(args)

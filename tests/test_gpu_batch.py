@@ -37,7 +37,9 @@ def test_batch_matches_single_and_oracle(precision):
         assert np.array_equal(U, Ua)
         assert [s["iters"] for s in row] == [s["iters"] for s in st_alone]
         ref = po.run(p, K)
-        assert np.max(np.abs(U - ref)) / np.max(np.abs(ref)) < tol
+        err = np.max(np.abs(U - ref)) / np.max(np.abs(ref))
+        print(f"PARITY batch instance {p.m}x{p.n} precision {precision}: {err:.2e} (bar {tol:g})")
+        assert err < tol
 
 
 def test_batch_failure_is_per_instance():

@@ -88,6 +88,8 @@ def test_c2_full_steps_match_oracle(c2_reference, precision, tol):
     for k, (U, Uref, kappa) in ref.items():
         Un, _ = _gpu_step(ctx, prob, k, U)
         bar = max(tol, 20.0 * kappa * np.finfo(float).eps)
+        print(f"PARITY C2 512x1024 level {k} precision {precision}: {_rel(Un, Uref):.2e} "
+              f"(bar {bar:.1e} = max(stated {tol:g}, 20 kappa eps), kappa {kappa:.2e})")
         assert _rel(Un, Uref) < bar, (k, _rel(Un, Uref), bar, kappa)
 
 
@@ -106,12 +108,18 @@ def test_c3_full_step_equation(c3_problem, precision):
     U = np.asarray(prob.u0)
     for k in (0, 1):                         # consecutive steps from the initial state
         Un, _ = _gpu_step(ctx, prob, k)
-        assert _scaled_residual(prob, L, B, U, Un, k) < RES_TOL, k
+        res = _scaled_residual(prob, L, B, U, Un, k)
+        print(f"PARITY C3 2048x4096 level {k} precision {precision}: step residual {res:.2e} "
+              f"(bar {RES_TOL:g})")
+        assert res < RES_TOL, k
         U = Un
     k = 1000                                 # mid-schedule, from the manufactured state
     U = np.ascontiguousarray(prob.exact(prob.t[k]))
     Un, _ = _gpu_step(ctx, prob, k, U)
-    assert _scaled_residual(prob, L, B, U, Un, k) < RES_TOL, k
+    res = _scaled_residual(prob, L, B, U, Un, k)
+    print(f"PARITY C3 2048x4096 level {k} precision {precision}: step residual {res:.2e} "
+          f"(bar {RES_TOL:g})")
+    assert res < RES_TOL, k
 
 
 # --------------------------------------------------------------------- 256 instances
@@ -134,6 +142,8 @@ def test_c4_full_batch_step_equation(c4_problems, precision):
         U, t = P.polar_get_state(c)
         assert t == p.t[1]
         worst = max(worst, _scaled_residual(p, L, B, u0, U, 0))
+    print(f"PARITY C4 256 instances step 0 precision {precision}: worst step residual "
+          f"{worst:.2e} (bar {RES_TOL:g})")
     assert worst < RES_TOL, worst
 
 
@@ -156,5 +166,8 @@ def test_c5_full_sampled_step_equation(precision):
     ctx = driver.create(prob, precision)
     U = np.asarray(prob.u0)
     Un, st = _gpu_step(ctx, prob, 0)
-    assert _scaled_residual(prob, L, B, U, Un, 0, rows) < RES_TOL
+    res = _scaled_residual(prob, L, B, U, Un, 0, rows)
+    print(f"PARITY C5 8192x16384 level 0 precision {precision}: step residual {res:.2e} on "
+          f"{len(rows)} rows (bar {RES_TOL:g}); {st}")
+    assert res < RES_TOL
     assert st["iters"] > 0
