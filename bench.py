@@ -398,7 +398,10 @@ def run_native(args):
         stats = []
         launches0 = P.polar_kernel_launches(ctx)
         if timers:
+            # the per-kernel pass runs the kernels eagerly (ncu does not see kernels inside
+            # conditional graph nodes); `ncu --profile-from-start off` captures this range
             P.polar_timing_enable(ctx, True)
+            torch.cuda.profiler.start()
         barrier()
         wall0 = time.perf_counter()
         for s, k in enumerate(lv):
@@ -411,6 +414,8 @@ def run_native(args):
             ev[s][1].record(stream)
             stats.append(st[0])
         barrier()
+        if timers:
+            torch.cuda.profiler.stop()
         wall = time.perf_counter() - wall0
         launches = P.polar_kernel_launches(ctx) - launches0
         kstats = P.polar_timing_query(ctx) if timers else {}

@@ -147,8 +147,22 @@ int polar_get_state(polar_ctx* ctx, double* u, double* t, int32_t memory);
  * runs the inner solve (vectors, operator, V-cycle) in FP32 and the residual and update
  * in FP64, and after a sweep that gains less than a factor 10 (FP32 cannot resolve rows
  * whose couplings exceed their row sums by about 1/eps32, e.g. long rings next to the
- * origin) finishes the step with FP64 BiCGStab preconditioned by the FP32 V-cycle.
- * Both paths stop at the same FP64 tolerance.
+ * origin), or an FP32 solve that breaks down or reaches max_iter, finishes the step with
+ * the FP64 inner solve (FP64 vectors, operator, V-cycle and ring factors, the factors
+ * formed when first needed for the step's dt and theta).  Both paths stop at the same
+ * FP64 tolerance.
+ *
+ * Separable operators -- uniform angles and ring coefficients that do not depend on the
+ * angle (D, b and a radial drift depending on r only; the parabolic equation of
+ * Section 2.1) -- have a direct inner solve instead: the discrete Fourier transform along
+ * theta diagonalises the periodic angular coupling, each Fourier mode is one tridiagonal
+ * system in r, and the origin row couples to the mean mode only (the Swarztrauber-Sweet
+ * structure of Section 2.1).  It runs in FP64 in both precisions (O(N log n)); one
+ * refinement sweep normally reaches the tolerance.  polar_set_coeffs detects
+ * separability (coefficients equal across angles to 1e-9 relative, angular couplings
+ * equal on both sides; the direct solve uses the coefficients of angle 0 and the FP64
+ * refinement absorbs the difference); the transform holds rings of n <= 8192 angles when n is a power
+ * of two, n <= 4096 otherwise.
  *
  * Solver controls (NULL -> defaults).
  *   tol         stop when max_i |r_i| / A_ii <= tol * max_i |U_i|, r = e - A U
@@ -158,22 +172,32 @@ int polar_get_state(polar_ctx* ctx, double* u, double* t, int32_t memory);
  *   inner_tol   reduction of the Jacobi-scaled max norm max_i |r_i| / A_ii that each FP32
  *               inner solve of the MIXED path reaches; default 1e-5.  Every inner solve
  *               (both paths) also goes at least as far as the outer test still needs:
- *               a tenth of tol * max_i |U_i| after its correction. */
+ *               a tenth of tol * max_i |U_i| after its correction.
+ *   method      POLAR_SOLVE_AUTO (default): the direct solve when the operator is
+ *               separable, else the Krylov solve; POLAR_SOLVE_KRYLOV; POLAR_SOLVE_DIRECT
+ *               (POLAR_EINVAL when the operator is not separable). */
+enum { POLAR_SOLVE_AUTO = 0, POLAR_SOLVE_KRYLOV = 1, POLAR_SOLVE_DIRECT = 2 };
 typedef struct {
   double tol;
   int32_t max_iter;
   int32_t max_refine;
   double inner_tol;
+  int32_t method;
+  int32_t reserved;
 } polar_solver_opts;
+
+/* 1 when the operator set by the last polar_set_coeffs is separable (the direct solve
+ * applies), 0 when it is not, POLAR_ESTATE before polar_set_coeffs. */
+int polar_is_separable(const polar_ctx* ctx);
 
 typedef struct {
   int32_t iters;         /* Krylov iterations of all inner solves                     */
   int32_t refinements;   /* FP64 residual evaluations (one more than the inner solves) */
   int32_t status;        /* POLAR_OK or the error of this step                        */
-  int32_t fp64_iters;    /* MIXED: of iters, those of FP64 Krylov solves over the FP32
-                            V-cycle, which the step switches to once a sweep of FP32
-                            refinement gains less than a factor 10 (or an FP32 solve
-                            breaks down or hits max_iter); 0 for FP64                 */
+  int32_t fp64_iters;    /* MIXED: of iters, those of FP64 inner solves, which the step
+                            switches to once a sweep of FP32 refinement gains less than
+                            a factor 10 (or an FP32 solve breaks down or hits
+                            max_iter); 0 for FP64                                     */
   double scaled_resid;   /* final max |r_i| / A_ii / max |U_i|                        */
 } polar_step_stats;
 

@@ -42,9 +42,12 @@ class polar_coeffs(C.Structure):
                 ("bnd", C.c_void_p * 4)]
 
 
+POLAR_SOLVE_AUTO, POLAR_SOLVE_KRYLOV, POLAR_SOLVE_DIRECT = 0, 1, 2
+
+
 class polar_solver_opts(C.Structure):
     _fields_ = [("tol", C.c_double), ("max_iter", C.c_int32), ("max_refine", C.c_int32),
-                ("inner_tol", C.c_double)]
+                ("inner_tol", C.c_double), ("method", C.c_int32), ("reserved", C.c_int32)]
 
 
 class polar_step_stats(C.Structure):
@@ -77,6 +80,7 @@ EXPORTS = {
     "polar_apply_operator": (C.c_int, [C.c_void_p, C.c_double, C.c_double, C.c_void_p,
                                        C.c_void_p, C.c_int32]),
     "polar_kernel_launches": (C.c_int64, [C.c_void_p]),
+    "polar_is_separable": (C.c_int, [C.c_void_p]),
     "polar_apply_rows_noalloc": (C.c_int, [C.c_int32, C.c_int32] + [C.c_void_p] * 6 +
                                  [C.c_double, C.c_double, C.c_void_p, C.c_void_p, C.c_void_p]),
     "polar_batch_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int32, C.c_void_p,
@@ -276,7 +280,8 @@ def _opts(opts):
     if opts is None:
         return None
     o = polar_solver_opts(opts.get("tol", 0.0), opts.get("max_iter", 0),
-                          opts.get("max_refine", 0), opts.get("inner_tol", 0.0))
+                          opts.get("max_refine", 0), opts.get("inner_tol", 0.0),
+                          opts.get("method", POLAR_SOLVE_AUTO), 0)
     return C.byref(o)
 
 
@@ -329,6 +334,13 @@ def polar_apply_rows_noalloc(m, n, R, W, E, S, N, o, alpha, beta, x, y, stream=N
 
 def polar_kernel_launches(ctx: Ctx) -> int:
     return int(load().polar_kernel_launches(ctx.handle))
+
+
+def polar_is_separable(ctx: Ctx) -> bool:
+    rc = load().polar_is_separable(ctx.handle)
+    if rc < 0:
+        _check(rc)
+    return rc == 1
 
 
 class Batch:

@@ -22,6 +22,7 @@
 #include <vector>
 
 #include "../../include/polar.h"
+#include "polar_fft.h"
 #include "polar_host.h"
 #include "polar_internal.h"
 
@@ -62,10 +63,12 @@ struct DevLevel {
   float *w32, *e32, *s32, *nn32, *o32, *ia32, *ib32;
   // per-step refresh, FP64 (FP64 path; level 0 diag also for the mixed path)
   double *diag, *fl, *fui, *fcu, *fq, *fring, *fz;
+  double* dinv;  // level 0: 1 / diag of the FP64 operator
   // per-step refresh, FP32 (mixed path)
   float *diag32, *fl32, *fui32, *fcu32, *fq32, *fring32, *fz32, *rsum32;
   // V-cycle right-hand side and solution (levels >= 1), in the inner precision
   void *b, *x;
+  double *b64, *x64;  // the same in FP64 (b, x themselves in the FP64 path)
 };
 
 struct PendingTimer {
@@ -128,10 +131,18 @@ struct polar_ctx {
   int64_t graph_kernels_fixed = 0, graph_kernels_sweep = 0, graph_kernels_iter = 0;
   int64_t graph_kernels_iter64 = 0;  // mixed path: an FP64 Krylov iteration over the FP32 V-cycle
   bool symmetric = false;  // S is symmetric (no drift): CG instead of BiCGStab
+  // direct solve of separable operators (Fourier in theta, tridiagonal in r)
+  bool separable = false;     // the current coefficients are separable
+  bool direct_now = false;    // the current advance uses the direct inner solve
+  FftPlan plan{};
+  SepRings sep{};
+  double *fx_r = nullptr, *fx_i = nullptr, *fcp = nullptr, *fzv = nullptr;
   int64_t generation = 0;         // bumped whenever a captured graph goes stale
-  // ring-solve tile shapes per level, [mode * 2 + parity] (autotuned on first use)
-  std::vector<std::array<RingShape, 4>> tiles;
+  // ring-solve tile shapes per level, [mode * 2 + parity], for FP32 and FP64 ring solves
+  // (autotuned on first use; a mixed context tunes both)
+  std::vector<std::array<RingShape, 4>> tiles32, tiles64;
   bool tuned = false;
+  double* stamp64 = nullptr;  // mixed path: (alpha, beta) its FP64 factors were formed for
   bool autotune = true;
   // device-side schedule of a polar_advance (graph mode)
   StepParams* sched = nullptr;
@@ -344,19 +355,21 @@ int alloc_levels(polar_ctx* c) {
     for (double** p : s64) TRY(dalloc(c, p, nv));
     TRY(dalloc(c, &d.o, (size_t)c->n));
     TRY(dalloc(c, &d.sc, 8));
-    if (!mixed || l == 0) TRY(dalloc(c, &d.diag, nv));
+    if (l == 0) TRY(dalloc(c, &d.dinv, nv));
+    // FP64 per-step factors and coarse vectors: the FP64 path's, and in the mixed path
+    // those of its FP64 solve, which takes over a step whose FP32 refinement stalls
+    TRY(dalloc(c, &d.diag, nv));
+    double** f64[] = {&d.fl, &d.fui, &d.fcu, &d.fq};
+    for (double** p : f64) TRY(dalloc(c, p, nv));
+    TRY(dalloc(c, &d.fring, nr));
+    TRY(dalloc(c, &d.fz, (size_t)c->n));
+    if (l > 0) {
+      TRY(dalloc(c, &d.b64, nv));
+      TRY(dalloc(c, &d.x64, nv));
+    }
     if (!mixed) {
-      double** f64[] = {&d.fl, &d.fui, &d.fcu, &d.fq};
-      for (double** p : f64) TRY(dalloc(c, p, nv));
-      TRY(dalloc(c, &d.fring, nr));
-      TRY(dalloc(c, &d.fz, (size_t)c->n));
-      if (l > 0) {
-        double *b = nullptr, *x = nullptr;
-        TRY(dalloc(c, &b, nv));
-        TRY(dalloc(c, &x, nv));
-        d.b = b;
-        d.x = x;
-      }
+      d.b = d.b64;
+      d.x = d.x64;
     } else {
       float** s32[] = {&d.w32, &d.e32, &d.s32, &d.nn32, &d.ia32, &d.ib32};
       for (float** p : s32) TRY(dalloc(c, p, nv));
@@ -394,6 +407,7 @@ int alloc_levels(polar_ctx* c) {
     a.ia = d.ia;
     a.ib = d.ib;
     a.diag = d.diag;
+    a.dinv = d.dinv;
     a.fl = d.fl;
     a.fui = d.fui;
     a.fcu = d.fcu;
@@ -483,22 +497,40 @@ const std::vector<LevelView<T>>& views(const polar_ctx* c) {
 
 // Per-step refresh: the matrix S = alpha V + beta V L changes with dt and theta.  The
 // kernel reads alpha, beta and do_refresh from the step parameters.
+// `stamp` (the mixed path's FP64 factors): formed on demand, once per (alpha, beta).
 template <typename T>
-int launch_refresh_all(polar_ctx* c) {
+int launch_refresh_all(polar_ctx* c, double* stamp = nullptr) {
   std::vector<LevelView<T>> vt = views<T>(c);
   double pts = 0.0;
   for (const DevLevel& d : c->lv) pts += (double)d.sh.m * d.sh.n;
   // reads 6 FP64 coefficient arrays, writes diag and 4 factor arrays
-  TLAUNCH("refresh", pts * (6.0 * 8 + 5.0 * sizeof(T)),
-          launch_refresh<T>(c->v64.data(), vt.data(), c->nlev(), c->sp, c->ws, c->cs));
+  TLAUNCH(stamp ? "refresh64" : "refresh", pts * (6.0 * 8 + 5.0 * sizeof(T)),
+          launch_refresh<T>(c->v64.data(), vt.data(), c->nlev(), c->sp, c->ws, c->cs, stamp));
   return POLAR_OK;
 }
 
+template <typename T>
+std::vector<std::array<RingShape, 4>>& tiles_of(polar_ctx* c) {
+  return sizeof(T) == 8 ? c->tiles64 : c->tiles32;
+}
+
 // tuned tile shape of a ring-solve launch (null: the launcher's default)
-const RingShape* tile(const polar_ctx* c, int l, int mode, int parity) {
-  if (!c->tuned || l >= (int)c->tiles.size()) return nullptr;
-  const RingShape& s = c->tiles[l][mode * 2 + parity];
+template <typename T>
+const RingShape* tile(polar_ctx* c, int l, int mode, int parity) {
+  const std::vector<std::array<RingShape, 4>>& t = tiles_of<T>(c);
+  if (!c->tuned || l >= (int)t.size()) return nullptr;
+  const RingShape& s = t[l][mode * 2 + parity];
   return s.P > 0 ? &s : nullptr;
+}
+
+// V-cycle vectors of level l >= 1 in precision T
+template <typename T>
+T* coarse_b(const polar_ctx* c, int l) {
+  return static_cast<T*>(sizeof(T) == 8 ? static_cast<void*>(c->lv[l].b64) : c->lv[l].b);
+}
+template <typename T>
+T* coarse_x(const polar_ctx* c, int l) {
+  return static_cast<T*>(sizeof(T) == 8 ? static_cast<void*>(c->lv[l].x64) : c->lv[l].x);
 }
 
 // x = M^{-1} b: one V(1,1) cycle of the radial multigrid (polar_mg.cu), one kernel per
@@ -514,8 +546,8 @@ int vcycle(polar_ctx* c, const T* b, T* x) {
   const int* done = (c->cs == c->st) ? &c->ks->done : nullptr;
   const double B = sizeof(T);
   const Params par = c->par();
-  auto bof = [&](int l) { return l == 0 ? b : static_cast<const T*>(c->lv[l].b); };
-  auto xof = [&](int l) { return l == 0 ? x : static_cast<T*>(c->lv[l].x); };
+  auto bof = [&](int l) { return l == 0 ? b : static_cast<const T*>(coarse_b<T>(c, l)); };
+  auto xof = [&](int l) { return l == 0 ? x : coarse_x<T>(c, l); };
   // kernel classes are timed per level group: the fine level, level 1, and the rest
   auto nm = [&](const char* base, int l) {
     static thread_local std::string s;
@@ -531,12 +563,12 @@ int vcycle(polar_ctx* c, const T* b, T* x) {
     // w, e, ia, ib of the odd rings and x of the even ones, writes the coarse rhs
     TLAUNCH(nm("ring_pre_odd", l), 6 * B * po,
             launch_ring<T>(L[l], L[l + 1], bof(l), xof(l), nullptr, par, 1, RING_PRE, done, c->cs,
-                           tile(c, l, RING_PRE, 1)));
+                           tile<T>(c, l, RING_PRE, 1)));
     TLAUNCH(nm("ring_pre_even", l), 9 * B * pe,
             launch_ring<T>(L[l], L[l + 1], bof(l), xof(l), nullptr, par, 0, RING_PRE, done, c->cs,
-                           tile(c, l, RING_PRE, 0)));
+                           tile<T>(c, l, RING_PRE, 0)));
     TLAUNCH(nm("restrict", l), B * (4 * po + 2 * pe),
-            launch_restrict<T>(L[l], L[l + 1], xof(l), static_cast<T*>(c->lv[l + 1].b), par, done,
+            launch_restrict<T>(L[l], L[l + 1], xof(l), coarse_b<T>(c, l + 1), par, done,
                                c->cs));
   }
   TLAUNCH("coarsest", 8 * B * L[nl - 1].sh.n,
@@ -547,11 +579,11 @@ int vcycle(polar_ctx* c, const T* b, T* x) {
     // even rings after the correction also read x, ia, ib of the odd rings and the
     // coarse solution (8 per even point + 3 per odd point + 1 per coarse point)
     TLAUNCH(nm("ring_post_even", l), B * (8 * pe + 3 * po + pe),
-            launch_ring<T>(L[l], L[l + 1], bof(l), xof(l), static_cast<const T*>(c->lv[l + 1].x),
-                           par, 0, RING_POST, done, c->cs, tile(c, l, RING_POST, 0)));
+            launch_ring<T>(L[l], L[l + 1], bof(l), xof(l), coarse_x<T>(c, l + 1),
+                           par, 0, RING_POST, done, c->cs, tile<T>(c, l, RING_POST, 0)));
     TLAUNCH(nm("ring_post_odd", l), 9 * B * po,
             launch_ring<T>(L[l], L[l + 1], bof(l), xof(l), nullptr, par, 1, RING_POST, done, c->cs,
-                           tile(c, l, RING_POST, 1)));
+                           tile<T>(c, l, RING_POST, 1)));
   }
   return POLAR_OK;
 }
@@ -588,7 +620,7 @@ int tune_rings(polar_ctx* c) {
   const std::vector<LevelView<T>>& L = views<T>(c);
   const int nl = c->nlev();
   const int lc = nl - 1;
-  c->tiles.assign(nl, std::array<RingShape, 4>{});
+  tiles_of<T>(c).assign(nl, std::array<RingShape, 4>{});
   CUDA_TRY(cudaMemsetAsync(&c->ks->done, 0, sizeof(int), c->st));
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   CUDA_TRY(cudaEventCreate(&e0));
@@ -597,9 +629,9 @@ int tune_rings(polar_ctx* c) {
   int rc = POLAR_OK;
   const int* done = &c->ks->done;
   for (int l = 0; l < lc && rc == POLAR_OK; ++l) {
-    T* b = l == 0 ? kvecs<T>(c).p : static_cast<T*>(c->lv[l].b);
-    T* x = l == 0 ? kvecs<T>(c).phat : static_cast<T*>(c->lv[l].x);
-    const T* X = static_cast<const T*>(c->lv[l + 1].x);
+    T* b = l == 0 ? kvecs<T>(c).p : coarse_b<T>(c, l);
+    T* x = l == 0 ? kvecs<T>(c).phat : coarse_x<T>(c, l);
+    const T* X = coarse_x<T>(c, l + 1);
     for (int mode = 0; mode < 2 && rc == POLAR_OK; ++mode)
       for (int parity = 0; parity < 2 && rc == POLAR_OK; ++parity) {
         const int lines = parity ? L[l].sh.no : L[l].sh.ne;
@@ -609,7 +641,7 @@ int tune_rings(polar_ctx* c) {
           std::lock_guard<std::mutex> g(g_tune_lock);
           auto it = g_tune_cache.find(key);
           if (it != g_tune_cache.end()) {
-            c->tiles[l][mode * 2 + parity] = it->second;
+            tiles_of<T>(c)[l][mode * 2 + parity] = it->second;
             continue;
           }
         }
@@ -639,12 +671,12 @@ int tune_rings(polar_ctx* c) {
             best = s;
           }
         }
-        c->tiles[l][mode * 2 + parity] = best;
+        tiles_of<T>(c)[l][mode * 2 + parity] = best;
         if (tune_log())
-          fprintf(stderr, "polar tune: %s level %d lines %d n %d %s %s -> RW %d TW %d P %d CS %d: "
-                  "%.2f us\n", sizeof(T) == 8 ? "fp64" : "fp32", l, lines, L[l].sh.n,
+          fprintf(stderr, "polar tune: %s level %d lines %d n %d %s %s -> RW %d TW %d P %d CS %d "
+                  "ST %d: %.2f us\n", sizeof(T) == 8 ? "fp64" : "fp32", l, lines, L[l].sh.n,
                   mode ? "post" : "pre", parity ? "odd" : "even", best.RW, best.TW, best.P,
-                  best.CS, 1e3 * best_ms / 3);
+                  best.CS, best.ST, 1e3 * best_ms / 3);
         std::lock_guard<std::mutex> g(g_tune_lock);
         g_tune_cache[key] = best;
       }
@@ -652,7 +684,6 @@ int tune_rings(polar_ctx* c) {
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   (void)cudaGetLastError();
-  if (rc == POLAR_OK) c->tuned = true;
   return rc;
 }
 
@@ -713,33 +744,6 @@ int krylov_iteration(polar_ctx* c, CondHandle cond) {
   return c->symmetric ? cg_iteration<T>(c, cond) : bicg_iteration<T>(c, cond);
 }
 
-// Mixed path fallback: one BiCGStab iteration in FP64 (vectors, matrix, scalars) whose
-// preconditioner is the FP32 V-cycle, entered and left through casts.  The FP32
-// rounding of the preconditioner changes only how fast the iteration converges, not the
-// FP64 residual it converges to.
-int bicg_iteration_x(polar_ctx* c, CondHandle cond) {
-  KVecs<double>& k = c->kv64;
-  KVecs<float>& f = c->kv32;
-  const LevelView<double>& L0 = c->v64[0];
-  const Reduce red = c->red();
-  const size_t nv = c->nv();
-  const double pts = (double)c->m * c->n;
-  TLAUNCH("cast", 12.0 * nv, launch_to_float(nv, k.p, f.r, c->cs));
-  TRY(vcycle<float>(c, f.r, f.phat));
-  TLAUNCH("cast", 12.0 * nv, launch_to_double(nv, f.phat, k.phat, c->cs));
-  TLAUNCH("stencil_dot", 64.0 * pts, launch_apply_dot<double>(L0, c->par(), k.phat, k.v, k.rhat, 0, c->cs, red));
-  TLAUNCH("bicg_s", 24.0 * nv, launch_bicg_s<double>(nv, k.r, k.v, k.s, c->cs, red));
-  TLAUNCH("cast", 12.0 * nv, launch_to_float(nv, k.s, f.r, c->cs));
-  TRY(vcycle<float>(c, f.r, f.shat));
-  TLAUNCH("cast", 12.0 * nv, launch_to_double(nv, f.shat, k.shat, c->cs));
-  TLAUNCH("stencil_dot", 64.0 * pts, launch_apply_dot<double>(L0, c->par(), k.shat, k.t, k.s, 1, c->cs, red));
-  TLAUNCH("bicg_update", 72.0 * nv,
-          launch_bicg_update<double>(nv, k.d, k.phat, k.shat, k.r, k.s, k.t, k.rhat, L0.diag,
-                                     L0.sc, c->cs, red));
-  TLAUNCH("bicg_p", 32.0 * nv, launch_bicg_p<double>(nv, k.p, k.r, k.v, cond, c->cs, red));
-  return POLAR_OK;
-}
-
 template <typename T>
 int bicg_begin(polar_ctx* c, CondHandle cond) {
   KVecs<T>& k = kvecs<T>(c);
@@ -772,42 +776,55 @@ int rhs(polar_ctx* c) {
   return POLAR_OK;
 }
 
+// Direct inner solve of a separable operator: the FP64 residual scaled by its max norm
+// (k_scale_cast), Fourier transform along theta, one tridiagonal solve per mode, inverse
+// transform, then X += rmax d in FP64 (k_correct).
+int direct_inner(polar_ctx* c) {
+  const size_t nv = c->nv();
+  const double pts = (double)c->m * c->n;
+  TLAUNCH("scale_cast", 16.0 * nv, launch_scale_cast<double>(nv, c->r64, c->kv64.r, c->cs, c->red()));
+  // ring values in and out (16 B), the mode coefficients through the three kernels (48 B)
+  // and the tridiagonal factors (8 B) per point
+  TLAUNCH("direct_solve", 72.0 * pts,
+          launch_direct_solve(c->sh0(), c->plan, c->sep, c->par(), c->kv64.r, c->kv64.d,
+                              c->fx_r, c->fx_i, c->fcp, c->fzv, c->ks, c->cs));
+  return POLAR_OK;
+}
+
 // Eager step: the host drives the refinement and Krylov loops (used when per-kernel
 // timing is on, and as the fallback when a graph cannot be built).
 template <typename T>
 int step_eager(polar_ctx* c, polar_step_stats& stats) {
   c->cs = c->st;
-  LAUNCH(launch_step_begin(c->cs, c->red()));  // step flags a graph run may have left set
+  LAUNCH(launch_step_begin(c->sp, c->cs, c->red()));  // step flags a graph run may have left set
   TRY(rhs(c));
   if (c->sp_host->do_refresh) TRY(launch_refresh_all<T>(c));
   CUDA_TRY(cudaMemcpyAsync(c->X, c->U, c->nv() * sizeof(double), cudaMemcpyDeviceToDevice, c->st));
-  stats.iters = 0;
-  stats.refinements = 0;
-  stats.fp64_iters = 0;
-  const StepParams& o = *c->sp_host;
-  // the same switch as k_refine_decide: a sweep that gained less than a factor 10, or an
-  // inner solve that broke down or hit its iteration limit, moves the mixed path to the
-  // FP64 Krylov solve for the rest of the step
-  bool use64 = false;
-  int inner_done = 0;
-  double prev = INFINITY;
-  for (int sweep = 0;; ++sweep) {
+  // the refinement decisions (converged, failed, switch of the mixed path to its FP64 solve)
+  // are taken on the device by the kernels the step graph runs; the host only reads them
+  for (;;) {
     TRY(resid(c));
+    LAUNCH(launch_refine_decide(c->sp, 0, c->cs, c->red()));
     TRY(read_scalars(c));
-    stats.refinements += 1;
-    const double xmax = std::max(c->ks_host->xmax, 1e-300);
-    const double scaled = c->ks_host->smax / xmax;
-    stats.scaled_resid = scaled;
-    if (!std::isfinite(scaled) || !std::isfinite(c->ks_host->rmax))
-      return fail(POLAR_ENONFINITE, "non-finite residual");
-    if (scaled <= o.tol) break;
-    if (sweep >= o.max_refine)
+    const KrylovScalars& h = *c->ks_host;
+    stats.refinements = h.sweeps;
+    stats.scaled_resid = h.scaled;
+    stats.iters = h.iters_total;
+    stats.fp64_iters = h.iters64;
+    if (h.failed == POLAR_ENONFINITE) return fail(POLAR_ENONFINITE, "non-finite residual");
+    if (h.failed)
       return fail(POLAR_ENOCONV, "refinement did not reach the tolerance (scaled residual " +
-                                     std::to_string(scaled) + ")");
-    if (sweep > 0 && (scaled > 0.1 * prev || inner_done >= 2)) use64 = true;
-    prev = scaled;
-    const bool x64 = use64 && sizeof(T) == 4;
+                                     std::to_string(h.scaled) + ")");
+    if (h.converged) break;
+    if (c->direct_now) {
+      TRY(direct_inner(c));
+      LAUNCH(launch_after_inner(0, c->cs, c->red()));
+      TRY(correct<double>(c));
+      continue;
+    }
+    const bool x64 = h.use64 && sizeof(T) == 4;
     if (x64) {
+      TRY(launch_refresh_all<double>(c, c->stamp64));  // FP64 factors, once per (alpha, beta)
       TRY(bicg_begin<double>(c, 0));
     } else {
       TRY(bicg_begin<T>(c, 0));
@@ -816,7 +833,7 @@ int step_eager(polar_ctx* c, polar_step_stats& stats) {
     for (;;) {
       for (int it = 0; it < batch; ++it) {
         if (x64) {
-          TRY(bicg_iteration_x(c, 0));
+          TRY(krylov_iteration<double>(c, 0));
         } else {
           TRY(krylov_iteration<T>(c, 0));
         }
@@ -825,19 +842,13 @@ int step_eager(polar_ctx* c, polar_step_stats& stats) {
       if (c->ks_host->done != 0) break;
       batch = std::min(batch * 2, 8);
     }
-    stats.iters += c->ks_host->iters;
-    if (x64) stats.fp64_iters += c->ks_host->iters;
-    inner_done = c->ks_host->done;
-    // as k_after_inner / k_correct: a non-finite FP32 solve of the mixed path is dropped
-    // and the step moves to the FP64 Krylov solve; a non-finite FP64 solve fails
-    if (c->ks_host->done == 3 && (x64 || sizeof(T) == 8))
-      return fail(POLAR_ENONFINITE, "non-finite value in the Krylov solve");
-    if (c->ks_host->done != 3) {
-      if (x64) {
-        TRY(correct<double>(c));
-      } else {
-        TRY(correct<T>(c));
-      }
+    // as in the graph: iteration counts, a non-finite FP32 solve of the mixed path dropped
+    // (the step moves to the FP64 solve), a non-finite FP64 solve failing the step
+    LAUNCH(launch_after_inner(sizeof(T) == 4 && !x64, c->cs, c->red()));
+    if (x64) {
+      TRY(correct<double>(c));
+    } else {
+      TRY(correct<T>(c));
     }
   }
   std::swap(c->U, c->X);
@@ -893,6 +904,7 @@ int append_inner(polar_ctx* c, cudaGraph_t g, const std::vector<cudaGraphNode_t>
   CUDA_TRY(cudaGraphConditionalHandleCreate(&hin, g, 0, 0));
   TRY(capture_begin(c, g, deps.empty() ? nullptr : deps.data(), deps.size()));
   if (x64) {
+    TRY(launch_refresh_all<double>(c, c->stamp64));  // FP64 factors, once per (alpha, beta)
     TRY(bicg_begin<double>(c, (CondHandle)hin));
   } else {
     TRY(bicg_begin<T>(c, (CondHandle)hin));
@@ -905,7 +917,7 @@ int append_inner(polar_ctx* c, cudaGraph_t g, const std::vector<cudaGraphNode_t>
   const int64_t a = c->launches;
   TRY(capture_begin(c, bin, nullptr, 0));
   if (x64) {
-    TRY(bicg_iteration_x(c, (CondHandle)hin));
+    TRY(krylov_iteration<double>(c, (CondHandle)hin));
   } else {
     TRY(krylov_iteration<T>(c, (CondHandle)hin));
   }
@@ -919,6 +931,17 @@ int append_inner(polar_ctx* c, cudaGraph_t g, const std::vector<cudaGraphNode_t>
   } else {
     TRY(correct<T>(c));
   }
+  TRY(capture_end(c, sinks));
+  return POLAR_OK;
+}
+
+// Appends the direct inner solve (separable operators) to graph g: scaled cast, the
+// transform / tridiagonal / inverse-transform kernels, bookkeeping and correction of X.
+int append_direct(polar_ctx* c, cudaGraph_t g, std::vector<cudaGraphNode_t>* sinks) {
+  TRY(capture_begin(c, g, nullptr, 0));
+  TRY(direct_inner(c));
+  LAUNCH(launch_after_inner(0, c->cs, c->red()));
+  TRY(correct<double>(c));
   TRY(capture_end(c, sinks));
   return POLAR_OK;
 }
@@ -953,9 +976,11 @@ int append_step(polar_ctx* c, cudaGraph_t g) {
   TRY(capture_end(c, &sinks));
   const int64_t l2 = c->launches;
   TRY(add_cond(bif, sinks, hout, cudaGraphCondTypeWhile, &nout, &bout));
-  int64_t iter_k = 0, iter64_k = 0;
+  int64_t iter_k = 0, iter64_k = 0, fixed64 = 0;
   std::vector<cudaGraphNode_t> body;
-  if (sizeof(T) == 8) {
+  if (c->direct_now) {
+    TRY(append_direct(c, bout, &body));
+  } else if (sizeof(T) == 8) {
     TRY(append_inner<T>(c, bout, body, false, &body, &iter_k));
   } else {
     // mixed path: IF (FP32 refinement) { FP32 Krylov solve } then
@@ -972,7 +997,9 @@ int append_step(polar_ctx* c, cudaGraph_t g) {
     std::vector<cudaGraphNode_t> none, tail;
     TRY(append_inner<T>(c, b32, none, false, &tail, &iter_k));
     TRY(add_cond(bout, std::vector<cudaGraphNode_t>{n32}, h64, cudaGraphCondTypeIf, &n64, &b64));
+    const int64_t before64 = c->launches;
     TRY(append_inner<T>(c, b64, none, true, &tail, &iter64_k));
+    fixed64 = c->launches - before64;
     body.assign(1, n64);
   }
   TRY(capture_begin(c, bout, body.data(), body.size()));
@@ -989,10 +1016,9 @@ int append_step(polar_ctx* c, cudaGraph_t g) {
   TRY(capture_end(c, nullptr));
   const int64_t l7 = c->launches;
   // kernels per executed step: fixed ones, per refinement sweep, per Krylov iteration
-  // (a mixed sweep runs one of its two inner solves, whose set-up and correction kernels
-  // are 4 each)
+  // (a mixed sweep runs one of its two inner solves; counted as the FP32 one)
   c->graph_kernels_fixed = (l2 - l0) + (l7 - l3);
-  c->graph_kernels_sweep = (l3 - l2) - (sizeof(T) == 8 ? 0 : 4);
+  c->graph_kernels_sweep = (l3 - l2) - fixed64;
   c->graph_kernels_iter = iter_k;
   c->graph_kernels_iter64 = iter64_k;
   c->launches = l0;  // captured launches run only when the graph is launched
@@ -1032,13 +1058,34 @@ polar_solver_opts resolve_opts(const polar_solver_opts* o) {
   r.max_iter = 500;
   r.max_refine = 12;
   r.inner_tol = 1e-5;
+  r.method = POLAR_SOLVE_AUTO;
+  r.reserved = 0;
   if (o) {
     if (o->tol > 0) r.tol = o->tol;
     if (o->max_iter > 0) r.max_iter = o->max_iter;
     if (o->max_refine > 0) r.max_refine = o->max_refine;
     if (o->inner_tol > 0) r.inner_tol = o->inner_tol;
+    r.method = o->method;
   }
   return r;
+}
+
+// Picks the inner solve of the coming steps (the direct one for separable operators
+// unless the caller asks for Krylov); a change invalidates the captured step graphs.
+int choose_method(polar_ctx* c, const polar_solver_opts& o) {
+  if (o.method != POLAR_SOLVE_AUTO && o.method != POLAR_SOLVE_KRYLOV &&
+      o.method != POLAR_SOLVE_DIRECT)
+    return fail(POLAR_EINVAL, "unknown solver method");
+  if (o.method == POLAR_SOLVE_DIRECT && !c->separable)
+    return fail(POLAR_EINVAL, "the direct solve needs a separable operator (uniform angles, "
+                              "angle-independent coefficients)");
+  const bool direct = c->separable && o.method != POLAR_SOLVE_KRYLOV;
+  if (direct != c->direct_now) {
+    c->direct_now = direct;
+    c->graph_ok = false;
+    c->generation += 1;
+  }
+  return POLAR_OK;
 }
 
 // Writes the step parameters to the device (the stream orders them before the step).
@@ -1058,6 +1105,7 @@ int set_step_params(polar_ctx* c, double alpha, double theta, const double* cf, 
   p.max_iter = o.max_iter;
   p.max_refine = o.max_refine;
   p.do_refresh = (alpha != c->cur_alpha || theta != c->cur_beta) ? 1 : 0;
+  p.mixed = (c->precision == POLAR_MIXED && !c->direct_now) ? 1 : 0;
   CUDA_TRY(cudaMemcpyAsync(c->sp, c->sp_host, sizeof(StepParams), cudaMemcpyHostToDevice, c->st));
   c->cur_alpha = alpha;
   c->cur_beta = theta;
@@ -1086,6 +1134,7 @@ int make_params(polar_ctx* c, double t0, double t1, double theta, const double* 
   p.max_iter = o.max_iter;
   p.max_refine = o.max_refine;
   p.do_refresh = (p.alpha != prev_alpha || theta != prev_beta) ? 1 : 0;
+  p.mixed = (c->precision == POLAR_MIXED && !c->direct_now) ? 1 : 0;
   return POLAR_OK;
 }
 
@@ -1221,7 +1270,11 @@ int prepare_tuning(polar_ctx* c, const double* t, double theta, const double* w,
   } else {
     TRY(launch_refresh_all<float>(c));
     TRY(tune_rings<float>(c));
+    // the FP64 ring solves of the mixed path's FP64 solve
+    TRY(launch_refresh_all<double>(c, c->stamp64));
+    TRY(tune_rings<double>(c));
   }
+  c->tuned = true;
   c->cur_alpha = p.alpha;
   c->cur_beta = theta;
   c->graph_ok = false;  // captured launches must use the tuned shapes
@@ -1235,8 +1288,9 @@ int advance(polar_ctx* c, int32_t K, const double* t, double theta, const double
   CUDA_TRY(cudaSetDevice(c->device));
   c->cs = c->st;
   const polar_solver_opts o = resolve_opts(opts);
+  TRY(choose_method(c, o));
   if (K == 0) return POLAR_OK;
-  if (c->autotune && !c->tuned) TRY(prepare_tuning(c, t, theta, w, o));
+  if (c->autotune && !c->tuned && !c->direct_now) TRY(prepare_tuning(c, t, theta, w, o));
   if (!c->use_graph || c->timing) return advance_eager(c, K, t, theta, w, o, stats);
   TRY(load_schedule(c, K, t, theta, w, o));
   if (!c->graph_ok) {
@@ -1265,6 +1319,100 @@ bool is_symmetric(const HLevel& L) {
     }
   }
   return true;
+}
+
+// Separability of the fine level (the direct solve applies): every ring's coefficients
+// (control volume, row sum, the four couplings) equal across the angles, the two angular
+// couplings of a row equal, the origin's couplings equal -- to 1e-9 relative: uniform
+// angles computed as 2 pi j / n already differ in their spacings by ~1e-12 relative at
+// n = 8192, and the direct solve of the j = 0 coefficients is then a preconditioner whose
+// FP64 refinement contracts by about kappa * 1e-9 per sweep.
+constexpr double kSepTol = 1e-9;
+bool is_separable(const HLevel& L) {
+  const int m = L.m, n = L.n;
+  auto ring_const = [&](const std::vector<double>& a, int i) {
+    const double ref = a[L.q(i, 0)];
+    double amax = 0.0;
+    for (int j = 0; j < n; ++j) amax = std::max(amax, std::fabs(a[L.q(i, j)]));
+    for (int j = 0; j < n; ++j)
+      if (std::fabs(a[L.q(i, j)] - ref) > kSepTol * amax) return false;
+    return true;
+  };
+  for (int i = 1; i <= m; ++i) {
+    for (const std::vector<double>* a : {&L.vol, &L.rs, &L.w, &L.e, &L.s, &L.nn})
+      if (!ring_const(*a, i)) return false;
+    for (int j = 0; j < n; ++j) {
+      const double sv = L.s[L.q(i, j)], nv = L.nn[L.q(i, j)];
+      if (std::fabs(sv - nv) > kSepTol * std::max(std::fabs(sv), std::fabs(nv))) return false;
+    }
+  }
+  double omax = 0.0;
+  for (double v : L.o) omax = std::max(omax, std::fabs(v));
+  for (double v : L.o)
+    if (std::fabs(v - L.o[0]) > kSepTol * omax) return false;
+  return true;
+}
+
+// Device data of the direct solve for a separable fine level: the rings' coefficients,
+// the transform tables and the work arrays (allocated on first use).
+int setup_direct(polar_ctx* c, const HLevel& H) {
+  int M = 0, logM = 0, rw = 0;
+  c->separable = is_separable(H) && fft_plan_sizes(c->n, &M, &logM, &rw);
+  if (!c->separable) return POLAR_OK;
+  const int m = c->m, n = c->n, nh = n / 2 + 1;
+  FftPlan& P = c->plan;
+  SepRings& R = c->sep;
+  if (!c->fx_r) {
+    double *twr, *twi, *chr, *chi, *bhr, *bhi, *lam, *vol, *rs, *w, *e, *sv;
+    TRY(dalloc(c, &twr, (size_t)M / 2));
+    TRY(dalloc(c, &twi, (size_t)M / 2));
+    TRY(dalloc(c, &chr, (size_t)n));
+    TRY(dalloc(c, &chi, (size_t)n));
+    TRY(dalloc(c, &bhr, (size_t)M));
+    TRY(dalloc(c, &bhi, (size_t)M));
+    TRY(dalloc(c, &lam, (size_t)nh));
+    double** ring[] = {&vol, &rs, &w, &e, &sv};
+    for (double** p : ring) TRY(dalloc(c, p, (size_t)m));
+    TRY(dalloc(c, &c->fx_r, (size_t)m * nh));
+    TRY(dalloc(c, &c->fx_i, (size_t)m * nh));
+    TRY(dalloc(c, &c->fcp, (size_t)m * nh));
+    TRY(dalloc(c, &c->fzv, (size_t)m));
+    P = FftPlan{n, nh, M, logM, rw, twr, twi, chr, chi, bhr, bhi, lam};
+    R.vol = vol;
+    R.rs = rs;
+    R.w = w;
+    R.e = e;
+    R.s = sv;
+    CUDA_TRY(cudaStreamSynchronize(c->st));  // zeroed before the uploads below
+    std::vector<double> htwr, htwi, hchr, hchi, hlam;
+    fft_host_tables(n, M, htwr, htwi, hchr, hchi, hlam);
+    TRY(upload(twr, htwr));
+    TRY(upload(twi, htwi));
+    TRY(upload(chr, hchr));
+    TRY(upload(chi, hchi));
+    TRY(upload(lam, hlam));
+    if (M != n) LAUNCH(launch_chirp_filter(P, bhr, bhi, c->st));
+  }
+  R.m = m;
+  std::vector<double> a[5];
+  for (int i = 1; i <= m; ++i) {
+    const size_t q = H.q(i, 0);
+    a[0].push_back(H.vol[q]);
+    a[1].push_back(H.rs[q]);
+    a[2].push_back(H.w[q]);
+    a[3].push_back(H.e[q]);
+    a[4].push_back(H.s[q]);
+  }
+  double* dst[5] = {const_cast<double*>(R.vol), const_cast<double*>(R.rs),
+                    const_cast<double*>(R.w), const_cast<double*>(R.e),
+                    const_cast<double*>(R.s)};
+  for (int k = 0; k < 5; ++k) TRY(upload(dst[k], a[k]));
+  R.vol0 = H.vol0;
+  R.rs0 = H.rs0;
+  R.o = H.o[0];
+  R.osum = 0.0;
+  for (double v : H.o) R.osum += v;
+  return POLAR_OK;
 }
 
 }  // namespace
@@ -1339,6 +1487,7 @@ int polar_mesh_create(const polar_mesh_desc* d, polar_ctx** out) {
     chk(alloc_kvecs(c, c->kv64));
     if (c->precision == POLAR_MIXED) chk(alloc_kvecs(c, c->kv32));
     chk(dalloc(c, &c->part, (size_t)kMaxBlocks * 4));
+    if (c->precision == POLAR_MIXED) chk(dalloc(c, &c->stamp64, 2));  // zero: no factors yet
     chk(dalloc(c, &c->ks, 1));
   }
   if (rc == POLAR_OK && cudaMallocHost((void**)&c->ks_host, sizeof(KrylovScalars)) != cudaSuccess) {
@@ -1413,6 +1562,7 @@ int polar_set_coeffs(polar_ctx* c, const polar_coeffs* k) {
     assemble_paper(c->r, c->theta, K, H[0]);
   }
   c->symmetric = is_symmetric(H[0]);
+  TRY(setup_direct(c, H[0]));
   for (int l = 0; l + 1 < c->nlev(); ++l) coarsen(H[l], H[l + 1]);
   for (int l = 0; l < c->nlev(); ++l) TRY(upload_level(c, l, H[l]));
   // sources in the split layout, scaled by the control volumes
@@ -1428,6 +1578,9 @@ int polar_set_coeffs(polar_ctx* c, const polar_coeffs* k) {
   }
   c->nsrc = k->nsrc;
   c->cur_alpha = c->cur_beta = -1.0;  // the per-step parts must be refreshed
+  // new coefficients: the mixed path tries its FP32 solve again from the next step
+  CUDA_TRY(cudaMemsetAsync(&c->ks->sticky64, 0, sizeof(int), c->st));
+  if (c->stamp64) CUDA_TRY(cudaMemsetAsync(c->stamp64, 0, 2 * sizeof(double), c->st));
   c->graph_ok = false;                // the step graph bakes in the source count
   c->generation += 1;
   CUDA_TRY(cudaStreamSynchronize(c->st));
@@ -1530,12 +1683,14 @@ int polar_batch_advance(polar_batch* b, int32_t nsteps, const double* const* t, 
     polar_ctx* c = b->ctx[i];
     TRY(check_schedule_args(c, nsteps, t[i], theta[i], w ? w[i] : nullptr));
     if (!c->use_graph) return fail(POLAR_ESTATE, "a context of the batch cannot run as a graph");
+    TRY(choose_method(c, o));
   }
   if (nsteps == 0) return POLAR_OK;
   for (int i = 0; i < count; ++i) {
     polar_ctx* c = b->ctx[i];
     c->cs = c->st;
-    if (c->autotune && !c->tuned) TRY(prepare_tuning(c, t[i], theta[i], w ? w[i] : nullptr, o));
+    if (c->autotune && !c->tuned && !c->direct_now)
+      TRY(prepare_tuning(c, t[i], theta[i], w ? w[i] : nullptr, o));
     TRY(load_schedule(c, nsteps, t[i], theta[i], w ? w[i] : nullptr, o));
     CUDA_TRY(cudaStreamSynchronize(c->st));  // uploads land before the batch graph runs
   }
@@ -1603,6 +1758,12 @@ int polar_apply_operator(polar_ctx* c, double alpha, double beta, const double* 
 }
 
 int64_t polar_kernel_launches(const polar_ctx* c) { return c ? c->launches : 0; }
+
+int polar_is_separable(const polar_ctx* c) {
+  if (!c) return fail(POLAR_EINVAL, "null context");
+  if (!c->have_coeffs) return fail(POLAR_ESTATE, "set_coeffs must come first");
+  return c->separable ? 1 : 0;
+}
 
 int polar_timing_enable(polar_ctx* c, int32_t on) {
   if (!c) return fail(POLAR_EINVAL, "null context");

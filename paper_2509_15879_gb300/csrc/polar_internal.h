@@ -70,14 +70,17 @@ struct LevelView {
   // per step
   T* diag;       // nv: alpha vol + beta (rs - w - e - s - nn)
   T* rsum;       // nv, level 0 of the FP32 path: alpha vol + beta rs (row sums of S)
+  double* dinv;  // nv, level 0 of the FP64 view: 1 / diag (the FP64 residual's Jacobi
+                 //   scaling, formed once per step so that no kernel divides per point)
   T* fl;         // line factors of every ring's periodic angular line, nv each
   T* fui;
   T* fcu;
   T* fq;
   T* fring;      // 2 per ring, ring order (odd rings, then even): vf, 1/(1 + v.q)
   T* fz;         // n: coarsest level only, T_1^{-1} (beta w_1)
-  double* sc;    // scalars: [0] diag0, [1] coarsest Schur denominator, [2] sum_j o_j (static),
-                 //          [3] vol0, [4] rs0 (static), [5] alpha vol0 + beta rs0
+  double* sc;    // scalars: [0] diag0, [1] coarsest Schur denominator of the FP32 factors,
+                 //          [2] sum_j o_j (static), [3] vol0, [4] rs0 (static),
+                 //          [5] alpha vol0 + beta rs0, [6] Schur denominator, FP64 factors
 };
 
 // Scalars of one Krylov solve, kept on the device so that no iteration needs the host.
@@ -111,8 +114,18 @@ struct KrylovScalars {
   int inner_done;  // `done` of the last inner solve
   double prev_scaled;
   int iters64;     // Krylov iterations of this step spent in FP64 Krylov solves
+  int sticky64;    // mixed path: steps left that start with the FP64 solve (set when a
+                   //   step had to switch to it; the FP32 solve is tried again after)
+  double sm_best;  // FP32 inner solve: best Jacobi-scaled residual so far and the
+  int sm_best_it;  //   iteration that last halved it (no halving in kStallIters: stall)
   int pad3;
 };
+
+// An FP32 inner solve whose Jacobi-scaled residual has not halved in this many iterations
+// has stalled (the step then switches to the FP64 solve); a switch makes this many
+// following steps of the context start with the FP64 solve.
+constexpr int kStallIters = 20;
+constexpr int kStickySteps = 8;
 
 // Result of one step of a device-side schedule (graph mode).
 struct StepOut {
@@ -136,7 +149,7 @@ struct StepParams {
   int max_iter;
   int max_refine;
   int do_refresh;    // the per-step refresh runs only when alpha or beta changed
-  int pad;
+  int mixed;         // 1: the context's inner solves are FP32 (mixed path)
 };
 
 // Conditional-node handle of a CUDA graph (0: not in a graph).
@@ -179,19 +192,21 @@ int launch_rhs(const LevelView<double>& L, const StepParams* sp, const double* u
                Reduce red);
 
 // Per-step refresh of every level: diag, angular line factors, origin scalars and the
-// coarsest-level Schur data.  Factors are formed in FP64 and stored in T.
+// coarsest-level Schur data.  Factors are formed in FP64 and stored in T.  With `stamp`
+// (2 doubles) the refresh runs unless stamp holds the step's (alpha, beta), and records
+// them afterwards (factors formed only on demand); without it, when sp->do_refresh.
 template <typename T>
 int launch_refresh(const LevelView<double>* L64, LevelView<T>* LT, int nlev,
-                   const StepParams* sp, double* ws, cudaStream_t st);
+                   const StepParams* sp, double* ws, cudaStream_t st, double* stamp = nullptr);
 
 // Multigrid V(1,1) cycle pieces (polar_mg.cu).  mode 0 = pre-smoothing (the level's
 // x starts from zero), 1 = post-smoothing (x of the odd rings is corrected on the fly
 // with the coarser level's solution X); parity 1 = odd rings, 0 = even rings + origin.
 enum { RING_PRE = 0, RING_POST = 1 };
 // tile shape of a ring solve launch: RW lines per CTA, TW chunk threads per line, P angles
-// per thread, CS CTAs per cluster along the angle
+// per thread, CS CTAs per cluster along the angle, ST staged operand loads (two CTAs/SM)
 struct RingShape {
-  int RW, TW, P, CS;
+  int RW, TW, P, CS, ST;
 };
 template <typename T>
 int launch_ring(const LevelView<T>& L, const LevelView<T>& C, const T* b, T* x, const T* X,
@@ -224,7 +239,6 @@ int launch_cg_p(size_t nv, T* p, const T* z, cudaStream_t st, Reduce red);
 template <typename T>
 int launch_cg_update(size_t nv, T* x, const T* p, T* r, const T* q, const T* diag,
                      const double* sc, CondHandle cond, cudaStream_t st, Reduce red);
-int launch_to_double(size_t n, const float* a, double* b, cudaStream_t st);
 int launch_choose_inner(CondHandle c32, CondHandle c64, cudaStream_t st, Reduce red);
 template <typename T>
 int launch_bicg_update(size_t nv, T* x, const T* phat, const T* shat, T* r, const T* s,
@@ -236,7 +250,7 @@ int launch_bicg_p(size_t nv, T* p, const T* r, const T* v, CondHandle cond, cuda
 
 // ---- device-side step control (graph mode; the host does the same in eager mode)
 // reset the step state
-int launch_step_begin(cudaStream_t st, Reduce red);
+int launch_step_begin(const StepParams* sp, cudaStream_t st, Reduce red);
 // schedule-driven steps: load step *kstep of `sched` into `sp` and reset the step state
 // (cond = 1), or record the step as skipped (cond = 0) after an earlier failure
 int launch_sched_begin(const StepParams* sched, const int* kstep, StepParams* sp,

@@ -97,6 +97,18 @@ __device__ void grid_totals(const double* part, double (&tot)[K]) {
 
 __device__ __forceinline__ double absfin(double v) { return isfinite(v) ? fabs(v) : INFINITY; }
 
+// |v| as the bit pattern of a non-negative double, NaN mapped to +inf.  Non-negative
+// doubles order like their bit patterns, so running maxima are integer maxima: no FP64
+// instruction per point (GB300's FP64 pipe is the scarce unit of the FP64 kernels).
+__device__ __forceinline__ unsigned long long abs_bits(double v) {
+  const unsigned long long u =
+      static_cast<unsigned long long>(__double_as_longlong(v)) & 0x7fffffffffffffffull;
+  return u > 0x7ff0000000000000ull ? 0x7ff0000000000000ull : u;
+}
+__device__ __forceinline__ double bits_to_double(unsigned long long u) {
+  return __longlong_as_double(static_cast<long long>(u));
+}
+
 // ------------------------------------------------------------------ point loops
 // Tiles of TK consecutive rings of one parity block x TJ consecutive angles; every
 // warp reads TK consecutive entries of a radial line (coalesced).
@@ -175,7 +187,10 @@ struct Slots {
 
 // y = S x in the direct form diag x + beta (w xW + e xE + s xS + nn xN) (Section 3.2.1
 // rows scaled by the control volumes); slot 0 collects sum_j o_j x_{1,j} for the
-// origin row (Section 3.2.2), which the last block finishes.
+// origin row (Section 3.2.2) in FP64, which the last block finishes.  The dot products
+// of the Krylov modes accumulate per thread in T (FP32 in the mixed path's inner
+// solves) and in FP64 across threads and blocks; the residual's maxima are kept as
+// integer maxima of bit patterns, its Jacobi scaling multiplies by 1 / diag.
 template <typename T, int MODE>
 __global__ void __launch_bounds__(256) k_stencil(StArgs<T> a) {
   if (MODE >= M_DOTV && a.red.ks->done) return;
@@ -185,6 +200,8 @@ __global__ void __launch_bounds__(256) k_stencil(StArgs<T> a) {
   double acc[K];
 #pragma unroll
   for (int k = 0; k < K; ++k) acc[k] = 0.0;
+  T dot1 = T(0), dot2 = T(0);
+  unsigned long long rbits = 0, sbits = 0, xbits = 0;
   const T* __restrict__ x = a.x;
   const T x0 = x[0];
   for_points(L.sh, a.t, [&](int i, int j, size_t idx, size_t west, size_t east, size_t south,
@@ -193,15 +210,13 @@ __global__ void __launch_bounds__(256) k_stencil(StArgs<T> a) {
     const T xw = (west == 0) ? x0 : x[west];
     const T xe = (east == (size_t)-1) ? T(0) : x[east];
     T val;
-    T dg = T(0);
     if (sizeof(T) == 8) {
       // FP64: direct form diag x + beta (w xW + e xE + s xS + nn xN)
       T off = L.w[idx] * xw;
       off = fma(L.e[idx], xe, off);
       off = fma(L.s[idx], x[south], off);
       off = fma(L.nn[idx], x[north], off);
-      dg = L.diag[idx];
-      val = fma(beta, off, dg * xc);
+      val = fma(beta, off, L.diag[idx] * xc);
       if (i == 1) acc[0] = fma((double)L.o[j], (double)xc, acc[0]);
     } else {
       // FP32: difference form rsum x + beta (w (xW - x) + ...): near the origin the angular
@@ -216,18 +231,31 @@ __global__ void __launch_bounds__(256) k_stencil(StArgs<T> a) {
     }
     if (MODE == M_RESID64) {
       val = a.b[idx] - val;
-      const double ar = absfin((double)val);
-      acc[1] = fmax(acc[1], ar);
-      acc[2] = fmax(acc[2], ar / fabs((double)dg));
-      acc[3] = fmax(acc[3], absfin((double)xc));
+      const unsigned long long ar = abs_bits((double)val);
+      rbits = ar > rbits ? ar : rbits;
+      // |r| / diag (diag > 0: S is an M-matrix with a positive diagonal)
+      const unsigned long long sr = abs_bits(bits_to_double(ar) * L.dinv[idx]);
+      sbits = sr > sbits ? sr : sbits;
+      const unsigned long long ax = abs_bits((double)xc);
+      xbits = ax > xbits ? ax : xbits;
     }
-    if (MODE == M_DOTV) acc[1] = fma((double)a.d1[idx], (double)val, acc[1]);
+    if (MODE == M_DOTV) dot1 = fma(a.d1[idx], val, dot1);
     if (MODE == M_DOTT) {
-      acc[1] = fma((double)val, (double)a.d1[idx], acc[1]);
-      acc[2] = fma((double)val, (double)val, acc[2]);
+      dot1 = fma(val, a.d1[idx], dot1);
+      dot2 = fma(val, val, dot2);
     }
     a.y[idx] = val;
   });
+  if (MODE == M_RESID64) {
+    acc[1] = bits_to_double(rbits);
+    acc[2] = bits_to_double(sbits);
+    acc[3] = bits_to_double(xbits);
+  }
+  if (MODE == M_DOTV) acc[1] = (double)dot1;
+  if (MODE == M_DOTT) {
+    acc[1] = (double)dot1;
+    acc[2] = (double)dot2;
+  }
   block_reduce<K, KMAX>(acc);
   if (!publish_and_arrive<K>(acc, a.red.part, &a.red.ks->counter)) return;
 
@@ -410,16 +438,16 @@ __global__ void __launch_bounds__(kVT) k_bicg_init(size_t nv, const T* r, T* rha
   const double rel_tol = sp->inner_tol;
   const int max_iter = sp->max_iter;
   double acc[1];
-  double s = 0.0;
+  T s = T(0);  // per thread in T, across threads in FP64
   for (size_t k = blockIdx.x * (size_t)kVT + threadIdx.x; k < nv; k += (size_t)gridDim.x * kVT) {
     const T rv = r[k];
     rhat[k] = rv;
     p[k] = rv;
     v[k] = T(0);
     x[k] = T(0);
-    s = fma((double)rv, (double)rv, s);
+    s = fma(rv, rv, s);
   }
-  acc[0] = s;
+  acc[0] = (double)s;
   block_reduce<1, 1>(acc);
   if (!publish_and_arrive<1>(acc, red.part, &red.ks->counter)) return;
   double tot[1];
@@ -438,6 +466,8 @@ __global__ void __launch_bounds__(kVT) k_bicg_init(size_t nv, const T* r, T* rha
   const double need = (ks->smax > 0.0) ? 0.1 * sp->tol * ks->xmax / ks->smax : 1.0;
   ks->sm_tol = fmax(rel_tol, need) * (ks->rmax > 0.0 ? ks->smax / ks->rmax : 0.0);
   ks->sm = INFINITY;
+  ks->sm_best = INFINITY;
+  ks->sm_best_it = 0;
   ks->alpha = 1.0;
   ks->omega = 1.0;
   ks->beta = 0.0;
@@ -467,6 +497,19 @@ __device__ __forceinline__ float scaled_abs(T r, T d) {
   return (float)fmin(fabs((double)r) / (double)d, 3.0e38);
 }
 
+// FP32 inner solves: true once the Jacobi-scaled residual `sm` has not halved for
+// kStallIters iterations (the FP32 operator cannot resolve what is left).
+template <typename T>
+__device__ __forceinline__ bool fp32_stalled(KrylovScalars* ks, double sm) {
+  if (sizeof(T) != 4) return false;
+  if (sm < 0.5 * ks->sm_best) {
+    ks->sm_best = sm;
+    ks->sm_best_it = ks->iters;
+    return false;
+  }
+  return ks->iters - ks->sm_best_it >= kStallIters;
+}
+
 template <typename T>
 __global__ void __launch_bounds__(kVT) k_bicg_update(size_t nv, T* x, const T* phat,
                                                      const T* shat, T* r, const T* s,
@@ -474,18 +517,18 @@ __global__ void __launch_bounds__(kVT) k_bicg_update(size_t nv, T* x, const T* p
                                                      const double* sc, Reduce red) {
   if (red.ks->done) return;
   const T alpha = (T)red.ks->alpha, omega = (T)red.ks->omega;
-  double s1 = 0.0, s2 = 0.0;
+  const T d0 = (T)sc[0];  // the origin's diagonal lives in the level scalars
+  T s1 = T(0), s2 = T(0);  // per thread in T, across threads in FP64
   float sm = 0.f;
   for (size_t k = blockIdx.x * (size_t)kVT + threadIdx.x; k < nv; k += (size_t)gridDim.x * kVT) {
     x[k] = fma(omega, shat[k], fma(alpha, phat[k], x[k]));
     const T rn = fma(-omega, t[k], s[k]);
     r[k] = rn;
-    s1 = fma((double)rhat[k], (double)rn, s1);
-    s2 = fma((double)rn, (double)rn, s2);
-    // the origin's diagonal lives in the level scalars (entry 0 of diag is unused)
-    sm = fmaxf(sm, scaled_abs<T>(rn, k == 0 ? (T)sc[0] : diag[k]));
+    s1 = fma(rhat[k], rn, s1);
+    s2 = fma(rn, rn, s2);
+    sm = fmaxf(sm, scaled_abs<T>(rn, k == 0 ? d0 : diag[k]));
   }
-  double acc[3] = {s1, s2, isfinite(sm) ? (double)sm : INFINITY};
+  double acc[3] = {(double)s1, (double)s2, isfinite(sm) ? (double)sm : INFINITY};
   block_reduce<3, 2>(acc);
   if (!publish_and_arrive<3>(acc, red.part, &red.ks->counter)) return;
   double tot[3];
@@ -500,7 +543,7 @@ __global__ void __launch_bounds__(kVT) k_bicg_update(size_t nv, T* x, const T* p
     ks->done = 3;
   } else if (tot[2] <= ks->sm_tol) {
     ks->done = 1;
-  } else if (ks->iters >= ks->max_iter) {
+  } else if (ks->iters >= ks->max_iter || fp32_stalled<T>(ks, tot[2])) {
     ks->done = 4;
   } else if (ks->omega == 0.0 || rho_new == 0.0 || ks->rho == 0.0) {
     ks->done = 2;
@@ -559,9 +602,10 @@ int launch_bicg_p(size_t nv, T* p, const T* r, const T* v, CondHandle cond, cuda
 template <typename T>
 __global__ void __launch_bounds__(kVT) k_cg_rho(size_t nv, const T* r, const T* z, Reduce red) {
   if (red.ks->done) return;
-  double acc[1] = {0.0};
+  T s = T(0);  // per thread in T, across threads in FP64
   for (size_t k = blockIdx.x * (size_t)kVT + threadIdx.x; k < nv; k += (size_t)gridDim.x * kVT)
-    acc[0] = fma((double)r[k], (double)z[k], acc[0]);
+    s = fma(r[k], z[k], s);
+  double acc[1] = {(double)s};
   block_reduce<1, 1>(acc);
   if (!publish_and_arrive<1>(acc, red.part, &red.ks->counter)) return;
   double tot[1];
@@ -597,12 +641,13 @@ __global__ void __launch_bounds__(kVT) k_cg_update(size_t nv, T* x, const T* p, 
     return;
   }
   const T alpha = (T)red.ks->alpha;
+  const T d0 = (T)sc[0];
   float sm = 0.f;
   for (size_t k = blockIdx.x * (size_t)kVT + threadIdx.x; k < nv; k += (size_t)gridDim.x * kVT) {
     x[k] = fma(alpha, p[k], x[k]);
     const T rn = fma(-alpha, q[k], r[k]);
     r[k] = rn;
-    sm = fmaxf(sm, scaled_abs<T>(rn, k == 0 ? (T)sc[0] : diag[k]));
+    sm = fmaxf(sm, scaled_abs<T>(rn, k == 0 ? d0 : diag[k]));
   }
   double acc[1] = {isfinite(sm) ? (double)sm : INFINITY};
   block_reduce<1, 0>(acc);
@@ -617,7 +662,7 @@ __global__ void __launch_bounds__(kVT) k_cg_update(size_t nv, T* x, const T* p, 
     ks->done = 3;
   } else if (tot[0] <= ks->sm_tol) {
     ks->done = 1;
-  } else if (ks->iters >= ks->max_iter) {
+  } else if (ks->iters >= ks->max_iter || fp32_stalled<T>(ks, tot[0])) {
     ks->done = 4;
   }
   ks->counter = 0;
@@ -642,9 +687,16 @@ int launch_cg_update(size_t nv, T* x, const T* p, T* r, const T* q, const T* dia
 }
 
 // ------------------------------------------------------------------ step control
-__global__ void k_step_begin(KrylovScalars* ks) {
+// The mixed path starts a step with the FP64 solve while the sticky countdown of an
+// earlier switch runs.
+__device__ __forceinline__ void start_step(const StepParams& p, KrylovScalars* ks) {
+  ks->use64 = (p.mixed && ks->sticky64 > 0) ? 1 : 0;
+  if (ks->use64) ks->sticky64 -= 1;
+}
+
+__global__ void k_step_begin(const StepParams* sp, KrylovScalars* ks) {
   ks->failed = 0;
-  ks->use64 = 0;
+  start_step(*sp, ks);
   ks->inner_done = 0;
   ks->prev_scaled = INFINITY;
   ks->iters64 = 0;
@@ -655,8 +707,8 @@ __global__ void k_step_begin(KrylovScalars* ks) {
   ks->done = 0;
   ks->counter = 0;
 }
-int launch_step_begin(cudaStream_t st, Reduce red) {
-  k_step_begin<<<1, 1, 0, st>>>(red.ks);
+int launch_step_begin(const StepParams* sp, cudaStream_t st, Reduce red) {
+  k_step_begin<<<1, 1, 0, st>>>(sp, red.ks);
   return 1;
 }
 
@@ -670,7 +722,7 @@ __global__ void k_sched_begin(const StepParams* sched, const int* kstep, StepPar
   }
   *sp = sched[k];
   ks->failed = 0;
-  ks->use64 = 0;
+  start_step(sched[k], ks);
   ks->inner_done = 0;
   ks->prev_scaled = INFINITY;
   ks->iters64 = 0;
@@ -722,8 +774,11 @@ __global__ void k_refine_decide(const StepParams* sp, CondHandle cond, KrylovSca
       more = true;
       // a correction that gained less than a factor 10, or an inner solve that broke
       // down or ran out of iterations, switches the step to the FP64 Krylov solve
-      if (ks->sweeps > 1 && (scaled > 0.1 * ks->prev_scaled || ks->inner_done >= 2))
+      if (ks->sweeps > 1 && (scaled > 0.1 * ks->prev_scaled || ks->inner_done >= 2) &&
+          !ks->use64) {
         ks->use64 = 1;
+        if (sp->mixed) ks->sticky64 = kStickySteps;
+      }
     }
     ks->prev_scaled = scaled;
   }
@@ -798,16 +853,6 @@ int launch_scale_cast(size_t nv, const double* r, T* rs, cudaStream_t st, Reduce
 template <typename T>
 int launch_correct(size_t nv, double* x, const T* d, cudaStream_t st, Reduce red) {
   k_correct<T><<<grid_for(nv, kVT), kVT, 0, st>>>(nv, x, d, red.ks);
-  return 1;
-}
-
-__global__ void k_to_double(size_t n, const float* a, double* b) {
-  for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n;
-       k += (size_t)gridDim.x * blockDim.x)
-    b[k] = (double)a[k];
-}
-int launch_to_double(size_t n, const float* a, double* b, cudaStream_t st) {
-  k_to_double<<<grid_for(n, 256), 256, 0, st>>>(n, a, b);
   return 1;
 }
 

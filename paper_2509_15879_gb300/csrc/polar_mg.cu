@@ -49,6 +49,7 @@ struct RefreshLevel {
   double* sc;
   void* diag;
   double* diag64;  // FP64 copy of diag when T is float (level 0 only), else null
+  double* dinv;    // level 0: 1 / diag in FP64 (both precisions), else null
   void* rsum;      // row sums alpha vol + beta rs when T is float (level 0 only), else null
   void* fl;
   void* fui;
@@ -64,7 +65,17 @@ struct RefreshArgs {
   RefreshLevel lv[kMaxLevels];
   int nlev;
   const StepParams* sp;
+  const double* stamp;  // null: refresh when sp->do_refresh; else refresh unless stamp
+                        // holds this step's (alpha, beta) (factors already current)
 };
+
+// Whether a refresh has work: the step's do_refresh flag, or, for factors kept beside the
+// step's own (the mixed path's FP64 factors, formed only when its FP64 solve runs), the
+// stamp of the (alpha, beta) they were last formed for.
+__device__ __forceinline__ bool refresh_due(const StepParams* sp, const double* stamp) {
+  if (!stamp) return sp->do_refresh != 0;
+  return !(stamp[0] == sp->alpha && stamp[1] == sp->beta);
+}
 
 // Ring i of a level is the periodic tridiagonal system
 //   a_j x_{j-1} + b_j x_j + c_j x_{j+1} = d_j  (indices mod n) with
@@ -156,7 +167,7 @@ __global__ void __launch_bounds__(RF * TF) k_refresh(RefreshArgs A) {
   __shared__ M2 sm2[(RF * TF / 32) * RF];
   __shared__ A2 sa2[(RF * TF / 32) * RF];
   __shared__ double qend[2][RF];
-  if (!A.sp->do_refresh) return;
+  if (!refresh_due(A.sp, A.stamp)) return;
   // which level, parity block and group of RF rings this CTA takes
   int l = 0;
   while (l + 1 < A.nlev && (int)blockIdx.x >= A.lv[l + 1].ring0) ++l;
@@ -240,6 +251,7 @@ __global__ void __launch_bounds__(RF * TF) k_refresh(RefreshArgs A) {
     const double bd = bdiag(q);
     diag[q] = (T)bd;
     if (L.diag64) L.diag64[q] = bd;
+    if (L.dinv) L.dinv[q] = 1.0 / bd;
     if (L.rsum) static_cast<T*>(L.rsum)[q] = (T)(alpha * L.vol[q] + beta * L.rs[q]);
     const double a = (j > 0) ? beta * L.s[q] : 0.0;
     const double c = cc(j);
@@ -304,14 +316,22 @@ __global__ void __launch_bounds__(RF * TF) k_refresh(RefreshArgs A) {
 }
 
 template <typename T>
-static int launch_schur(const LevelView<T>& L, const StepParams* sp, cudaStream_t st);
+static int launch_schur(const LevelView<T>& L, const StepParams* sp, const double* stamp,
+                        cudaStream_t st);
+
+// after a stamped refresh: record the (alpha, beta) the factors now hold
+__global__ void k_stamp(const StepParams* sp, double* stamp) {
+  stamp[0] = sp->alpha;
+  stamp[1] = sp->beta;
+}
 
 template <typename T>
 int launch_refresh(const LevelView<double>* L64, LevelView<T>* LT, int nlev,
-                   const StepParams* sp, double* ws, cudaStream_t st) {
+                   const StepParams* sp, double* ws, cudaStream_t st, double* stamp) {
   RefreshArgs A{};
   A.nlev = nlev;
   A.sp = sp;
+  A.stamp = stamp;
   int rings = 0;
   size_t wofs = 0;
   for (int l = 0; l < nlev; ++l) {
@@ -328,6 +348,7 @@ int launch_refresh(const LevelView<double>* L64, LevelView<T>* LT, int nlev,
     r.sc = LT[l].sc;
     r.diag = LT[l].diag;
     r.diag64 = (sizeof(T) == 4 && l == 0) ? L64[0].diag : nullptr;
+    r.dinv = (l == 0) ? L64[0].dinv : nullptr;
     r.rsum = (sizeof(T) == 4 && l == 0) ? (void*)LT[0].rsum : nullptr;
     r.fl = LT[l].fl;
     r.fui = LT[l].fui;
@@ -341,8 +362,18 @@ int launch_refresh(const LevelView<double>* L64, LevelView<T>* LT, int nlev,
     rings += (d.sh.no + RF - 1) / RF + (d.sh.ne + RF - 1) / RF;
   }
   k_refresh<T><<<rings, dim3(RF, TF), 0, st>>>(A);
-  return 1 + launch_schur<T>(LT[nlev - 1], sp, st);
+  int k = 1 + launch_schur<T>(LT[nlev - 1], sp, stamp, st);
+  if (stamp) {
+    k_stamp<<<1, 1, 0, st>>>(sp, stamp);
+    ++k;
+  }
+  return k;
 }
+
+// Slot of the level scalars holding the coarsest level's Schur denominator: one per
+// precision, since a mixed context forms FP32 and FP64 factors of the same levels.
+template <typename T>
+constexpr int kSchurSlot = sizeof(T) == 8 ? 6 : 1;
 
 // ---------------------------------------------------------------------------------
 // ring solves
@@ -544,7 +575,11 @@ __device__ __forceinline__ void chunk_scan(T A, T B, bool rev, T* sWA, T* sWB, T
 // Rhs(j) gives d_j of this thread's line; Out(j, x) stores the solution.  The chunk's
 // right-hand side and LU factors are loaded once into registers (all loads in flight
 // together); the Sherman-Morrison vector is read at the end.
-template <typename T, int P, typename Rhs, typename Fac, typename Out>
+// STAGED: the operands arrive in three groups -- right-hand side and l before the forward
+// scan, 1/u and c/u after it, q at the end -- so that fewer registers are live and two
+// CTAs share an SM (the kernel variant launched with two CTAs per SM), letting one CTA's
+// scans overlap another's loads.  Unstaged: every operand is loaded up front.
+template <typename T, int P, bool STAGED = false, typename Rhs, typename Fac, typename Out>
 __device__ void solve_lines(int n, bool valid, Rhs rhs, Fac fac, T vf, T inv, Out out) {
   extern __shared__ unsigned char smraw[];
   const int RW = blockDim.x, TW = blockDim.y;
@@ -562,16 +597,20 @@ __device__ void solve_lines(int n, bool valid, Rhs rhs, Fac fac, T vf, T inv, Ou
   const int j0 = gc * P;
   // the Sherman-Morrison vector is loaded with the rest when registers allow (short
   // chunks), so that the final correction waits on no memory access
-  constexpr bool kPrefetchQ = (P * sizeof(T) <= 32);
-  T v[P], fl[P], fu[P], fc[P], fqv[kPrefetchQ ? P : 1];
+  constexpr bool kPrefetchQ = !STAGED && (P * sizeof(T) <= 32);
+  // staged: fu / fc share the registers of fl (dead after the forward replay)
+  T v[P], fl[P], fu_[STAGED ? 1 : P], fc[P], fqv[kPrefetchQ ? P : 1];
+  T* fu = STAGED ? fl : fu_;
 #pragma unroll
   for (int p = 0; p < P; ++p) {
     const int j = j0 + p;
     const bool in = valid && j < n;
     v[p] = in ? rhs(j) : T(0);
     fl[p] = in ? fac.l(j) : T(0);
-    fu[p] = in ? fac.ui(j) : T(0);
-    fc[p] = in ? fac.cu(j) : T(0);
+    if constexpr (!STAGED) {
+      fu_[p] = in ? fac.ui(j) : T(0);
+      fc[p] = in ? fac.cu(j) : T(0);
+    }
     if constexpr (kPrefetchQ) fqv[p] = in ? fac.q(j) : T(0);
   }
   // forward substitution y_j = d_j - l_j y_{j-1}  (padding: l = 0, d = 0 -> identity-like)
@@ -605,6 +644,15 @@ __device__ void solve_lines(int n, bool valid, Rhs rhs, Fac fac, T vf, T inv, Ou
     if (valid && j0 + p < n) {
       prev = fma(-fl[p], prev, v[p]);
       v[p] = prev;
+    }
+  }
+  if constexpr (STAGED) {
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+      const int j = j0 + p;
+      const bool in = valid && j < n;
+      fu[p] = in ? fac.ui(j) : T(0);
+      fc[p] = in ? fac.cu(j) : T(0);
     }
   }
   // backward substitution x_j = ui_j y_j - cu_j x_{j+1}
@@ -710,7 +758,7 @@ __device__ void relax_origin(const RingArgs<T>& a, T beta) {
 
 // One zebra half-sweep over the lines [kbase, kbase + RW) of the parity (all threads of
 // the CTA call it together).
-template <typename T, int P>
+template <typename T, int P, bool STAGED>
 __device__ void ring_body(const RingArgs<T>& a, T beta, int kbase) {
   const Shape& sh = a.L.sh;
   const int nl = a.parity ? sh.no : sh.ne;
@@ -727,15 +775,25 @@ __device__ void ring_body(const RingArgs<T>& a, T beta, int kbase) {
   RingFac<T> fac{a.L.fl, a.L.fui, a.L.fcu, a.L.fq, own};
   const RingRhs<T> rhs = make_ring_rhs(a, beta, valid ? i : 1);
   T* x = a.x;
-  solve_lines<T, P>(sh.n, valid, rhs, fac, vf, inv, [&](int j, T v) { x[own.at(j)] = v; });
+  solve_lines<T, P, STAGED>(sh.n, valid, rhs, fac, vf, inv,
+                            [&](int j, T v) { x[own.at(j)] = v; });
 }
 
 template <typename T, int P>
 __global__ void __launch_bounds__(512) k_ring(RingArgs<T> a) {
   if (a.done && *a.done) return;
   const T beta = (T)a.par[1];
-  ring_body<T, P>(a, beta, blockIdx.x * blockDim.x);
+  ring_body<T, P, false>(a, beta, blockIdx.x * blockDim.x);
   // the origin is relaxed with the even rings; ring 1 (odd) is not written here
+  if (a.parity == 0 && blockIdx.x == 0 && blockIdx.y == 0) relax_origin(a, beta);
+}
+
+// the same half-sweep with staged operand loads, two 512-thread CTAs per SM
+template <typename T, int P>
+__global__ void __launch_bounds__(512, 2) k_ring_staged(RingArgs<T> a) {
+  if (a.done && *a.done) return;
+  const T beta = (T)a.par[1];
+  ring_body<T, P, true>(a, beta, blockIdx.x * blockDim.x);
   if (a.parity == 0 && blockIdx.x == 0 && blockIdx.y == 0) relax_origin(a, beta);
 }
 
@@ -827,7 +885,7 @@ __device__ void coarsest_body(const LevelView<T>& L, const T* b, T* x, T beta) {
   if (tid == 0) {
     double tot = 0.0;
     for (int w = 0; w < (nt + 31) / 32; ++w) tot += red[w];
-    const T x0 = (T)(((double)b[0] - (double)beta * tot) / L.sc[1]);
+    const T x0 = (T)(((double)b[0] - (double)beta * tot) / L.sc[kSchurSlot<T>]);
     x[0] = x0;
     x0s = x0;
   }
@@ -849,8 +907,9 @@ __global__ void __launch_bounds__(512) k_coarsest(LevelView<T> L, const T* b, T*
 // Schur data of the coarsest level (after k_refresh): z = T_1^{-1} (beta w_1) by a ring
 // solve, and the origin row's denominator diag0 - beta sum_j o_j z_j.
 template <typename T, int P>
-__global__ void __launch_bounds__(512) k_schur(LevelView<T> L, const StepParams* sp) {
-  if (!sp->do_refresh) return;
+__global__ void __launch_bounds__(512) k_schur(LevelView<T> L, const StepParams* sp,
+                                               const double* stamp) {
+  if (!refresh_due(sp, stamp)) return;
   const T beta = (T)sp->beta;
   const Shape& sh = L.sh;
   const Line own = line_of(sh, 1);
@@ -872,7 +931,7 @@ __global__ void __launch_bounds__(512) k_schur(LevelView<T> L, const StepParams*
   if (tid == 0) {
     double tot = 0.0;
     for (int k = 0; k < (nt + 31) / 32; ++k) tot += red[k];
-    L.sc[1] = L.sc[0] - sp->beta * tot;
+    L.sc[kSchurSlot<T>] = L.sc[0] - sp->beta * tot;
   }
 }
 
@@ -888,7 +947,7 @@ constexpr int kMaxCluster = 16;
 // P = 16, in FP32 with P = 32).
 template <typename T>
 static RingShape ring_shape(int nlines, int n) {
-  RingShape s;
+  RingShape s{};
   s.RW = (sizeof(T) == 8) ? 4 : 8;
   while (s.RW > 1 && s.RW > nlines) s.RW >>= 1;
   const int maxTW = kRingThreads / s.RW;
@@ -901,6 +960,7 @@ static RingShape ring_shape(int nlines, int n) {
   if (s.TW > maxTW) s.TW = maxTW;
   while (s.RW * s.TW < 32) s.TW <<= 1;  // whole warps (the scans shuffle across lanes)
   s.CS = (n + s.TW * s.P - 1) / (s.TW * s.P);
+  s.ST = 0;
   return s;
 }
 
@@ -913,8 +973,9 @@ static size_t ring_smem(const RingShape& s) {
 template <typename T, int P>
 static int launch_ring_p(const RingArgs<T>& a, const RingShape& s, int nl, cudaStream_t st) {
   const int grid = (nl + s.RW - 1) / s.RW;
+  void (*kern)(RingArgs<T>) = s.ST ? k_ring_staged<T, P> : k_ring<T, P>;
   if (s.CS == 1) {
-    k_ring<T, P><<<grid, dim3(s.RW, s.TW), ring_smem<T>(s), st>>>(a);
+    kern<<<grid, dim3(s.RW, s.TW), ring_smem<T>(s), st>>>(a);
     return 1;
   }
   // a ring spread over the CS CTAs of a cluster (grid.y), which exchange segment maps
@@ -923,6 +984,7 @@ static int launch_ring_p(const RingArgs<T>& a, const RingShape& s, int nl, cudaS
   static bool allowed = false;
   if (!allowed && s.CS > 8) {
     cudaFuncSetAttribute(k_ring<T, P>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    cudaFuncSetAttribute(k_ring_staged<T, P>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     allowed = true;
   }
   cudaLaunchConfig_t cfg = {};
@@ -937,7 +999,7 @@ static int launch_ring_p(const RingArgs<T>& a, const RingShape& s, int nl, cudaS
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, k_ring<T, P>, a) == cudaSuccess ? 1 : -1;
+  return cudaLaunchKernelEx(&cfg, kern, a) == cudaSuccess ? 1 : -1;
 }
 
 // Candidate tile shapes of the ring solve for the autotuner: RW lines per CTA, P angles
@@ -950,13 +1012,19 @@ void ring_candidates(int nlines, int n, std::vector<RingShape>& out) {
     if (RW > 1 && RW / 2 >= nlines) break;
     for (int P = 4; P <= maxP; P <<= 1) {
       for (int CS = 1; CS <= kMaxCluster; CS <<= 1) {
-        RingShape s{RW, 1, P, CS};
+        RingShape s{RW, 1, P, CS, 0};
         const int chunks = (n + P * CS - 1) / (P * CS);
         while (s.TW < chunks) s.TW <<= 1;
         while (s.RW * s.TW < 32) s.TW <<= 1;
         if (s.RW * s.TW > kRingThreads) continue;
         if ((CS - 1) * s.TW * P >= n) continue;  // every CTA of the cluster holds angles
         out.push_back(s);
+        // staged loads where a full-size CTA would otherwise hold one CTA per SM and the
+        // three live operand arrays fit the two-CTA register budget
+        if (s.RW * s.TW == kRingThreads && P >= 8 && P * sizeof(T) <= 64) {
+          s.ST = 1;
+          out.push_back(s);
+        }
       }
     }
   }
@@ -1004,7 +1072,7 @@ int launch_restrict(const LevelView<T>& L, const LevelView<T>& C, const T* x, T*
 template <typename T>
 int launch_coarsest(const LevelView<T>& L, const T* b, T* x, Params p, const int* done,
                     cudaStream_t st) {
-  RingShape s;
+  RingShape s{};
   s.RW = 1;
   s.P = 8;
   while (s.P < 32 && (L.sh.n + s.P - 1) / s.P > kRingThreads) s.P <<= 1;
@@ -1020,8 +1088,9 @@ int launch_coarsest(const LevelView<T>& L, const T* b, T* x, Params p, const int
 }
 
 template <typename T>
-static int launch_schur(const LevelView<T>& L, const StepParams* sp, cudaStream_t st) {
-  RingShape s;
+static int launch_schur(const LevelView<T>& L, const StepParams* sp, const double* stamp,
+                        cudaStream_t st) {
+  RingShape s{};
   s.RW = 1;
   s.P = 8;
   while (s.P < 32 && (L.sh.n + s.P - 1) / s.P > kRingThreads) s.P <<= 1;
@@ -1029,9 +1098,9 @@ static int launch_schur(const LevelView<T>& L, const StepParams* sp, cudaStream_
   while (s.TW < (L.sh.n + s.P - 1) / s.P) s.TW <<= 1;
   const size_t smem = ring_smem<T>(s);
   switch (s.P) {
-    case 8: k_schur<T, 8><<<1, dim3(1, s.TW), smem, st>>>(L, sp); break;
-    case 16: k_schur<T, 16><<<1, dim3(1, s.TW), smem, st>>>(L, sp); break;
-    default: k_schur<T, 32><<<1, dim3(1, s.TW), smem, st>>>(L, sp); break;
+    case 8: k_schur<T, 8><<<1, dim3(1, s.TW), smem, st>>>(L, sp, stamp); break;
+    case 16: k_schur<T, 16><<<1, dim3(1, s.TW), smem, st>>>(L, sp, stamp); break;
+    default: k_schur<T, 32><<<1, dim3(1, s.TW), smem, st>>>(L, sp, stamp); break;
   }
   return 1;
 }
@@ -1041,7 +1110,7 @@ static int launch_schur(const LevelView<T>& L, const StepParams* sp, cudaStream_
 
 #define POLAR_MG_INST(T)                                                                      \
   template int launch_refresh<T>(const LevelView<double>*, LevelView<T>*, int,                \
-                                 const StepParams*, double*, cudaStream_t);                   \
+                                 const StepParams*, double*, cudaStream_t, double*);          \
   template int launch_ring<T>(const LevelView<T>&, const LevelView<T>&, const T*, T*,          \
                               const T*, Params, int, int, const int*, cudaStream_t,           \
                               const RingShape*);                                              \

@@ -68,3 +68,19 @@ def batch_advance(batch, problems, k0=0, k1=None, opts=None, check=True):
         ts.append(t[k0:kk + 1])
         ws.append(p.weight_table()[k0:kk + 1])
     return P.polar_batch_advance(batch, ts, [p.theta_w for p in problems], ws, opts, check)
+
+
+def sweep(problems, precision=P.POLAR_FP64, stream=None, opts=None):
+    """Advances every problem over its whole schedule together: one polar_batch whose
+    CUDA graph holds a step of every instance per launch (parameter sweeps, mesh-tuning
+    studies).  The problems must have the same number of steps.  Returns the final
+    states and the per-instance step statistics."""
+    K = len(problems[0].t) - 1
+    if any(len(p.t) - 1 != K for p in problems):
+        raise ValueError("every problem of a sweep needs the same number of steps")
+    ctxs = [create(p, precision, stream) for p in problems]
+    batch = P.polar_batch_create(ctxs, stream)
+    stats, _ = batch_advance(batch, problems, 0, K, opts)
+    states = [P.polar_get_state(c)[0] for c in ctxs]
+    P.polar_batch_destroy(batch)
+    return states, stats
