@@ -223,9 +223,14 @@ int polar_advance(polar_ctx* ctx, int32_t nsteps, const double* t, double theta,
  * must keep them alive); polar_batch_advance advances every instance over its own
  * schedule of nsteps steps: t[i] holds nsteps+1 levels of instance i (t[i][0] its current
  * time), theta[i] its implicit weight, w[i] its (nsteps+1) x nsrc source weights (w may be
- * NULL when no instance has sources).  One CUDA graph holds one step of every instance
- * as independent branches (each with its device-side refinement and Krylov loops) and is
- * launched nsteps times on `stream`; the graph is rebuilt when a context changed.  stats
+ * NULL when no instance has sources).  One CUDA graph advances every instance by one step
+ * and is launched nsteps times on `stream`: each kernel class of the step runs as one
+ * launch per phase over a work list of (instance, block) -- every instance keeps the
+ * block partition of its own launches, so its result equals that of advancing it alone
+ * bit for bit -- and the refinement and Krylov loops run while any instance still needs
+ * them, the instances that are done masked out.  Launches whose block or cluster shape
+ * differs between instances (ring-solve tiles, coarsest-level solves) run once per shape.
+ * The graph is rebuilt when a context changed.  stats
  * (count x nsteps, instance-major) or NULL.  An instance stops at its first failing step
  * (state kept at its last committed level, later entries POLAR_ESTATE); the others go on.
  * Returns the first error of any instance.  Contexts must not be stepped concurrently
@@ -236,6 +241,9 @@ int polar_batch_destroy(polar_batch* batch);
 int polar_batch_advance(polar_batch* batch, int32_t nsteps, const double* const* t,
                         const double* theta, const double* const* w,
                         const polar_solver_opts* opts, polar_step_stats* stats);
+/* Number of CUDA kernels the batch's step graphs have launched (counted from the steps'
+ * sweep and iteration counts). */
+int64_t polar_batch_kernel_launches(const polar_batch* batch);
 
 /* y = (alpha I + beta L) x for one vector x with homogeneous Dirichlet data
  * (g = 0): the matrix-free operator every kernel of the step is built on.

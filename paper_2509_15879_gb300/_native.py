@@ -86,6 +86,7 @@ EXPORTS = {
     "polar_batch_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int32, C.c_void_p,
                                      C.POINTER(C.c_void_p)]),
     "polar_batch_destroy": (C.c_int, [C.c_void_p]),
+    "polar_batch_kernel_launches": (C.c_int64, [C.c_void_p]),
     "polar_batch_advance": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(_dp), _dp, C.POINTER(_dp),
                                       C.POINTER(polar_solver_opts), C.POINTER(polar_step_stats)]),
     "polar_timing_enable": (C.c_int, [C.c_void_p, C.c_int32]),
@@ -361,6 +362,10 @@ def polar_batch_create(ctxs, stream=None) -> Batch:
     h = C.c_void_p()
     _check(load().polar_batch_create(arr, len(ctxs), stream, C.byref(h)))
     return Batch(h, ctxs)
+
+
+def polar_batch_kernel_launches(batch: Batch) -> int:
+    return int(load().polar_batch_kernel_launches(batch.handle))
 
 
 def polar_batch_destroy(batch: Batch):

@@ -89,9 +89,15 @@ struct polar_ctx;
 struct polar_batch {
   std::vector<polar_ctx*> ctx;
   cudaStream_t st = nullptr;
+  cudaStream_t cap = nullptr;  // private stream for graph capture
   cudaGraph_t g = nullptr;
   cudaGraphExec_t ex = nullptr;
-  std::vector<int64_t> gens;  // context generations the graph was captured with
+  std::vector<int64_t> gens;   // context generations the graph was captured with
+  void* arena = nullptr;       // argument tables and work lists of the batched launches
+  size_t arena_bytes = 0;
+  // kernels per batch step: fixed, per refinement sweep, per FP32 / FP64 Krylov iteration
+  int64_t kernels_fixed = 0, kernels_sweep = 0, kernels_iter32 = 0, kernels_iter64 = 0;
+  int64_t launches = 0;        // kernels launched by the batch's graphs
 };
 
 struct polar_ctx {
@@ -497,6 +503,15 @@ const std::vector<LevelView<T>>& views(const polar_ctx* c) {
 
 // Per-step refresh: the matrix S = alpha V + beta V L changes with dt and theta.  The
 // kernel reads alpha, beta and do_refresh from the step parameters.
+// Kernel-class name for the per-kernel timing: ".f32" marks FP32 launches (a mixed
+// context runs FP32 and FP64 versions of the same kernels).
+template <typename T>
+const char* tname(const char* base) {
+  static thread_local std::string s;
+  s = std::string(base) + (sizeof(T) == 4 ? ".f32" : "");
+  return s.c_str();
+}
+
 // `stamp` (the mixed path's FP64 factors): formed on demand, once per (alpha, beta).
 template <typename T>
 int launch_refresh_all(polar_ctx* c, double* stamp = nullptr) {
@@ -551,7 +566,8 @@ int vcycle(polar_ctx* c, const T* b, T* x) {
   // kernel classes are timed per level group: the fine level, level 1, and the rest
   auto nm = [&](const char* base, int l) {
     static thread_local std::string s;
-    s = std::string(base) + (l == 0 ? "@L0" : l == 1 ? "@L1" : "@L2+");
+    s = std::string(base) + (l == 0 ? "@L0" : l == 1 ? "@L1" : "@L2+") +
+        (sizeof(T) == 4 ? ".f32" : "");
     return s.c_str();
   };
   const int lc = nl - 1;
@@ -571,7 +587,7 @@ int vcycle(polar_ctx* c, const T* b, T* x) {
             launch_restrict<T>(L[l], L[l + 1], xof(l), coarse_b<T>(c, l + 1), par, done,
                                c->cs));
   }
-  TLAUNCH("coarsest", 8 * B * L[nl - 1].sh.n,
+  TLAUNCH(tname<T>("coarsest"), 8 * B * L[nl - 1].sh.n,
           launch_coarsest<T>(L[nl - 1], bof(nl - 1), xof(nl - 1), par, done, c->cs));
   for (int l = lc - 1; l >= 0; --l) {
     const Shape& s = L[l].sh;
@@ -707,14 +723,14 @@ int bicg_iteration(polar_ctx* c, CondHandle cond) {
   const double B = sizeof(T), pts = (double)c->m * c->n;
   TRY(vcycle<T>(c, k.p, k.phat));
   // stencil with dot: reads x, diag, 4 couplings, d1; writes y (8 words per point)
-  TLAUNCH("stencil_dot", 8 * B * pts, launch_apply_dot<T>(L0, c->par(), k.phat, k.v, k.rhat, 0, c->cs, red));
-  TLAUNCH("bicg_s", 3 * B * nv, launch_bicg_s<T>(nv, k.r, k.v, k.s, c->cs, red));
+  TLAUNCH(tname<T>("stencil_dot"), 8 * B * pts, launch_apply_dot<T>(L0, c->par(), k.phat, k.v, k.rhat, 0, c->cs, red));
+  TLAUNCH(tname<T>("bicg_s"), 3 * B * nv, launch_bicg_s<T>(nv, k.r, k.v, k.s, c->cs, red));
   TRY(vcycle<T>(c, k.s, k.shat));
-  TLAUNCH("stencil_dot", 8 * B * pts, launch_apply_dot<T>(L0, c->par(), k.shat, k.t, k.s, 1, c->cs, red));
-  TLAUNCH("bicg_update", 9 * B * nv,
+  TLAUNCH(tname<T>("stencil_dot"), 8 * B * pts, launch_apply_dot<T>(L0, c->par(), k.shat, k.t, k.s, 1, c->cs, red));
+  TLAUNCH(tname<T>("bicg_update"), 9 * B * nv,
           launch_bicg_update<T>(nv, k.d, k.phat, k.shat, k.r, k.s, k.t, k.rhat, L0.diag,
                                 L0.sc, c->cs, red));
-  TLAUNCH("bicg_p", 4 * B * nv, launch_bicg_p<T>(nv, k.p, k.r, k.v, cond, c->cs, red));
+  TLAUNCH(tname<T>("bicg_p"), 4 * B * nv, launch_bicg_p<T>(nv, k.p, k.r, k.v, cond, c->cs, red));
   return POLAR_OK;
 }
 
@@ -729,11 +745,11 @@ int cg_iteration(polar_ctx* c, CondHandle cond) {
   const size_t nv = c->nv();
   const double B = sizeof(T), pts = (double)c->m * c->n;
   TRY(vcycle<T>(c, k.r, k.phat));
-  TLAUNCH("cg_rho", 2 * B * nv, launch_cg_rho<T>(nv, k.r, k.phat, c->cs, red));
-  TLAUNCH("cg_p", 3 * B * nv, launch_cg_p<T>(nv, k.p, k.phat, c->cs, red));
+  TLAUNCH(tname<T>("cg_rho"), 2 * B * nv, launch_cg_rho<T>(nv, k.r, k.phat, c->cs, red));
+  TLAUNCH(tname<T>("cg_p"), 3 * B * nv, launch_cg_p<T>(nv, k.p, k.phat, c->cs, red));
   // stencil with dot: reads p, diag, 4 couplings; writes q (7 words per point)
-  TLAUNCH("stencil_dot", 7 * B * pts, launch_apply_dot<T>(L0, c->par(), k.p, k.v, k.p, 0, c->cs, red));
-  TLAUNCH("cg_update", 7 * B * nv,
+  TLAUNCH(tname<T>("stencil_dot"), 7 * B * pts, launch_apply_dot<T>(L0, c->par(), k.p, k.v, k.p, 0, c->cs, red));
+  TLAUNCH(tname<T>("cg_update"), 7 * B * nv,
           launch_cg_update<T>(nv, k.d, k.p, k.r, k.v, L0.diag, L0.sc, cond, c->cs, red));
   return POLAR_OK;
 }
@@ -749,8 +765,8 @@ int bicg_begin(polar_ctx* c, CondHandle cond) {
   KVecs<T>& k = kvecs<T>(c);
   const size_t nv = c->nv();
   const Reduce red = c->red();
-  TLAUNCH("scale_cast", (8.0 + sizeof(T)) * nv, launch_scale_cast<T>(nv, c->r64, k.r, c->cs, red));
-  TLAUNCH("bicg_init", 5.0 * sizeof(T) * nv,
+  TLAUNCH(tname<T>("scale_cast"), (8.0 + sizeof(T)) * nv, launch_scale_cast<T>(nv, c->r64, k.r, c->cs, red));
+  TLAUNCH(tname<T>("bicg_init"), 5.0 * sizeof(T) * nv,
           launch_bicg_init<T>(nv, k.r, k.rhat, k.p, k.v, k.d, c->sp, cond, c->cs, red));
   return POLAR_OK;
 }
@@ -764,7 +780,7 @@ int resid(polar_ctx* c) {
 template <typename T>
 int correct(polar_ctx* c) {
   const size_t nv = c->nv();
-  TLAUNCH("correct", (16.0 + sizeof(T)) * nv, launch_correct<T>(nv, c->X, kvecs<T>(c).d, c->cs, c->red()));
+  TLAUNCH(tname<T>("correct"), (16.0 + sizeof(T)) * nv, launch_correct<T>(nv, c->X, kvecs<T>(c).d, c->cs, c->red()));
   return POLAR_OK;
 }
 
@@ -1190,7 +1206,8 @@ int load_schedule(polar_ctx* c, int32_t K, const double* t, double theta, const 
 
 // Reads the results of the K steps just run, fills stats, advances t to the last
 // committed level and returns the first failure.
-int finish_schedule(polar_ctx* c, int32_t K, const double* t, polar_step_stats* stats) {
+int finish_schedule(polar_ctx* c, int32_t K, const double* t, polar_step_stats* stats,
+                    bool count_launches = true) {
   CUDA_TRY(cudaMemcpyAsync(c->out_host, c->dout, (size_t)K * sizeof(StepOut),
                            cudaMemcpyDeviceToHost, c->st));
   CUDA_TRY(cudaStreamSynchronize(c->st));
@@ -1206,7 +1223,12 @@ int finish_schedule(polar_ctx* c, int32_t K, const double* t, polar_step_stats* 
       stats[k].fp64_iters = r.iters64;
       stats[k].scaled_resid = r.scaled;
     }
-    if (r.status != POLAR_ESTATE) {
+    if (!count_launches) {
+      if (r.status != POLAR_ESTATE) {
+        c->cur_alpha = c->sched_host[k].alpha;
+        c->cur_beta = c->sched_host[k].beta;
+      }
+    } else if (r.status != POLAR_ESTATE) {
       c->launches += 2 + c->graph_kernels_fixed + (int64_t)std::max(r.sweeps - 1, 0) * c->graph_kernels_sweep +
                      (int64_t)(r.iters - r.iters64) * c->graph_kernels_iter +
                      (int64_t)r.iters64 * c->graph_kernels_iter64;
@@ -1412,6 +1434,751 @@ int setup_direct(polar_ctx* c, const HLevel& H) {
   R.o = H.o[0];
   R.osum = 0.0;
   for (double v : H.o) R.osum += v;
+  return POLAR_OK;
+}
+
+// ---- batched execution: one launch per kernel class and phase for all instances.
+//
+// A batch step graph is built in two passes of the same code: the plan pass collects every
+// launch's per-instance argument table and work list in a host image; the image goes to
+// the device in one copy; the capture pass records the launches, whose tables now sit at
+// the same offsets of the device arena.  Every instance keeps its own grid partition
+// (BWork: block vb of its lone grid vg), so its arithmetic -- and its result -- is the same
+// as when it runs alone.  Gates and per-instance `done` flags mask the instances a launch
+// does not serve at that moment; WHILE nodes loop while any instance is still active.
+
+struct BatchBuild {
+  polar_batch* b = nullptr;
+  bool plan = true;                  // plan pass (collect) or capture pass (launch)
+  std::vector<unsigned char> image;  // arena image (plan pass)
+  unsigned char* dev = nullptr;      // arena (capture pass)
+  size_t off = 0;
+  cudaStream_t cs = nullptr;         // capture stream
+  int64_t launches = 0;              // kernels captured so far
+
+  // a table in the arena: appended in the plan pass, its device address in the capture pass
+  template <class A>
+  const A* put(const std::vector<A>& v) {
+    off = (off + 255) & ~(size_t)255;
+    const size_t at = off;
+    off += std::max<size_t>(v.size(), 1) * sizeof(A);
+    if (plan) {
+      image.resize(off);
+      if (!v.empty()) std::memcpy(image.data() + at, v.data(), v.size() * sizeof(A));
+      return nullptr;
+    }
+    return reinterpret_cast<const A*>(dev + at);
+  }
+  // launch helper: counts, checks, skips in the plan pass
+  template <class F>
+  int launch(F f) {
+    if (plan) return POLAR_OK;
+    const int k = f();
+    if (k < 0) {
+      const cudaError_t e = cudaGetLastError();
+      return fail(POLAR_ECUDA, std::string("batched launch: ") + cudaGetErrorString(e));
+    }
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(POLAR_ECUDA, std::string("batched launch: ") + cudaGetErrorString(e));
+    launches += k;
+    return POLAR_OK;
+  }
+};
+
+// per-instance facts the planner groups by
+struct BInst {
+  polar_ctx* c;
+  int idx;          // position in the batch
+  bool mixed;       // FP32 inner solves (and the FP64 fallback)
+  bool direct;      // separable: the direct inner solve
+};
+
+BWork bwork(const polar_ctx* c, int inst, int vb, int vg, int aux) {
+  return BWork{inst, vb, vg, aux, c->ks, c->sp};
+}
+
+// Work list of a grid-stride launch: instance k of `list` gets vg = grid_of(c) blocks.
+template <class G>
+std::vector<BWork> grid_work(const std::vector<const BInst*>& list, G grid_of) {
+  std::vector<BWork> w;
+  for (int k = 0; k < (int)list.size(); ++k) {
+    const int vg = grid_of(list[k]->c);
+    for (int vb = 0; vb < vg; ++vb) w.push_back(bwork(list[k]->c, k, vb, vg, 0));
+  }
+  return w;
+}
+
+int stencil_grid(const Shape& sh) {
+  const Tiling t = make_tiling(sh);
+  return t.ntiles > kMaxBlocks ? kMaxBlocks : t.ntiles;
+}
+
+template <typename T>
+StArgs<T> st_args(const polar_ctx* c, const T* x, T* y, const T* d1, const T* b) {
+  StArgs<T> a{};
+  a.L = views<T>(c)[0];
+  a.par = c->par();
+  a.x = x;
+  a.b = b;
+  a.y = y;
+  a.d1 = d1;
+  a.red = c->red();
+  a.t = make_tiling(a.L.sh);
+  return a;
+}
+
+template <typename T>
+VecArgs<T> vargs(const polar_ctx* c) {
+  VecArgs<T> a{};
+  a.nv = c->nv();
+  a.red = c->red();
+  a.sp = c->sp;
+  return a;
+}
+
+// Stencil launches: instances grouped by their tiling's TK (the block shape).
+template <typename T, class MakeArgs>
+int batch_stencil(BatchBuild& B, int mode, const std::vector<const BInst*>& list, int gate,
+                  MakeArgs make) {
+  for (int TK = 32; TK <= 256; TK <<= 1) {
+    std::vector<const BInst*> sub;
+    std::vector<StArgs<T>> args;
+    for (const BInst* i : list)
+      if (make_tiling(i->c->sh0()).TK == TK) {
+        sub.push_back(i);
+        args.push_back(make(i->c));
+      }
+    if (sub.empty()) continue;
+    const std::vector<BWork> w = grid_work(sub, [](const polar_ctx* c) { return stencil_grid(c->sh0()); });
+    const StArgs<T>* A = B.put(args);
+    const BWork* W = B.put(w);
+    TRY(B.launch([&] { return launch_stencil_b<T>(mode, A, W, (int)w.size(), TK, gate, B.cs); }));
+  }
+  return POLAR_OK;
+}
+
+// Vector-kernel launch over `list` (grid_for(nv) blocks each).
+template <typename T, class MakeArgs>
+int batch_vec(BatchBuild& B, int kind, const std::vector<const BInst*>& list, int gate,
+              MakeArgs make) {
+  if (list.empty()) return POLAR_OK;
+  std::vector<VecArgs<T>> args;
+  for (const BInst* i : list) args.push_back(make(i->c));
+  const std::vector<BWork> w = grid_work(list, [](const polar_ctx* c) { return grid_for(c->nv(), 256); });
+  const VecArgs<T>* A = B.put(args);
+  const BWork* W = B.put(w);
+  return B.launch([&] { return launch_vec_b<T>(kind, A, W, (int)w.size(), gate, B.cs); });
+}
+
+CtlArgs ctl_args(polar_ctx* c) {
+  CtlArgs a{};
+  a.sched = c->sched;
+  a.kstep = c->kstep;
+  a.kstep_w = c->kstep;
+  a.sp = c->sp;
+  a.out = c->dout;
+  a.ks = c->ks;
+  return a;
+}
+
+int batch_ctl(BatchBuild& B, int kind, const std::vector<const BInst*>& list, int gate) {
+  if (list.empty()) return POLAR_OK;
+  std::vector<CtlArgs> args;
+  for (const BInst* i : list) args.push_back(ctl_args(i->c));
+  const CtlArgs* A = B.put(args);
+  return B.launch([&] { return launch_ctl_b(kind, A, (int)args.size(), gate, B.cs); });
+}
+
+int batch_any(BatchBuild& B, const std::vector<const BInst*>& list, int gate, int need_running,
+              CondHandle cond) {
+  std::vector<CtlArgs> args;
+  for (const BInst* i : list) args.push_back(ctl_args(i->c));
+  const CtlArgs* A = B.put(args);
+  return B.launch([&] { return launch_any_b(A, (int)args.size(), gate, need_running, cond, B.cs); });
+}
+
+// Inputs and outputs of one V-cycle per instance (level 0 vectors in precision T).
+template <typename T>
+struct VIO {
+  const T* b;
+  T* x;
+};
+
+// One batched V(1,1) cycle of every instance of `list`: down through the levels
+// (pre-smoothing of odd then even rings, restriction), the coarsest solves, up again
+// (post-smoothing of even then odd rings).  A phase serves the instances that have the
+// level; ring launches are grouped by tile shape (the block and cluster shape of a
+// launch).  Each instance checks its own `done` flag, as its lone cycle does.
+template <typename T>
+int batch_vcycle(BatchBuild& B, const std::vector<const BInst*>& list,
+                 const std::vector<VIO<T>>& io, int gate) {
+  int lmax = 0;
+  for (const BInst* i : list) lmax = std::max(lmax, i->c->nlev() - 1);
+  auto bof = [&](int k, int l) { return l == 0 ? io[k].b : static_cast<const T*>(coarse_b<T>(list[k]->c, l)); };
+  auto xof = [&](int k, int l) { return l == 0 ? io[k].x : coarse_x<T>(list[k]->c, l); };
+  auto ring_phase = [&](int l, int mode, int parity) -> int {
+    // (shape -> instances) for this level, mode and parity
+    std::vector<std::pair<RingShape, std::vector<int>>> groups;
+    for (int k = 0; k < (int)list.size(); ++k) {
+      polar_ctx* c = list[k]->c;
+      if (l >= c->nlev() - 1) continue;
+      const LevelView<T>& L = views<T>(c)[l];
+      const int nl = parity ? L.sh.no : L.sh.ne;
+      if (nl == 0) continue;
+      const RingShape* t = tile<T>(c, l, mode, parity);
+      const RingShape s = t ? *t : ring_default<T>(nl, L.sh.n);
+      bool found = false;
+      for (auto& g : groups)
+        if (std::memcmp(&g.first, &s, sizeof(RingShape)) == 0) {
+          g.second.push_back(k);
+          found = true;
+        }
+      if (!found) groups.push_back({s, {k}});
+    }
+    for (auto& g : groups) {
+      const RingShape& s = g.first;
+      std::vector<RingArgs<T>> args;
+      std::vector<BWork> w;
+      for (int k : g.second) {
+        polar_ctx* c = list[k]->c;
+        const std::vector<LevelView<T>>& L = views<T>(c);
+        RingArgs<T> a{};
+        a.L = L[l];
+        a.C = L[l + 1];
+        a.b = bof(k, l);
+        a.x = xof(k, l);
+        a.X = mode == RING_POST ? coarse_x<T>(c, l + 1) : nullptr;
+        a.par = c->par();
+        a.done = &c->ks->done;
+        a.parity = parity;
+        a.mode = mode;
+        const int nl = parity ? L[l].sh.no : L[l].sh.ne;
+        const int ng = (nl + s.RW - 1) / s.RW;
+        for (int q = 0; q < ng; ++q) w.push_back(bwork(c, (int)args.size(), q, ng, q * s.RW));
+        args.push_back(a);
+      }
+      const RingArgs<T>* A = B.put(args);
+      const BWork* W = B.put(w);
+      TRY(B.launch([&] { return launch_ring_b<T>(s, A, W, (int)w.size(), gate, B.cs); }));
+    }
+    return POLAR_OK;
+  };
+  for (int l = 0; l < lmax; ++l) {
+    TRY(ring_phase(l, RING_PRE, 1));
+    TRY(ring_phase(l, RING_PRE, 0));
+    std::vector<const BInst*> sub;
+    std::vector<RestrictArgs<T>> args;
+    for (int k = 0; k < (int)list.size(); ++k) {
+      polar_ctx* c = list[k]->c;
+      if (l >= c->nlev() - 1) continue;
+      const std::vector<LevelView<T>>& L = views<T>(c);
+      args.push_back(RestrictArgs<T>{L[l], L[l + 1], xof(k, l), coarse_b<T>(c, l + 1), c->par(),
+                                     &c->ks->done});
+      sub.push_back(list[k]);
+    }
+    if (!sub.empty()) {
+      const int lv = l;
+      const std::vector<BWork> w = grid_work(sub, [&](const polar_ctx* c) {
+        const std::vector<LevelView<T>>& L = views<T>(c);
+        return grid_for((size_t)L[lv + 1].sh.m * L[lv].sh.n, 256);
+      });
+      const RestrictArgs<T>* A = B.put(args);
+      const BWork* W = B.put(w);
+      TRY(B.launch([&] { return launch_restrict_b<T>(A, W, (int)w.size(), gate, B.cs); }));
+    }
+  }
+  // coarsest levels, grouped by their launch shape
+  std::vector<std::pair<std::pair<int, int>, std::vector<int>>> cg;
+  for (int k = 0; k < (int)list.size(); ++k) {
+    const LevelView<T>& L = views<T>(list[k]->c).back();
+    int P = 0, TW = 0;
+    coarsest_shape<T>(L.sh.n, &P, &TW);
+    bool found = false;
+    for (auto& g : cg)
+      if (g.first == std::make_pair(P, TW)) {
+        g.second.push_back(k);
+        found = true;
+      }
+    if (!found) cg.push_back({{P, TW}, {k}});
+  }
+  for (auto& g : cg) {
+    std::vector<CoarsestArgs<T>> args;
+    std::vector<BWork> w;
+    for (int k : g.second) {
+      polar_ctx* c = list[k]->c;
+      const int lc = c->nlev() - 1;
+      CoarsestArgs<T> a{};
+      a.L = views<T>(c)[lc];
+      a.b = bof(k, lc);
+      a.x = xof(k, lc);
+      a.par = c->par();
+      a.done = &c->ks->done;
+      w.push_back(bwork(c, (int)args.size(), 0, 1, 0));
+      args.push_back(a);
+    }
+    const CoarsestArgs<T>* A = B.put(args);
+    const BWork* W = B.put(w);
+    const int P = g.first.first, TW = g.first.second;
+    TRY(B.launch([&] { return launch_coarsest_b<T>(P, TW, 0, A, W, (int)w.size(), gate, B.cs); }));
+  }
+  for (int l = lmax - 1; l >= 0; --l) {
+    TRY(ring_phase(l, RING_POST, 0));
+    TRY(ring_phase(l, RING_POST, 1));
+  }
+  return POLAR_OK;
+}
+
+// Per-step refresh of every instance of `list` in precision T (the refresh kernel checks
+// each instance's do_refresh, or its stamp when `stamped`), then the coarsest levels'
+// Schur data and, when stamped, the stamps.
+template <typename T>
+int batch_refresh(BatchBuild& B, const std::vector<const BInst*>& list, bool stamped, int gate) {
+  if (list.empty()) return POLAR_OK;
+  std::vector<RefreshArgs> args;
+  std::vector<BWork> w;
+  for (int k = 0; k < (int)list.size(); ++k) {
+    polar_ctx* c = list[k]->c;
+    std::vector<LevelView<T>> vt = views<T>(c);
+    int nb = 0;
+    args.push_back(make_refresh_args<T>(c->v64.data(), vt.data(), c->nlev(), c->sp, c->ws,
+                                        stamped ? c->stamp64 : nullptr, &nb));
+    for (int vb = 0; vb < nb; ++vb) w.push_back(bwork(c, k, vb, nb, 0));
+  }
+  const RefreshArgs* A = B.put(args);
+  const BWork* W = B.put(w);
+  TRY(B.launch([&] { return launch_refresh_b<T>(A, W, (int)w.size(), gate, B.cs); }));
+  std::vector<std::pair<std::pair<int, int>, std::vector<int>>> cg;
+  for (int k = 0; k < (int)list.size(); ++k) {
+    int P = 0, TW = 0;
+    coarsest_shape<T>(views<T>(list[k]->c).back().sh.n, &P, &TW);
+    bool found = false;
+    for (auto& g : cg)
+      if (g.first == std::make_pair(P, TW)) {
+        g.second.push_back(k);
+        found = true;
+      }
+    if (!found) cg.push_back({{P, TW}, {k}});
+  }
+  for (auto& g : cg) {
+    std::vector<CoarsestArgs<T>> sargs;
+    std::vector<BWork> sw;
+    for (int k : g.second) {
+      polar_ctx* c = list[k]->c;
+      CoarsestArgs<T> a{};
+      a.L = views<T>(c).back();
+      a.sp = c->sp;
+      a.stamp = stamped ? c->stamp64 : nullptr;
+      sw.push_back(bwork(c, (int)sargs.size(), 0, 1, 0));
+      sargs.push_back(a);
+    }
+    const CoarsestArgs<T>* A2 = B.put(sargs);
+    const BWork* W2 = B.put(sw);
+    const int P = g.first.first, TW = g.first.second;
+    TRY(B.launch([&] { return launch_coarsest_b<T>(P, TW, 1, A2, W2, (int)sw.size(), gate, B.cs); }));
+  }
+  if (stamped) {
+    std::vector<double*> stamps;
+    std::vector<BWork> ow;
+    for (int k = 0; k < (int)list.size(); ++k) {
+      ow.push_back(bwork(list[k]->c, k, 0, 1, 0));
+      stamps.push_back(list[k]->c->stamp64);
+    }
+    double* const* S = B.put(stamps);
+    const BWork* W3 = B.put(ow);
+    TRY(B.launch([&] { return launch_stamp_b(W3, S, (int)ow.size(), gate, B.cs); }));
+  }
+  return POLAR_OK;
+}
+
+// One Krylov iteration of every instance of `list` in precision T: CG for the symmetric
+// ones, BiCGStab for the others (each instance's kernels in its lone order).
+template <typename T>
+int batch_iteration(BatchBuild& B, const std::vector<const BInst*>& list, int gate) {
+  std::vector<const BInst*> cgl, bil;
+  for (const BInst* i : list) (i->c->symmetric ? cgl : bil).push_back(i);
+  std::vector<VIO<T>> io;
+  for (const BInst* i : list) {
+    KVecs<T>& k = kvecs<T>(i->c);
+    io.push_back(i->c->symmetric ? VIO<T>{k.r, k.phat} : VIO<T>{k.p, k.phat});
+  }
+  TRY(batch_vcycle<T>(B, list, io, gate));
+  TRY(batch_vec<T>(B, V_CG_RHO, cgl, gate, [](polar_ctx* c) {
+    VecArgs<T> a = vargs<T>(c);
+    a.v0 = kvecs<T>(c).r;
+    a.v1 = kvecs<T>(c).phat;
+    return a;
+  }));
+  TRY(batch_vec<T>(B, V_CG_P, cgl, gate, [](polar_ctx* c) {
+    VecArgs<T> a = vargs<T>(c);
+    a.v0 = kvecs<T>(c).p;
+    a.v1 = kvecs<T>(c).phat;
+    return a;
+  }));
+  // q = S p (CG) and v = S phat (BiCGStab), both the stencil's DOTV mode
+  TRY(batch_stencil<T>(B, M_DOTV, list, gate, [](polar_ctx* c) {
+    KVecs<T>& k = kvecs<T>(c);
+    return c->symmetric ? st_args<T>(c, k.p, k.v, k.p, nullptr)
+                        : st_args<T>(c, k.phat, k.v, k.rhat, nullptr);
+  }));
+  TRY(batch_vec<T>(B, V_CG_UPDATE, cgl, gate, [](polar_ctx* c) {
+    KVecs<T>& k = kvecs<T>(c);
+    VecArgs<T> a = vargs<T>(c);
+    a.v0 = k.d;
+    a.v1 = k.p;
+    a.v2 = k.r;
+    a.v3 = k.v;
+    a.diag = views<T>(c)[0].diag;
+    a.sc = views<T>(c)[0].sc;
+    return a;
+  }));
+  if (bil.empty()) return POLAR_OK;
+  TRY(batch_vec<T>(B, V_BICG_S, bil, gate, [](polar_ctx* c) {
+    KVecs<T>& k = kvecs<T>(c);
+    VecArgs<T> a = vargs<T>(c);
+    a.v0 = k.r;
+    a.v1 = k.v;
+    a.v2 = k.s;
+    return a;
+  }));
+  std::vector<VIO<T>> io2;
+  for (const BInst* i : bil) io2.push_back(VIO<T>{kvecs<T>(i->c).s, kvecs<T>(i->c).shat});
+  TRY(batch_vcycle<T>(B, bil, io2, gate));
+  TRY(batch_stencil<T>(B, M_DOTT, bil, gate, [](polar_ctx* c) {
+    KVecs<T>& k = kvecs<T>(c);
+    return st_args<T>(c, k.shat, k.t, k.s, nullptr);
+  }));
+  TRY(batch_vec<T>(B, V_BICG_UPDATE, bil, gate, [](polar_ctx* c) {
+    KVecs<T>& k = kvecs<T>(c);
+    VecArgs<T> a = vargs<T>(c);
+    a.v0 = k.d;
+    a.v1 = k.phat;
+    a.v2 = k.shat;
+    a.v3 = k.r;
+    a.v4 = k.s;
+    a.v5 = k.t;
+    a.v6 = k.rhat;
+    a.diag = views<T>(c)[0].diag;
+    a.sc = views<T>(c)[0].sc;
+    return a;
+  }));
+  TRY(batch_vec<T>(B, V_BICG_P, bil, gate, [](polar_ctx* c) {
+    KVecs<T>& k = kvecs<T>(c);
+    VecArgs<T> a = vargs<T>(c);
+    a.v0 = k.p;
+    a.v1 = k.r;
+    a.v2 = k.v;
+    return a;
+  }));
+  return POLAR_OK;
+}
+
+// Batched direct solves (separable instances): scaled cast, transform / modes / inverse.
+int batch_direct(BatchBuild& B, const std::vector<const BInst*>& list, int gate) {
+  if (list.empty()) return POLAR_OK;
+  TRY(batch_vec<double>(B, V_SCALE_CAST, list, gate, [](polar_ctx* c) {
+    VecArgs<double> a = vargs<double>(c);
+    a.v0 = c->kv64.r;
+    a.w0 = c->r64;
+    return a;
+  }));
+  std::vector<DirectArgs> args;
+  std::vector<BWork> wr, wm, wo;
+  size_t smem = 0;
+  for (int k = 0; k < (int)list.size(); ++k) {
+    polar_ctx* c = list[k]->c;
+    DirectArgs a{};
+    a.sh = c->sh0();
+    a.P = c->plan;
+    a.R = c->sep;
+    a.par = c->par();
+    a.b = c->kv64.r;
+    a.x = c->kv64.d;
+    a.Xr = c->fx_r;
+    a.Xi = c->fx_i;
+    a.cp = c->fcp;
+    a.z = c->fzv;
+    const int rw = c->plan.rw;
+    const int groups = (a.sh.no + rw - 1) / rw + (a.sh.ne + rw - 1) / rw;
+    for (int q = 0; q < groups; ++q) wr.push_back(bwork(c, k, q, groups, 0));
+    const int mg = (c->plan.nh + 127) / 128;
+    for (int q = 0; q < mg; ++q) wm.push_back(bwork(c, k, q, mg, 0));
+    wo.push_back(bwork(c, k, 0, 1, 0));
+    smem = std::max(smem, dft_smem(c->plan));
+    args.push_back(a);
+  }
+  const DirectArgs* A = B.put(args);
+  const BWork* Wr = B.put(wr);
+  const BWork* Wm = B.put(wm);
+  const BWork* Wo = B.put(wo);
+  TRY(B.launch([&] {
+    return launch_direct_b(A, Wr, (int)wr.size(), Wm, (int)wm.size(), Wo, (int)wo.size(), smem,
+                           gate, B.cs);
+  }));
+  TRY(batch_ctl(B, C_AFTER_INNER, list, gate));
+  return batch_vec<double>(B, V_CORRECT, list, gate, [](polar_ctx* c) {
+    VecArgs<double> a = vargs<double>(c);
+    a.v0 = c->kv64.d;
+    a.w0 = c->X;
+    return a;
+  });
+}
+
+// capture helpers of the batch (its own capture stream)
+int bcap_begin(BatchBuild& B, cudaGraph_t g, const std::vector<cudaGraphNode_t>& deps) {
+  if (B.plan) return POLAR_OK;
+  CUDA_TRY(cudaStreamBeginCaptureToGraph(B.cs, g, deps.empty() ? nullptr : deps.data(), nullptr,
+                                         deps.size(), cudaStreamCaptureModeThreadLocal));
+  return POLAR_OK;
+}
+int bcap_end(BatchBuild& B, std::vector<cudaGraphNode_t>* sinks) {
+  if (B.plan) return POLAR_OK;
+  if (sinks) {
+    cudaStreamCaptureStatus status;
+    const cudaGraphNode_t* deps = nullptr;
+    size_t nd = 0;
+    CUDA_TRY(cudaStreamGetCaptureInfo(B.cs, &status, nullptr, nullptr, &deps, nullptr, &nd));
+    sinks->assign(deps, deps + nd);
+  }
+  cudaGraph_t out = nullptr;
+  CUDA_TRY(cudaStreamEndCapture(B.cs, &out));
+  return POLAR_OK;
+}
+int bcond(BatchBuild& B, cudaGraph_t g, CondHandle* h) {
+  *h = 0;
+  if (B.plan) return POLAR_OK;
+  cudaGraphConditionalHandle c;
+  CUDA_TRY(cudaGraphConditionalHandleCreate(&c, g, 0, 0));
+  *h = (CondHandle)c;
+  return POLAR_OK;
+}
+int bwhile(BatchBuild& B, cudaGraph_t g, const std::vector<cudaGraphNode_t>& deps, CondHandle h,
+           cudaGraphNode_t* node, cudaGraph_t* body) {
+  if (B.plan) {
+    *node = nullptr;
+    *body = nullptr;
+    return POLAR_OK;
+  }
+  return add_cond(g, deps, (cudaGraphConditionalHandle)h, cudaGraphCondTypeWhile, node, body);
+}
+
+// One inner Krylov solve of the instances of `list` in precision T (gate: the branch),
+// appended to graph g after `deps`: set-up, WHILE (any iterating) { iteration }, counts and
+// correction of X.  *sinks receives the last node.
+template <typename T>
+int batch_inner(BatchBuild& B, cudaGraph_t g, std::vector<cudaGraphNode_t> deps,
+                const std::vector<const BInst*>& list, int gate, bool fp64_refresh,
+                std::vector<cudaGraphNode_t>* sinks, int64_t* per_iter) {
+  CondHandle hit = 0;
+  TRY(bcond(B, g, &hit));
+  TRY(bcap_begin(B, g, deps));
+  if (fp64_refresh) {  // mixed instances entering their FP64 solve: FP64 factors on demand
+    std::vector<const BInst*> mixed;
+    for (const BInst* i : list)
+      if (i->mixed) mixed.push_back(i);
+    TRY(batch_refresh<double>(B, mixed, true, gate));
+  }
+  TRY(batch_vec<T>(B, V_SCALE_CAST, list, gate, [](polar_ctx* c) {
+    VecArgs<T> a = vargs<T>(c);
+    a.v0 = kvecs<T>(c).r;
+    a.w0 = c->r64;
+    return a;
+  }));
+  TRY(batch_vec<T>(B, V_BICG_INIT, list, gate, [](polar_ctx* c) {
+    KVecs<T>& k = kvecs<T>(c);
+    VecArgs<T> a = vargs<T>(c);
+    a.v0 = k.r;
+    a.v1 = k.rhat;
+    a.v2 = k.p;
+    a.v3 = k.v;
+    a.v4 = k.d;
+    return a;
+  }));
+  TRY(batch_any(B, list, gate, 1, hit));
+  std::vector<cudaGraphNode_t> s1;
+  TRY(bcap_end(B, &s1));
+  cudaGraphNode_t nit;
+  cudaGraph_t bit;
+  TRY(bwhile(B, g, s1, hit, &nit, &bit));
+  const int64_t a0 = B.launches;
+  TRY(bcap_begin(B, bit, {}));
+  TRY(batch_iteration<T>(B, list, gate));
+  TRY(batch_any(B, list, gate, 1, hit));
+  TRY(bcap_end(B, nullptr));
+  *per_iter = B.launches - a0;
+  TRY(bcap_begin(B, g, std::vector<cudaGraphNode_t>{nit}));
+  TRY(batch_ctl(B, C_AFTER_INNER, list, gate));
+  TRY(batch_vec<T>(B, V_CORRECT, list, gate, [](polar_ctx* c) {
+    VecArgs<T> a = vargs<T>(c);
+    a.v0 = kvecs<T>(c).d;
+    a.w0 = c->X;
+    return a;
+  }));
+  TRY(bcap_end(B, sinks));
+  return POLAR_OK;
+}
+
+// The FP64 residual of the instances of `list` (r64 = e - S X with its max-norm reductions).
+int batch_resid(BatchBuild& B, const std::vector<const BInst*>& list, int gate) {
+  return batch_stencil<double>(B, M_RESID64, list, gate, [](polar_ctx* c) {
+    return st_args<double>(c, c->X, c->r64, nullptr, c->e);
+  });
+}
+
+// One theta-step of every instance of the batch as one graph:
+//   schedule step -> right-hand sides, refreshes, X = U, residuals, decisions ->
+//   WHILE (any refining) { FP32 solves | FP64 solves | direct solves, residuals,
+//                          decisions } -> commit, results, next step.
+int batch_step_graph(BatchBuild& B, cudaGraph_t g, const std::vector<BInst>& inst) {
+  std::vector<const BInst*> all, krylov32, krylov64, direct, f64, f32;
+  for (const BInst& i : inst) {
+    all.push_back(&i);
+    if (i.direct) {
+      direct.push_back(&i);
+    } else {
+      krylov64.push_back(&i);           // FP64 instances and the mixed ones' FP64 solve
+      if (i.mixed) krylov32.push_back(&i);
+    }
+    (i.mixed ? f32 : f64).push_back(&i);
+  }
+  polar_batch* b = B.b;
+  CondHandle hre = 0;
+  TRY(bcond(B, g, &hre));
+  const int64_t l0 = B.launches;
+  TRY(bcap_begin(B, g, {}));
+  TRY(batch_ctl(B, C_SCHED_BEGIN, all, G_ALL));
+  for (int TK = 32; TK <= 256; TK <<= 1) {
+    std::vector<const BInst*> sub;
+    std::vector<RhsArgs> args;
+    for (const BInst* i : all) {
+      polar_ctx* c = i->c;
+      if (make_tiling(c->sh0()).TK != TK) continue;
+      RhsArgs a{};
+      a.L = c->v64[0];
+      a.sp = c->sp;
+      a.u = c->U;
+      a.e = c->e;
+      a.nsrc = c->nsrc;
+      for (int q = 0; q < c->nsrc; ++q) {
+        a.vsrc[q] = c->vsrc[q];
+        a.bnd[q] = c->bnd[q];
+      }
+      a.red = c->red();
+      a.t = make_tiling(c->sh0());
+      args.push_back(a);
+      sub.push_back(i);
+    }
+    if (sub.empty()) continue;
+    const std::vector<BWork> w = grid_work(sub, [](const polar_ctx* c) { return stencil_grid(c->sh0()); });
+    const RhsArgs* A = B.put(args);
+    const BWork* W = B.put(w);
+    TRY(B.launch([&] { return launch_rhs_b(A, W, (int)w.size(), TK, G_STEP, B.cs); }));
+  }
+  TRY(batch_refresh<double>(B, f64, false, G_STEP));
+  TRY(batch_refresh<float>(B, f32, false, G_STEP));
+  TRY(batch_vec<double>(B, V_COPY, all, G_STEP, [](polar_ctx* c) {
+    VecArgs<double> a = vargs<double>(c);
+    a.w0 = c->U;
+    a.w1 = c->X;
+    a.flag = 0;
+    return a;
+  }));
+  TRY(batch_resid(B, all, G_STEP));
+  TRY(batch_ctl(B, C_DECIDE, all, G_STEP));
+  TRY(batch_any(B, all, G_REFINE, 0, hre));
+  std::vector<cudaGraphNode_t> sinks;
+  TRY(bcap_end(B, &sinks));
+  const int64_t l1 = B.launches;
+  cudaGraphNode_t nre;
+  cudaGraph_t bre;
+  TRY(bwhile(B, g, sinks, hre, &nre, &bre));
+  std::vector<cudaGraphNode_t> tail;
+  int64_t it32 = 0, it64 = 0;
+  if (!krylov32.empty()) TRY(batch_inner<float>(B, bre, tail, krylov32, G_32, false, &tail, &it32));
+  if (!krylov64.empty())
+    TRY(batch_inner<double>(B, bre, tail, krylov64, G_64, !krylov32.empty(), &tail, &it64));
+  TRY(bcap_begin(B, bre, tail));
+  TRY(batch_direct(B, direct, G_64));
+  TRY(batch_resid(B, all, G_REFINE));
+  TRY(batch_ctl(B, C_DECIDE, all, G_REFINE));
+  TRY(batch_any(B, all, G_REFINE, 0, hre));
+  TRY(bcap_end(B, nullptr));
+  const int64_t l2 = B.launches;
+  TRY(bcap_begin(B, g, std::vector<cudaGraphNode_t>{nre}));
+  TRY(batch_vec<double>(B, V_COPY, all, G_STEP, [](polar_ctx* c) {
+    VecArgs<double> a = vargs<double>(c);
+    a.w0 = c->X;
+    a.w1 = c->U;
+    a.flag = 1;  // commit only a converged step
+    return a;
+  }));
+  TRY(batch_ctl(B, C_SCHED_END, all, G_STEP));
+  TRY(batch_ctl(B, C_SCHED_NEXT, all, G_ALL));
+  TRY(bcap_end(B, nullptr));
+  const int64_t l3 = B.launches;
+  b->kernels_fixed = (l1 - l0) + (l3 - l2);
+  b->kernels_sweep = (l2 - l1) - it32 - it64;
+  b->kernels_iter32 = it32;
+  b->kernels_iter64 = it64;
+  return POLAR_OK;
+}
+
+// (Re)builds the batch's step graph: plan pass, arena upload, capture pass.
+int build_batch_graph(polar_batch* b) {
+  CUDA_TRY(cudaStreamSynchronize(b->st));  // no launch of the old graph still reads the arena
+  if (b->ex) cudaGraphExecDestroy(b->ex);
+  if (b->g) cudaGraphDestroy(b->g);
+  b->ex = nullptr;
+  b->g = nullptr;
+  if (!b->cap) CUDA_TRY(cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking));
+  std::vector<BInst> inst;
+  for (int i = 0; i < (int)b->ctx.size(); ++i) {
+    polar_ctx* c = b->ctx[i];
+    inst.push_back(BInst{c, i, c->precision == POLAR_MIXED && !c->direct_now, c->direct_now});
+  }
+  BatchBuild plan;
+  plan.b = b;
+  plan.plan = true;
+  TRY(batch_step_graph(plan, nullptr, inst));
+  polar_ctx* c0 = b->ctx[0];
+  if (plan.off > b->arena_bytes) {
+    if (b->arena) {
+      if (c0->free_fn) c0->free_fn(b->arena, c0->st, c0->alloc_user);
+      else cudaFree(b->arena);
+    }
+    b->arena = nullptr;
+    b->arena_bytes = 0;
+    void* q = nullptr;
+    if (c0->alloc) {
+      q = c0->alloc(plan.off, c0->st, c0->alloc_user);
+      if (!q) return fail(POLAR_ENOMEM, "the caller's allocator returned NULL (batch tables)");
+    } else {
+      CUDA_TRY(cudaMalloc(&q, plan.off));
+    }
+    b->arena = q;
+    b->arena_bytes = plan.off;
+  }
+  CUDA_TRY(cudaMemcpy(b->arena, plan.image.data(), plan.off, cudaMemcpyHostToDevice));
+  BatchBuild cap;
+  cap.b = b;
+  cap.plan = false;
+  cap.dev = static_cast<unsigned char*>(b->arena);
+  cap.cs = b->cap;
+  CUDA_TRY(cudaGraphCreate(&b->g, 0));
+  const int rc = batch_step_graph(cap, b->g, inst);
+  if (rc != POLAR_OK) {
+    cudaGraph_t junk = nullptr;
+    cudaStreamCaptureStatus status;
+    if (cudaStreamIsCapturing(b->cap, &status) == cudaSuccess &&
+        status != cudaStreamCaptureStatusNone)
+      cudaStreamEndCapture(b->cap, &junk);
+    if (junk) cudaGraphDestroy(junk);
+    (void)cudaGetLastError();
+    return rc;
+  }
+  if (cap.off != plan.off) return fail(POLAR_ECUDA, "batch plan and capture disagree");
+  CUDA_TRY(cudaGraphInstantiate(&b->ex, b->g, 0));
+  b->gens.resize(b->ctx.size());
+  for (size_t i = 0; i < b->ctx.size(); ++i) b->gens[i] = b->ctx[i]->generation;
   return POLAR_OK;
 }
 
@@ -1668,9 +2435,17 @@ int polar_batch_destroy(polar_batch* b) {
   cudaStreamSynchronize(b->st);
   if (b->ex) cudaGraphExecDestroy(b->ex);
   if (b->g) cudaGraphDestroy(b->g);
+  if (b->arena) {
+    polar_ctx* c0 = b->ctx[0];
+    if (c0->free_fn) c0->free_fn(b->arena, c0->st, c0->alloc_user);
+    else cudaFree(b->arena);
+  }
+  if (b->cap) cudaStreamDestroy(b->cap);
   delete b;
   return POLAR_OK;
 }
+
+int64_t polar_batch_kernel_launches(const polar_batch* b) { return b ? b->launches : 0; }
 
 int polar_batch_advance(polar_batch* b, int32_t nsteps, const double* const* t, const double* theta,
                         const double* const* w, const polar_solver_opts* opts,
@@ -1696,33 +2471,31 @@ int polar_batch_advance(polar_batch* b, int32_t nsteps, const double* const* t, 
   }
   bool stale = !b->ex || (int)b->gens.size() != count;
   for (int i = 0; !stale && i < count; ++i) stale = b->gens[i] != b->ctx[i]->generation;
-  if (stale) {
-    if (b->ex) cudaGraphExecDestroy(b->ex);
-    if (b->g) cudaGraphDestroy(b->g);
-    b->ex = nullptr;
-    b->g = nullptr;
-    CUDA_TRY(cudaGraphCreate(&b->g, 0));
-    for (int i = 0; i < count; ++i) {
-      polar_ctx* c = b->ctx[i];
-      const int rc = (c->precision == POLAR_FP64) ? append_step<double>(c, b->g)
-                                                  : append_step<float>(c, b->g);
-      if (rc != POLAR_OK) {
-        abandon_capture(c);
-        return rc;
-      }
-    }
-    CUDA_TRY(cudaGraphInstantiate(&b->ex, b->g, 0));
-    b->gens.resize(count);
-    for (int i = 0; i < count; ++i) b->gens[i] = b->ctx[i]->generation;
-  }
-  // one graph launch advances every instance by one step; instances run as independent
-  // branches of the graph
+  if (stale) TRY(build_batch_graph(b));
+  // one graph launch advances every instance by one step: each kernel class runs once per
+  // phase over all instances
   for (int k = 0; k < nsteps; ++k) CUDA_TRY(cudaGraphLaunch(b->ex, b->st));
   CUDA_TRY(cudaStreamSynchronize(b->st));
   int rc = POLAR_OK;
   for (int i = 0; i < count; ++i) {
-    const int r = finish_schedule(b->ctx[i], nsteps, t[i], stats ? stats + (size_t)i * nsteps : nullptr);
+    const int r = finish_schedule(b->ctx[i], nsteps, t[i], stats ? stats + (size_t)i * nsteps : nullptr,
+                                  false);
     if (rc == POLAR_OK && r != POLAR_OK) rc = r;
+  }
+  // kernels launched: per step the fixed ones, then every loop runs as long as its slowest
+  // instance
+  for (int k = 0; k < nsteps; ++k) {
+    int sweeps = 0, it32 = 0, it64 = 0;
+    for (polar_ctx* c : b->ctx) {
+      const StepOut& r = c->out_host[k];
+      if (r.status == POLAR_ESTATE) continue;
+      sweeps = std::max(sweeps, r.sweeps - 1);
+      const int i64 = c->precision == POLAR_MIXED ? r.iters64 : r.iters;
+      it64 = std::max(it64, i64);
+      it32 = std::max(it32, r.iters - i64);
+    }
+    b->launches += b->kernels_fixed + (int64_t)sweeps * b->kernels_sweep +
+                   (int64_t)it32 * b->kernels_iter32 + (int64_t)it64 * b->kernels_iter64;
   }
   return rc;
 }

@@ -127,10 +127,10 @@ __device__ void dft_rings(double* re, double* im, int rw, const FftPlan& P) {
 struct RingGroup {
   int parity, k0, count;
 };
-__device__ __forceinline__ RingGroup ring_group(const Shape& sh, int rw) {
+__device__ __forceinline__ RingGroup ring_group(const Shape& sh, int rw, int vb) {
   const int godd = (sh.no + rw - 1) / rw;
   RingGroup g;
-  int b = blockIdx.x;
+  int b = vb;
   g.parity = b < godd ? 1 : 0;
   if (!g.parity) b -= godd;
   g.k0 = b * rw;
@@ -141,15 +141,13 @@ __device__ __forceinline__ RingGroup ring_group(const Shape& sh, int rw) {
 
 // forward: x (split layout) -> X_ip, p < nh;  inverse: X -> x
 template <bool INVERSE>
-__global__ void __launch_bounds__(kFftThreads) k_dft_rings(Shape sh, FftPlan P, const double* x,
-                                                           double* Xr, double* Xi, double* y,
-                                                           const int* done) {
-  if (done && *done) return;
+__device__ __forceinline__ void dft_rings_body(const Shape& sh, const FftPlan& P, const double* x,
+                                               double* Xr, double* Xi, double* y, int vb) {
   extern __shared__ double smem[];
   const int rw = P.rw, M = P.M, n = P.n, nh = P.nh, nt = blockDim.x;
   double* re = smem;
   double* im = smem + (size_t)rw * M;
-  const RingGroup g = ring_group(sh, rw);
+  const RingGroup g = ring_group(sh, rw, vb);
   const size_t base = g.parity ? sh.odd0 : sh.even0;
   const int ld = g.parity ? sh.ldo : sh.lde;
   auto ring_of = [&](int r) { return g.parity ? 2 * (g.k0 + r) + 1 : 2 * (g.k0 + r) + 2; };
@@ -201,17 +199,23 @@ __global__ void __launch_bounds__(kFftThreads) k_dft_rings(Shape sh, FftPlan P, 
   }
 }
 
+template <bool INVERSE>
+__global__ void __launch_bounds__(kFftThreads) k_dft_rings(Shape sh, FftPlan P, const double* x,
+                                                           double* Xr, double* Xi, double* y) {
+  dft_rings_body<INVERSE>(sh, P, x, Xr, Xi, y, blockIdx.x);
+}
+
 // One thread per Fourier mode p < nh: Thomas along r of
 //   (diag_i + 2 beta s_i cos(2 pi p / n)) X_i + beta w_i X_{i-1} + beta e_i X_{i+1} = B_i
 // for the real and imaginary parts (the same real matrix).  Mode 0 carries the origin:
 // ring 1 sees n beta w_1 x_0 (x_0 at every angle), the origin row reads
 // diag0 x_0 + beta o X_{1,0} = b_0; with y = T^{-1} B and z = T^{-1} (n beta w_1 e_1),
 // x_0 = (b_0 - beta o y_1) / (diag0 - beta o z_1) and X = y - z x_0.
-__global__ void __launch_bounds__(128) k_modes(SepRings R, FftPlan P, Params par, const double* b,
-                                               double* x, double* Xr, double* Xi, double* cp,
-                                               double* z, KrylovScalars* ks) {
+__device__ __forceinline__ void modes_body(const SepRings& R, const FftPlan& P, Params par,
+                                           const double* b, double* x, double* Xr, double* Xi,
+                                           double* cp, double* z, KrylovScalars* ks, int vb) {
   if (ks->done) return;
-  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  const int p = vb * blockDim.x + threadIdx.x;
   const int m = R.m, nh = P.nh;
   if (p >= nh) return;
   const double alpha = par[0], beta = par[1];
@@ -262,12 +266,49 @@ __global__ void __launch_bounds__(128) k_modes(SepRings R, FftPlan P, Params par
   }
 }
 
+__global__ void __launch_bounds__(128) k_modes(SepRings R, FftPlan P, Params par, const double* b,
+                                               double* x, double* Xr, double* Xi, double* cp,
+                                               double* z, KrylovScalars* ks) {
+  modes_body(R, P, par, b, x, Xr, Xi, cp, z, ks, blockIdx.x);
+}
+
 __global__ void k_pre_direct(KrylovScalars* ks) {
   ks->iters = 0;
   ks->done = 0;
 }
 
-size_t dft_smem(const FftPlan& P) { return (size_t)P.rw * P.M * 2 * sizeof(double); }
+// batched forms (per-instance DirectArgs; gate and work list as the other batched kernels)
+__global__ void k_pre_direct_b(const BWork* W, int nwork, int gate) {
+  for (int it = blockIdx.x * blockDim.x + threadIdx.x; it < nwork; it += gridDim.x * blockDim.x) {
+    const BWork w = W[it];
+    if (!gate_pass(gate, w.ks, w.sp)) continue;
+    w.ks->iters = 0;
+    w.ks->done = 0;
+  }
+}
+template <bool INVERSE>
+__global__ void __launch_bounds__(kFftThreads) k_dft_rings_b(const DirectArgs* A, const BWork* W,
+                                                             int nwork, int gate) {
+  for (int it = blockIdx.x; it < nwork; it += gridDim.x) {
+    const BWork w = W[it];
+    if (!gate_pass(gate, w.ks, w.sp)) continue;
+    const DirectArgs& a = A[w.inst];
+    const Shape sh = a.sh;
+    const FftPlan P = a.P;
+    dft_rings_body<INVERSE>(sh, P, a.b, a.Xr, a.Xi, a.x, w.vb);
+    __syncthreads();  // the transform's shared memory is reused by the next item
+  }
+}
+__global__ void __launch_bounds__(128) k_modes_b(const DirectArgs* A, const BWork* W, int nwork,
+                                                 int gate) {
+  for (int it = blockIdx.x; it < nwork; it += gridDim.x) {
+    const BWork w = W[it];
+    if (!gate_pass(gate, w.ks, w.sp)) continue;
+    const DirectArgs& a = A[w.inst];
+    modes_body(a.R, a.P, a.par, a.b, a.x, a.Xr, a.Xi, a.cp, a.z, w.ks, w.vb);
+  }
+}
+
 
 // Transform of the chirp filter b (b_k = conj c_k for |k| < n, circularly), once per mesh.
 __global__ void __launch_bounds__(kFftThreads) k_chirp_filter(FftPlan P, double* bhr, double* bhi) {
@@ -291,6 +332,8 @@ __global__ void __launch_bounds__(kFftThreads) k_chirp_filter(FftPlan P, double*
 }
 
 }  // namespace
+
+size_t dft_smem(const FftPlan& P) { return (size_t)P.rw * P.M * 2 * sizeof(double); }
 
 bool fft_plan_sizes(int n, int* M, int* logM, int* rw) {
   int m2 = 1, lg = 0;
@@ -362,9 +405,29 @@ int launch_direct_solve(const Shape& sh, const FftPlan& P, const SepRings& R, Pa
   }
   const int groups = (sh.no + P.rw - 1) / P.rw + (sh.ne + P.rw - 1) / P.rw;
   k_pre_direct<<<1, 1, 0, st>>>(ks);
-  k_dft_rings<false><<<groups, kFftThreads, smem, st>>>(sh, P, b, Xr, Xi, nullptr, nullptr);
+  k_dft_rings<false><<<groups, kFftThreads, smem, st>>>(sh, P, b, Xr, Xi, nullptr);
   k_modes<<<(P.nh + 127) / 128, 128, 0, st>>>(R, P, par, b, x, Xr, Xi, cp, z, ks);
-  k_dft_rings<true><<<groups, kFftThreads, smem, st>>>(sh, P, nullptr, Xr, Xi, x, nullptr);
+  k_dft_rings<true><<<groups, kFftThreads, smem, st>>>(sh, P, nullptr, Xr, Xi, x);
+  return 4;
+}
+
+
+int launch_direct_b(const DirectArgs* A, const BWork* Wrings, int nrings, const BWork* Wmodes,
+                    int nmodes, const BWork* Wone, int count, size_t smem, int gate,
+                    cudaStream_t st) {
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_dft_rings_b<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)kFftSmemCap);
+    cudaFuncSetAttribute(k_dft_rings_b<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)kFftSmemCap);
+    attr = true;
+  }
+  k_pre_direct_b<<<(count + 127) / 128, 128, 0, st>>>(Wone, count, gate);
+  const int gr = persistent_grid(nrings, 2), gm = persistent_grid(nmodes, 8);
+  k_dft_rings_b<false><<<gr, kFftThreads, smem, st>>>(A, Wrings, nrings, gate);
+  k_modes_b<<<gm, 128, 0, st>>>(A, Wmodes, nmodes, gate);
+  k_dft_rings_b<true><<<gr, kFftThreads, smem, st>>>(A, Wrings, nrings, gate);
   return 4;
 }
 

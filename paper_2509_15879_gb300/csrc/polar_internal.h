@@ -114,6 +114,8 @@ struct KrylovScalars {
   int inner_done;  // `done` of the last inner solve
   double prev_scaled;
   int iters64;     // Krylov iterations of this step spent in FP64 Krylov solves
+  int step_on;     // batched execution: this instance runs the current step (not halted)
+  int refine_on;   // batched execution: this instance takes the current refinement sweep
   int sticky64;    // mixed path: steps left that start with the FP64 solve (set when a
                    //   step had to switch to it; the FP32 solve is tried again after)
   double sm_best;  // FP32 inner solve: best Jacobi-scaled residual so far and the
@@ -155,6 +157,46 @@ struct StepParams {
 // Conditional-node handle of a CUDA graph (0: not in a graph).
 using CondHandle = unsigned long long;
 
+// ---- batched execution (many instances, one launch per kernel class and phase)
+// A block of a batched launch works as block `vb` of the `vg`-block grid that instance
+// `inst`'s own launch would have used, so every instance computes exactly what it computes
+// alone (same partition of its points, same reduction order).  `aux` carries a launch-
+// specific index (the first line of a ring-solve block).  The gate says which instances a
+// launch serves at this point of the step; the others' blocks return at once.
+struct BWork {
+  int inst, vb, vg, aux;
+  KrylovScalars* ks;
+  const StepParams* sp;
+};
+enum {
+  G_ALL = 0,     // every instance
+  G_STEP = 1,    // instances running this step (not halted by an earlier failure)
+  G_REFINE = 2,  // instances in the current refinement sweep
+  G_32 = 3,      // ... whose sweep takes the FP32 inner solve (mixed path)
+  G_64 = 4       // ... whose sweep takes an FP64 inner solve (FP64 path, mixed fallback)
+};
+// Step data of one instance for the batched control kernels (one thread per instance).
+struct CtlArgs {
+  const StepParams* sched;  // the instance's schedule
+  const int* kstep;         // its step counter
+  int* kstep_w;
+  StepParams* sp;           // its current step's parameters
+  StepOut* out;             // its per-step results
+  KrylovScalars* ks;
+  int tolerant;             // after an inner solve: a non-finite FP32 solve does not fail
+  int pad;
+};
+
+__device__ __forceinline__ bool gate_pass(int g, const KrylovScalars* ks, const StepParams* sp) {
+  switch (g) {
+    case G_STEP: return ks->step_on != 0;
+    case G_REFINE: return ks->refine_on != 0;
+    case G_32: return ks->refine_on && !ks->use64;
+    case G_64: return ks->refine_on && (ks->use64 || !sp->mixed);
+    default: return true;
+  }
+}
+
 struct Reduce {
   double* part;        // partial sums, kMaxBlocks * 4
   KrylovScalars* ks;   // device scalars
@@ -165,6 +207,151 @@ constexpr int kMaxBlocks = 2048;
 using Params = const double*;
 
 int grid_for(size_t work, int threads);
+
+
+// ----------------------------------------------------------------- kernel arguments
+// (lone launches pass them by value; batched launches read one per instance from device
+// memory)
+// ------------------------------------------------------------------ point loops
+// Tiles of TK consecutive rings of one parity block x TJ consecutive angles; every
+// warp reads TK consecutive entries of a radial line (coalesced).
+struct Tiling {
+  int TK, TJ;
+  int tko, tke, tj;  // tiles along k (odd, even) and along j
+  int ntiles;
+};
+
+__host__ __device__ inline Tiling make_tiling(const Shape& sh) {
+  Tiling t;
+  const int kmax = sh.no > sh.ne ? sh.no : sh.ne;
+  t.TK = 32;
+  while (t.TK < kmax && t.TK < 256) t.TK <<= 1;
+  t.TJ = 256 / t.TK;
+  t.tko = (sh.no + t.TK - 1) / t.TK;
+  t.tke = (sh.ne + t.TK - 1) / t.TK;
+  t.tj = (sh.n + t.TJ - 1) / t.TJ;
+  t.ntiles = (t.tko + t.tke) * t.tj;
+  return t;
+}
+
+enum { M_APPLY = 0, M_RESID64 = 1, M_DOTV = 2, M_DOTT = 3 };
+
+template <typename T>
+struct StArgs {
+  LevelView<T> L;
+  Params par;
+  const T* x;
+  const T* b;   // M_RESID64: right-hand side
+  T* y;
+  const T* d1;  // M_DOTV: rhat; M_DOTT: s
+  Reduce red;
+  Tiling t;
+};
+
+struct RhsArgs {
+  LevelView<double> L;
+  const StepParams* sp;
+  const double* u;
+  double* e;
+  int nsrc;
+  const double* vsrc[4];
+  const double* bnd[4];
+  Reduce red;
+  Tiling t;
+};
+
+// Arguments of the vector kernels of the Krylov solves (one struct for all of them; each
+// kernel reads the fields its comment names).  Lone launches pass it by value, batched
+// launches hold one per instance in device memory.
+template <typename T>
+struct VecArgs {
+  size_t nv;
+  T* v0;
+  T* v1;
+  T* v2;
+  T* v3;
+  T* v4;
+  T* v5;
+  T* v6;
+  T* v7;
+  const T* diag;
+  const double* sc;
+  const StepParams* sp;
+  Reduce red;
+  CondHandle cond;
+  double* w0;  // FP64 vectors of the refinement kernels
+  double* w1;
+  int flag;
+};
+
+struct RefreshLevel {
+  Shape sh;
+  const double* vol;
+  const double* rs;
+  const double* w;
+  const double* e;
+  const double* s;
+  const double* nn;
+  const double* o;
+  double* sc;
+  void* diag;
+  double* diag64;  // FP64 copy of diag when T is float (level 0 only), else null
+  double* dinv;    // level 0: 1 / diag in FP64 (both precisions), else null
+  void* rsum;      // row sums alpha vol + beta rs when T is float (level 0 only), else null
+  void* fl;
+  void* fui;
+  void* fcu;
+  void* fq;
+  void* fring;
+  void* fz;
+  double* ws;  // 2 nv doubles: forward values y and pivot reciprocals (FP64)
+  int ring0;   // first CTA of this level in the refresh grid
+};
+constexpr int kMaxLevels = 20;
+struct RefreshArgs {
+  RefreshLevel lv[kMaxLevels];
+  int nlev;
+  const StepParams* sp;
+  const double* stamp;  // null: refresh when sp->do_refresh; else refresh unless stamp
+                        // holds this step's (alpha, beta) (factors already current)
+};
+
+constexpr int RF = 4;     // rings per CTA
+constexpr int TF = 128;   // threads per ring
+
+template <typename T>
+struct RingArgs {
+  LevelView<T> L;   // level being smoothed
+  LevelView<T> C;   // next coarser level (RING_POST, even rings)
+  const T* b;       // right-hand side of this level
+  T* x;             // solution of this level (updated in place)
+  const T* X;       // solution of the coarser level (RING_POST)
+  Params par;
+  const int* done;
+  int parity;       // 1: odd rings, 0: even rings (+ origin)
+  int mode;
+};
+
+template <typename T>
+struct RestrictArgs {
+  LevelView<T> L;
+  LevelView<T> C;
+  const T* x;
+  T* B;
+  Params par;
+  const int* done;
+};
+
+template <typename T>
+struct CoarsestArgs {
+  LevelView<T> L;
+  const T* b;
+  T* x;
+  Params par;
+  const int* done;
+  const StepParams* sp;  // refresh form (k_schur): the step's parameters
+  const double* stamp;
+};
 
 // ----------------------------------------------------------------- launchers
 // All launchers enqueue on `st` and return the number of kernels launched.
@@ -224,6 +411,49 @@ int launch_restrict(const LevelView<T>& L, const LevelView<T>& C, const T* x, T*
 template <typename T>
 int launch_coarsest(const LevelView<T>& L, const T* b, T* x, Params p, const int* done,
                     cudaStream_t st);
+
+
+// ----------------------------------------------------------------- batched launchers
+// grid of a persistent batched launch: per_sm blocks per SM, at most nwork
+int persistent_grid(int nwork, int per_sm);
+// Each launches nwork blocks; block b works as W[b] says (instance, virtual block) and
+// returns at once unless its instance passes `gate`.  Per-instance arguments in A.
+template <typename T>
+int launch_stencil_b(int mode, const StArgs<T>* A, const BWork* W, int nwork, int TK, int gate,
+                     cudaStream_t st);
+int launch_rhs_b(const RhsArgs* A, const BWork* W, int nwork, int TK, int gate, cudaStream_t st);
+enum { V_BICG_INIT, V_BICG_S, V_BICG_UPDATE, V_BICG_P, V_CG_RHO, V_CG_P, V_CG_UPDATE,
+       V_SCALE_CAST, V_CORRECT, V_COPY };
+template <typename T>
+int launch_vec_b(int kind, const VecArgs<T>* A, const BWork* W, int nwork, int gate,
+                 cudaStream_t st);
+enum { C_SCHED_BEGIN, C_DECIDE, C_AFTER_INNER, C_SCHED_END, C_SCHED_NEXT };
+int launch_ctl_b(int kind, const CtlArgs* A, int count, int gate, cudaStream_t st);
+// sets `cond` to whether any of the `count` instances passes `gate` (and, with
+// need_running, still iterates: done == 0)
+int launch_any_b(const CtlArgs* A, int count, int gate, int need_running, CondHandle cond,
+                 cudaStream_t st);
+template <typename T>
+int launch_refresh_b(const RefreshArgs* A, const BWork* W, int nwork, int gate, cudaStream_t st);
+template <typename T>
+int launch_ring_b(const RingShape& s, const RingArgs<T>* A, const BWork* W, int nwork, int gate,
+                  cudaStream_t st);
+template <typename T>
+int launch_restrict_b(const RestrictArgs<T>* A, const BWork* W, int nwork, int gate,
+                      cudaStream_t st);
+// coarsest-level solve (schur = 0) or its per-step Schur data (schur = 1), one CTA per
+// instance of the (P, TW) shape coarsest_shape gives for its n
+template <typename T>
+int launch_coarsest_b(int P, int TW, int schur, const CoarsestArgs<T>* A, const BWork* W,
+                      int nwork, int gate, cudaStream_t st);
+template <typename T>
+void coarsest_shape(int n, int* P, int* TW);
+int launch_stamp_b(const BWork* W, double* const* stamps, int nwork, int gate, cudaStream_t st);
+// refresh arguments of one context's levels (as launch_refresh builds them); *nblocks:
+// the refresh grid of that context
+template <typename T>
+RefreshArgs make_refresh_args(const LevelView<double>* L64, LevelView<T>* LT, int nlev,
+                              const StepParams* sp, double* ws, double* stamp, int* nblocks);
 
 // ---- BiCGStab vector kernels
 template <typename T>

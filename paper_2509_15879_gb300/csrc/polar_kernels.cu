@@ -10,6 +10,7 @@
 // scalar recurrences of the Krylov solver on the device.
 #include "polar_internal.h"
 
+#include <algorithm>
 #include <cmath>
 
 namespace polar {
@@ -61,16 +62,16 @@ __device__ void block_reduce(double (&v)[K]) {
 // Publishes this block's partials (thread 0 holds them) and reports whether this
 // block is the last one of the grid to arrive.
 template <int K>
-__device__ bool publish_and_arrive(const double (&v)[K], double* part, unsigned int* counter) {
+__device__ bool publish_and_arrive(const double (&v)[K], double* part, unsigned int* counter,
+                                   int bid, int nb) {
   __shared__ unsigned int s_last;
   const int tid = threadIdx.x + blockDim.x * threadIdx.y;
-  const int bid = blockIdx.x + gridDim.x * blockIdx.y;
   if (tid == 0) {
 #pragma unroll
     for (int k = 0; k < K; ++k) part[k * kMaxBlocks + bid] = v[k];
     __threadfence();
     unsigned int prev = atomicAdd(counter, 1u);
-    s_last = (prev == gridDim.x * gridDim.y - 1) ? 1u : 0u;
+    s_last = (prev == (unsigned int)nb - 1) ? 1u : 0u;
   }
   __syncthreads();
   if (s_last) __threadfence();
@@ -79,8 +80,7 @@ __device__ bool publish_and_arrive(const double (&v)[K], double* part, unsigned 
 
 // Called by every thread of the last block: totals in block order (result in thread 0).
 template <int K, int KMAX>
-__device__ void grid_totals(const double* part, double (&tot)[K]) {
-  const int nb = gridDim.x * gridDim.y;
+__device__ void grid_totals(const double* part, double (&tot)[K], int nb) {
   const int nt = blockDim.x * blockDim.y;
   const int tid = threadIdx.x + blockDim.x * threadIdx.y;
 #pragma unroll
@@ -109,35 +109,13 @@ __device__ __forceinline__ double bits_to_double(unsigned long long u) {
   return __longlong_as_double(static_cast<long long>(u));
 }
 
-// ------------------------------------------------------------------ point loops
-// Tiles of TK consecutive rings of one parity block x TJ consecutive angles; every
-// warp reads TK consecutive entries of a radial line (coalesced).
-struct Tiling {
-  int TK, TJ;
-  int tko, tke, tj;  // tiles along k (odd, even) and along j
-  int ntiles;
-};
-
-__host__ __device__ inline Tiling make_tiling(const Shape& sh) {
-  Tiling t;
-  const int kmax = sh.no > sh.ne ? sh.no : sh.ne;
-  t.TK = 32;
-  while (t.TK < kmax && t.TK < 256) t.TK <<= 1;
-  t.TJ = 256 / t.TK;
-  t.tko = (sh.no + t.TK - 1) / t.TK;
-  t.tke = (sh.ne + t.TK - 1) / t.TK;
-  t.tj = (sh.n + t.TJ - 1) / t.TJ;
-  t.ntiles = (t.tko + t.tke) * t.tj;
-  return t;
-}
-
 // Calls f(i, j, idx, west, east, south, north) for every point of this thread; west and
 // east are indices of the radial neighbours (west = 0 is the origin for ring 1, east =
 // SIZE_MAX marks the Dirichlet ring), south/north the periodic angular neighbours.
 template <typename F>
-__device__ __forceinline__ void for_points(const Shape& sh, const Tiling& t, F f) {
+__device__ __forceinline__ void for_points(const Shape& sh, const Tiling& t, int vb, int vg, F f) {
   const int n = sh.n, m = sh.m;
-  for (int tile = blockIdx.x; tile < t.ntiles; tile += gridDim.x) {
+  for (int tile = vb; tile < t.ntiles; tile += vg) {
     const int tj = tile % t.tj;
     const int tk = tile / t.tj;
     const bool odd = tk < t.tko;
@@ -165,20 +143,6 @@ __device__ __forceinline__ void for_points(const Shape& sh, const Tiling& t, F f
 }
 
 // ------------------------------------------------------------------ stencil
-enum { M_APPLY = 0, M_RESID64 = 1, M_DOTV = 2, M_DOTT = 3 };
-
-template <typename T>
-struct StArgs {
-  LevelView<T> L;
-  Params par;
-  const T* x;
-  const T* b;   // M_RESID64: right-hand side
-  T* y;
-  const T* d1;  // M_DOTV: rhat; M_DOTT: s
-  Reduce red;
-  Tiling t;
-};
-
 template <int MODE>
 struct Slots {
   static constexpr int K = (MODE == M_RESID64) ? 4 : (MODE == M_DOTV) ? 2 : (MODE == M_DOTT) ? 3 : 1;
@@ -192,7 +156,7 @@ struct Slots {
 // solves) and in FP64 across threads and blocks; the residual's maxima are kept as
 // integer maxima of bit patterns, its Jacobi scaling multiplies by 1 / diag.
 template <typename T, int MODE>
-__global__ void __launch_bounds__(256) k_stencil(StArgs<T> a) {
+__device__ __forceinline__ void stencil_body(const StArgs<T>& a, int vb, int vg) {
   if (MODE >= M_DOTV && a.red.ks->done) return;
   constexpr int K = Slots<MODE>::K, KMAX = Slots<MODE>::KMAX;
   const T beta = (T)a.par[1];
@@ -204,8 +168,8 @@ __global__ void __launch_bounds__(256) k_stencil(StArgs<T> a) {
   unsigned long long rbits = 0, sbits = 0, xbits = 0;
   const T* __restrict__ x = a.x;
   const T x0 = x[0];
-  for_points(L.sh, a.t, [&](int i, int j, size_t idx, size_t west, size_t east, size_t south,
-                            size_t north) {
+  for_points(L.sh, a.t, vb, vg, [&](int i, int j, size_t idx, size_t west, size_t east,
+                                    size_t south, size_t north) {
     const T xc = x[idx];
     const T xw = (west == 0) ? x0 : x[west];
     const T xe = (east == (size_t)-1) ? T(0) : x[east];
@@ -257,11 +221,11 @@ __global__ void __launch_bounds__(256) k_stencil(StArgs<T> a) {
     acc[2] = (double)dot2;
   }
   block_reduce<K, KMAX>(acc);
-  if (!publish_and_arrive<K>(acc, a.red.part, &a.red.ks->counter)) return;
+  if (!publish_and_arrive<K>(acc, a.red.part, &a.red.ks->counter, vb, vg)) return;
 
   // ---- last block: origin row and the scalar epilogue
   double tot[K];
-  grid_totals<K, KMAX>(a.red.part, tot);
+  grid_totals<K, KMAX>(a.red.part, tot, vg);
   const int tid = threadIdx.x + blockDim.x * threadIdx.y;
   if (tid != 0) return;
   KrylovScalars* ks = a.red.ks;
@@ -295,6 +259,23 @@ __global__ void __launch_bounds__(256) k_stencil(StArgs<T> a) {
     ks->omega = (tt > 0.0) ? ts / tt : 0.0;
   }
   ks->counter = 0;
+}
+
+template <typename T, int MODE>
+__global__ void __launch_bounds__(256) k_stencil(StArgs<T> a) {
+  stencil_body<T, MODE>(a, blockIdx.x, gridDim.x);
+}
+// Batched kernels are persistent: a grid sized to fill the GPU walks the work list, and
+// items of instances the gate masks cost one load (late in a Krylov loop most are masked).
+template <typename T, int MODE>
+__global__ void __launch_bounds__(256) k_stencil_b(const StArgs<T>* A, const BWork* W, int nwork,
+                                                   int gate) {
+  for (int it = blockIdx.x; it < nwork; it += gridDim.x) {
+    const BWork w = W[it];
+    if (!gate_pass(gate, w.ks, w.sp)) continue;
+    const StArgs<T> a = A[w.inst];
+    stencil_body<T, MODE>(a, w.vb, w.vg);
+  }
 }
 
 template <typename T, int MODE>
@@ -343,22 +324,11 @@ int launch_resid64(const LevelView<double>& L, Params p, const double* x, const 
 }
 
 // ------------------------------------------------------------------ right-hand side
-struct RhsArgs {
-  LevelView<double> L;
-  const StepParams* sp;
-  const double* u;
-  double* e;
-  int nsrc;
-  const double* vsrc[4];
-  const double* bnd[4];
-  Reduce red;
-  Tiling t;
-};
 
 // e = alpha V u - (1 - theta) (V L) u + sum_q cf_q V src_q + e_{m,j} g_j, the explicit
 // half of Eq. (2.5) with the sources of both levels and the Dirichlet data of both
 // levels (g_j = sum_q cg_q bnd_q[j], Eq. 2.9) moved to the right-hand side.
-__global__ void __launch_bounds__(256) k_rhs(RhsArgs a) {
+__device__ __forceinline__ void rhs_body(const RhsArgs& a, int vb, int vg) {
   const LevelView<double>& L = a.L;
   const double alpha = a.sp->alpha, omt = a.sp->omt;
   double cf[4], cg[4];
@@ -369,8 +339,8 @@ __global__ void __launch_bounds__(256) k_rhs(RhsArgs a) {
   double acc[1] = {0.0};
   const double* __restrict__ u = a.u;
   const double u0 = u[0];
-  for_points(L.sh, a.t, [&](int i, int j, size_t idx, size_t west, size_t east, size_t south,
-                            size_t north) {
+  for_points(L.sh, a.t, vb, vg, [&](int i, int j, size_t idx, size_t west, size_t east,
+                                    size_t south, size_t north) {
     const double uc = u[idx];
     const double uw = (west == 0) ? u0 : u[west];
     const double ue = (east == (size_t)-1) ? 0.0 : u[east];
@@ -392,9 +362,9 @@ __global__ void __launch_bounds__(256) k_rhs(RhsArgs a) {
     a.e[idx] = val;
   });
   block_reduce<1, 1>(acc);
-  if (!publish_and_arrive<1>(acc, a.red.part, &a.red.ks->counter)) return;
+  if (!publish_and_arrive<1>(acc, a.red.part, &a.red.ks->counter, vb, vg)) return;
   double tot[1];
-  grid_totals<1, 1>(a.red.part, tot);
+  grid_totals<1, 1>(a.red.part, tot, vg);
   if (threadIdx.x + blockDim.x * threadIdx.y != 0) return;
   const double vol0 = L.sc[3], rs0 = L.sc[4], osum = L.sc[2];
   const double Lu0 = fma(rs0 - osum, u0, tot[0]);
@@ -402,6 +372,17 @@ __global__ void __launch_bounds__(256) k_rhs(RhsArgs a) {
   for (int q = 0; q < a.nsrc; ++q) e0 = fma(cf[q], a.vsrc[q][0], e0);
   a.e[0] = e0;
   a.red.ks->counter = 0;
+}
+
+__global__ void __launch_bounds__(256) k_rhs(RhsArgs a) { rhs_body(a, blockIdx.x, gridDim.x); }
+__global__ void __launch_bounds__(256) k_rhs_b(const RhsArgs* A, const BWork* W, int nwork,
+                                               int gate) {
+  for (int it = blockIdx.x; it < nwork; it += gridDim.x) {
+    const BWork w = W[it];
+    if (!gate_pass(gate, w.ks, w.sp)) continue;
+    const RhsArgs a = A[w.inst];
+    rhs_body(a, w.vb, w.vg);
+  }
 }
 
 int launch_rhs(const LevelView<double>& L, const StepParams* sp, const double* u, int nsrc,
@@ -431,15 +412,37 @@ __device__ __forceinline__ void set_cond(CondHandle cond, bool value) {
   if (cond) cudaGraphSetConditional((cudaGraphConditionalHandle)cond, value ? 1u : 0u);
 }
 
+
+// Batched wrapper of a vector-kernel body: block w.vb of instance w.inst's own grid.
+#define POLAR_VEC_BATCHED(NAME, BODY)                                                   \
+  template <typename T>                                                                \
+  __global__ void __launch_bounds__(kVT) NAME(const VecArgs<T>* A, const BWork* W,     \
+                                              int nwork, int gate) {                   \
+    for (int it = blockIdx.x; it < nwork; it += gridDim.x) {                           \
+      const BWork w = W[it];                                                           \
+      if (!gate_pass(gate, w.ks, w.sp)) continue;                                      \
+      const VecArgs<T> a = A[w.inst];                                                  \
+      BODY<T>(a, w.vb, w.vg);                                                          \
+    }                                                                                  \
+  }                                                                                    \
+  template <typename T>                                                                \
+  __global__ void __launch_bounds__(kVT) NAME##_lone(VecArgs<T> a) {                   \
+    BODY<T>(a, blockIdx.x, gridDim.x);                                                 \
+  }
+
+// init: r = v0 -> rhat v1, p v2, v v3 = 0, x v4 = 0; the solve's scalars and threshold
 template <typename T>
-__global__ void __launch_bounds__(kVT) k_bicg_init(size_t nv, const T* r, T* rhat, T* p, T* v,
-                                                   T* x, const StepParams* sp, CondHandle cond,
-                                                   Reduce red) {
+__device__ __forceinline__ void bicg_init_body(const VecArgs<T>& a, int vb, int vg) {
+  const StepParams* sp = a.sp;
+  const Reduce red = a.red;
+  const size_t nv = a.nv;
+  const T* r = a.v0;
+  T *rhat = a.v1, *p = a.v2, *v = a.v3, *x = a.v4;
   const double rel_tol = sp->inner_tol;
   const int max_iter = sp->max_iter;
   double acc[1];
   T s = T(0);  // per thread in T, across threads in FP64
-  for (size_t k = blockIdx.x * (size_t)kVT + threadIdx.x; k < nv; k += (size_t)gridDim.x * kVT) {
+  for (size_t k = vb * (size_t)kVT + threadIdx.x; k < nv; k += (size_t)vg * kVT) {
     const T rv = r[k];
     rhat[k] = rv;
     p[k] = rv;
@@ -449,9 +452,9 @@ __global__ void __launch_bounds__(kVT) k_bicg_init(size_t nv, const T* r, T* rha
   }
   acc[0] = (double)s;
   block_reduce<1, 1>(acc);
-  if (!publish_and_arrive<1>(acc, red.part, &red.ks->counter)) return;
+  if (!publish_and_arrive<1>(acc, red.part, &red.ks->counter, vb, vg)) return;
   double tot[1];
-  grid_totals<1, 1>(red.part, tot);
+  grid_totals<1, 1>(red.part, tot, vg);
   if (threadIdx.x != 0) return;
   KrylovScalars* ks = red.ks;
   ks->rr0 = tot[0];
@@ -475,17 +478,22 @@ __global__ void __launch_bounds__(kVT) k_bicg_init(size_t nv, const T* r, T* rha
   ks->max_iter = max_iter;
   ks->done = !isfinite(tot[0]) ? 3 : (tot[0] == 0.0 ? 1 : 0);
   ks->counter = 0;
-  set_cond(cond, ks->done == 0);
+  set_cond(a.cond, ks->done == 0);
 }
+POLAR_VEC_BATCHED(k_bicg_init, bicg_init_body)
 
+// s v2 = r v0 - alpha v v1
 template <typename T>
-__global__ void __launch_bounds__(kVT) k_bicg_s(size_t nv, const T* r, const T* v, T* s,
-                                                KrylovScalars* ks) {
+__device__ __forceinline__ void bicg_s_body(const VecArgs<T>& a, int vb, int vg) {
+  const KrylovScalars* ks = a.red.ks;
   if (ks->done) return;
   const T alpha = (T)ks->alpha;
-  for (size_t k = blockIdx.x * (size_t)kVT + threadIdx.x; k < nv; k += (size_t)gridDim.x * kVT)
+  const T *r = a.v0, *v = a.v1;
+  T* s = a.v2;
+  for (size_t k = vb * (size_t)kVT + threadIdx.x; k < a.nv; k += (size_t)vg * kVT)
     s[k] = fma(-alpha, v[k], r[k]);
 }
+POLAR_VEC_BATCHED(k_bicg_s, bicg_s_body)
 
 // |r| / d in FP32 (a stopping test needs no more), in FP64 when d is outside the FP32
 // range; padding entries have d = 0
@@ -510,17 +518,21 @@ __device__ __forceinline__ bool fp32_stalled(KrylovScalars* ks, double sm) {
   return ks->iters - ks->sm_best_it >= kStallIters;
 }
 
+// x v0 += alpha phat v1 + omega shat v2;  r v3 = s v4 - omega t v5;  rho = rhat v6 . r,
+// rr = r . r and the stopping test on max |r_i| / diag_i
 template <typename T>
-__global__ void __launch_bounds__(kVT) k_bicg_update(size_t nv, T* x, const T* phat,
-                                                     const T* shat, T* r, const T* s,
-                                                     const T* t, const T* rhat, const T* diag,
-                                                     const double* sc, Reduce red) {
+__device__ __forceinline__ void bicg_update_body(const VecArgs<T>& a, int vb, int vg) {
+  const Reduce red = a.red;
   if (red.ks->done) return;
   const T alpha = (T)red.ks->alpha, omega = (T)red.ks->omega;
-  const T d0 = (T)sc[0];  // the origin's diagonal lives in the level scalars
+  const T d0 = (T)a.sc[0];  // the origin's diagonal lives in the level scalars
+  T* x = a.v0;
+  const T *phat = a.v1, *shat = a.v2;
+  T* r = a.v3;
+  const T *s = a.v4, *t = a.v5, *rhat = a.v6, *diag = a.diag;
   T s1 = T(0), s2 = T(0);  // per thread in T, across threads in FP64
   float sm = 0.f;
-  for (size_t k = blockIdx.x * (size_t)kVT + threadIdx.x; k < nv; k += (size_t)gridDim.x * kVT) {
+  for (size_t k = vb * (size_t)kVT + threadIdx.x; k < a.nv; k += (size_t)vg * kVT) {
     x[k] = fma(omega, shat[k], fma(alpha, phat[k], x[k]));
     const T rn = fma(-omega, t[k], s[k]);
     r[k] = rn;
@@ -530,9 +542,9 @@ __global__ void __launch_bounds__(kVT) k_bicg_update(size_t nv, T* x, const T* p
   }
   double acc[3] = {(double)s1, (double)s2, isfinite(sm) ? (double)sm : INFINITY};
   block_reduce<3, 2>(acc);
-  if (!publish_and_arrive<3>(acc, red.part, &red.ks->counter)) return;
+  if (!publish_and_arrive<3>(acc, red.part, &red.ks->counter, vb, vg)) return;
   double tot[3];
-  grid_totals<3, 2>(red.part, tot);
+  grid_totals<3, 2>(red.part, tot, vg);
   if (threadIdx.x != 0) return;
   KrylovScalars* ks = red.ks;
   const double rho_new = tot[0], rr = tot[1];
@@ -553,41 +565,80 @@ __global__ void __launch_bounds__(kVT) k_bicg_update(size_t nv, T* x, const T* p
   }
   ks->counter = 0;
 }
+POLAR_VEC_BATCHED(k_bicg_update, bicg_update_body)
 
+// p v0 = r v1 + beta (p - omega v v2); "keep iterating" to the graph's WHILE node
 template <typename T>
-__global__ void __launch_bounds__(kVT) k_bicg_p(size_t nv, T* p, const T* r, const T* v,
-                                                KrylovScalars* ks, CondHandle cond) {
+__device__ __forceinline__ void bicg_p_body(const VecArgs<T>& a, int vb, int vg) {
+  const KrylovScalars* ks = a.red.ks;
   const bool running = ks->done == 0;
-  if (blockIdx.x == 0 && threadIdx.x == 0) set_cond(cond, running);
+  if (vb == 0 && threadIdx.x == 0) set_cond(a.cond, running);
   if (!running) return;
   const T beta = (T)ks->beta, omega = (T)ks->omega;
-  for (size_t k = blockIdx.x * (size_t)kVT + threadIdx.x; k < nv; k += (size_t)gridDim.x * kVT)
+  T* p = a.v0;
+  const T *r = a.v1, *v = a.v2;
+  for (size_t k = vb * (size_t)kVT + threadIdx.x; k < a.nv; k += (size_t)vg * kVT)
     p[k] = fma(beta, fma(-omega, v[k], p[k]), r[k]);
+}
+POLAR_VEC_BATCHED(k_bicg_p, bicg_p_body)
+
+template <typename T>
+VecArgs<T> vec_args(size_t nv, Reduce red) {
+  VecArgs<T> a{};
+  a.nv = nv;
+  a.red = red;
+  return a;
 }
 
 template <typename T>
 int launch_bicg_init(size_t nv, const T* r, T* rhat, T* p, T* v, T* x, const StepParams* sp,
                      CondHandle cond, cudaStream_t st, Reduce red) {
-  k_bicg_init<T><<<grid_for(nv, kVT), kVT, 0, st>>>(nv, r, rhat, p, v, x, sp, cond, red);
+  VecArgs<T> a = vec_args<T>(nv, red);
+  a.v0 = const_cast<T*>(r);
+  a.v1 = rhat;
+  a.v2 = p;
+  a.v3 = v;
+  a.v4 = x;
+  a.sp = sp;
+  a.cond = cond;
+  k_bicg_init_lone<T><<<grid_for(nv, kVT), kVT, 0, st>>>(a);
   return 1;
 }
 template <typename T>
 int launch_bicg_s(size_t nv, const T* r, const T* v, T* s, cudaStream_t st, Reduce red) {
-  k_bicg_s<T><<<grid_for(nv, kVT), kVT, 0, st>>>(nv, r, v, s, red.ks);
+  VecArgs<T> a = vec_args<T>(nv, red);
+  a.v0 = const_cast<T*>(r);
+  a.v1 = const_cast<T*>(v);
+  a.v2 = s;
+  k_bicg_s_lone<T><<<grid_for(nv, kVT), kVT, 0, st>>>(a);
   return 1;
 }
 template <typename T>
 int launch_bicg_update(size_t nv, T* x, const T* phat, const T* shat, T* r, const T* s,
                        const T* t, const T* rhat, const T* diag, const double* sc,
                        cudaStream_t st, Reduce red) {
-  k_bicg_update<T><<<grid_for(nv, kVT), kVT, 0, st>>>(nv, x, phat, shat, r, s, t, rhat, diag,
-                                                       sc, red);
+  VecArgs<T> a = vec_args<T>(nv, red);
+  a.v0 = x;
+  a.v1 = const_cast<T*>(phat);
+  a.v2 = const_cast<T*>(shat);
+  a.v3 = r;
+  a.v4 = const_cast<T*>(s);
+  a.v5 = const_cast<T*>(t);
+  a.v6 = const_cast<T*>(rhat);
+  a.diag = diag;
+  a.sc = sc;
+  k_bicg_update_lone<T><<<grid_for(nv, kVT), kVT, 0, st>>>(a);
   return 1;
 }
 template <typename T>
 int launch_bicg_p(size_t nv, T* p, const T* r, const T* v, CondHandle cond, cudaStream_t st,
                   Reduce red) {
-  k_bicg_p<T><<<grid_for(nv, kVT), kVT, 0, st>>>(nv, p, r, v, red.ks, cond);
+  VecArgs<T> a = vec_args<T>(nv, red);
+  a.v0 = p;
+  a.v1 = const_cast<T*>(r);
+  a.v2 = const_cast<T*>(v);
+  a.cond = cond;
+  k_bicg_p_lone<T><<<grid_for(nv, kVT), kVT, 0, st>>>(a);
   return 1;
 }
 
@@ -599,17 +650,21 @@ int launch_bicg_p(size_t nv, T* p, const T* r, const T* v, CondHandle cond, cuda
 // alpha = rho / p.q (the stencil's DOTV mode with d1 = p), then x += alpha p,
 // r -= alpha q and the stopping test (k_cg_update).  Set-up is k_bicg_init (x = 0, the
 // stopping threshold; its p = r is scaled by beta = 0 in the first iteration).
+
+// rho = r v0 . z v1
 template <typename T>
-__global__ void __launch_bounds__(kVT) k_cg_rho(size_t nv, const T* r, const T* z, Reduce red) {
+__device__ __forceinline__ void cg_rho_body(const VecArgs<T>& a, int vb, int vg) {
+  const Reduce red = a.red;
   if (red.ks->done) return;
+  const T *r = a.v0, *z = a.v1;
   T s = T(0);  // per thread in T, across threads in FP64
-  for (size_t k = blockIdx.x * (size_t)kVT + threadIdx.x; k < nv; k += (size_t)gridDim.x * kVT)
+  for (size_t k = vb * (size_t)kVT + threadIdx.x; k < a.nv; k += (size_t)vg * kVT)
     s = fma(r[k], z[k], s);
   double acc[1] = {(double)s};
   block_reduce<1, 1>(acc);
-  if (!publish_and_arrive<1>(acc, red.part, &red.ks->counter)) return;
+  if (!publish_and_arrive<1>(acc, red.part, &red.ks->counter, vb, vg)) return;
   double tot[1];
-  grid_totals<1, 1>(red.part, tot);
+  grid_totals<1, 1>(red.part, tot, vg);
   if (threadIdx.x != 0) return;
   KrylovScalars* ks = red.ks;
   const double rho = tot[0];
@@ -623,27 +678,37 @@ __global__ void __launch_bounds__(kVT) k_cg_rho(size_t nv, const T* r, const T* 
   }
   ks->counter = 0;
 }
+POLAR_VEC_BATCHED(k_cg_rho, cg_rho_body)
 
+// p v0 = z v1 + beta p
 template <typename T>
-__global__ void __launch_bounds__(kVT) k_cg_p(size_t nv, T* p, const T* z, const KrylovScalars* ks) {
+__device__ __forceinline__ void cg_p_body(const VecArgs<T>& a, int vb, int vg) {
+  const KrylovScalars* ks = a.red.ks;
   if (ks->done) return;
   const T beta = (T)ks->beta;
-  for (size_t k = blockIdx.x * (size_t)kVT + threadIdx.x; k < nv; k += (size_t)gridDim.x * kVT)
+  T* p = a.v0;
+  const T* z = a.v1;
+  for (size_t k = vb * (size_t)kVT + threadIdx.x; k < a.nv; k += (size_t)vg * kVT)
     p[k] = fma(beta, p[k], z[k]);
 }
+POLAR_VEC_BATCHED(k_cg_p, cg_p_body)
 
+// x v0 += alpha p v1;  r v2 -= alpha q v3;  stopping test on max |r_i| / diag_i
 template <typename T>
-__global__ void __launch_bounds__(kVT) k_cg_update(size_t nv, T* x, const T* p, T* r, const T* q,
-                                                   const T* diag, const double* sc, Reduce red,
-                                                   CondHandle cond) {
+__device__ __forceinline__ void cg_update_body(const VecArgs<T>& a, int vb, int vg) {
+  const Reduce red = a.red;
   if (red.ks->done) {
-    if (blockIdx.x == 0 && threadIdx.x == 0) set_cond(cond, false);
+    if (vb == 0 && threadIdx.x == 0) set_cond(a.cond, false);
     return;
   }
   const T alpha = (T)red.ks->alpha;
-  const T d0 = (T)sc[0];
+  const T d0 = (T)a.sc[0];
+  T* x = a.v0;
+  const T* p = a.v1;
+  T* r = a.v2;
+  const T *q = a.v3, *diag = a.diag;
   float sm = 0.f;
-  for (size_t k = blockIdx.x * (size_t)kVT + threadIdx.x; k < nv; k += (size_t)gridDim.x * kVT) {
+  for (size_t k = vb * (size_t)kVT + threadIdx.x; k < a.nv; k += (size_t)vg * kVT) {
     x[k] = fma(alpha, p[k], x[k]);
     const T rn = fma(-alpha, q[k], r[k]);
     r[k] = rn;
@@ -651,9 +716,9 @@ __global__ void __launch_bounds__(kVT) k_cg_update(size_t nv, T* x, const T* p, 
   }
   double acc[1] = {isfinite(sm) ? (double)sm : INFINITY};
   block_reduce<1, 0>(acc);
-  if (!publish_and_arrive<1>(acc, red.part, &red.ks->counter)) return;
+  if (!publish_and_arrive<1>(acc, red.part, &red.ks->counter, vb, vg)) return;
   double tot[1];
-  grid_totals<1, 0>(red.part, tot);
+  grid_totals<1, 0>(red.part, tot, vg);
   if (threadIdx.x != 0) return;
   KrylovScalars* ks = red.ks;
   ks->sm = tot[0];
@@ -666,23 +731,38 @@ __global__ void __launch_bounds__(kVT) k_cg_update(size_t nv, T* x, const T* p, 
     ks->done = 4;
   }
   ks->counter = 0;
-  set_cond(cond, ks->done == 0);
+  set_cond(a.cond, ks->done == 0);
 }
+POLAR_VEC_BATCHED(k_cg_update, cg_update_body)
 
 template <typename T>
 int launch_cg_rho(size_t nv, const T* r, const T* z, cudaStream_t st, Reduce red) {
-  k_cg_rho<T><<<grid_for(nv, kVT), kVT, 0, st>>>(nv, r, z, red);
+  VecArgs<T> a = vec_args<T>(nv, red);
+  a.v0 = const_cast<T*>(r);
+  a.v1 = const_cast<T*>(z);
+  k_cg_rho_lone<T><<<grid_for(nv, kVT), kVT, 0, st>>>(a);
   return 1;
 }
 template <typename T>
 int launch_cg_p(size_t nv, T* p, const T* z, cudaStream_t st, Reduce red) {
-  k_cg_p<T><<<grid_for(nv, kVT), kVT, 0, st>>>(nv, p, z, red.ks);
+  VecArgs<T> a = vec_args<T>(nv, red);
+  a.v0 = p;
+  a.v1 = const_cast<T*>(z);
+  k_cg_p_lone<T><<<grid_for(nv, kVT), kVT, 0, st>>>(a);
   return 1;
 }
 template <typename T>
 int launch_cg_update(size_t nv, T* x, const T* p, T* r, const T* q, const T* diag,
                      const double* sc, CondHandle cond, cudaStream_t st, Reduce red) {
-  k_cg_update<T><<<grid_for(nv, kVT), kVT, 0, st>>>(nv, x, p, r, q, diag, sc, red, cond);
+  VecArgs<T> a = vec_args<T>(nv, red);
+  a.v0 = x;
+  a.v1 = const_cast<T*>(p);
+  a.v2 = r;
+  a.v3 = const_cast<T*>(q);
+  a.diag = diag;
+  a.sc = sc;
+  a.cond = cond;
+  k_cg_update_lone<T><<<grid_for(nv, kVT), kVT, 0, st>>>(a);
   return 1;
 }
 
@@ -695,6 +775,7 @@ __device__ __forceinline__ void start_step(const StepParams& p, KrylovScalars* k
 }
 
 __global__ void k_step_begin(const StepParams* sp, KrylovScalars* ks) {
+  ks->step_on = 1;
   ks->failed = 0;
   start_step(*sp, ks);
   ks->inner_done = 0;
@@ -712,14 +793,18 @@ int launch_step_begin(const StepParams* sp, cudaStream_t st, Reduce red) {
   return 1;
 }
 
-__global__ void k_sched_begin(const StepParams* sched, const int* kstep, StepParams* sp,
-                              StepOut* out, CondHandle cond, KrylovScalars* ks) {
+__device__ __forceinline__ void sched_begin_body(const StepParams* sched, const int* kstep,
+                                                 StepParams* sp, StepOut* out, CondHandle cond,
+                                                 KrylovScalars* ks) {
   const int k = *kstep;
   if (ks->halt) {
     out[k] = StepOut{0, 0, -7, 0, 0.0};  // POLAR_ESTATE: not run
+    ks->step_on = 0;
+    ks->refine_on = 0;
     set_cond(cond, false);
     return;
   }
+  ks->step_on = 1;
   *sp = sched[k];
   ks->failed = 0;
   start_step(sched[k], ks);
@@ -733,6 +818,10 @@ __global__ void k_sched_begin(const StepParams* sched, const int* kstep, StepPar
   ks->done = 0;
   ks->counter = 0;
   set_cond(cond, true);
+}
+__global__ void k_sched_begin(const StepParams* sched, const int* kstep, StepParams* sp,
+                              StepOut* out, CondHandle cond, KrylovScalars* ks) {
+  sched_begin_body(sched, kstep, sp, out, cond, ks);
 }
 int launch_sched_begin(const StepParams* sched, const int* kstep, StepParams* sp, StepOut* out,
                        CondHandle cond, cudaStream_t st, Reduce red) {
@@ -758,7 +847,8 @@ int launch_sched_next(int* kstep, cudaStream_t st) {
 // After the FP64 residual (rmax, smax, xmax): the step has converged when the
 // Jacobi-scaled residual is within the tolerance; it fails after max_refine corrections
 // or on a non-finite residual.
-__global__ void k_refine_decide(const StepParams* sp, CondHandle cond, KrylovScalars* ks) {
+__device__ __forceinline__ void refine_decide_body(const StepParams* sp, CondHandle cond,
+                                                   KrylovScalars* ks) {
   bool more = false;
   if (ks->failed == 0) {
     ks->sweeps += 1;
@@ -782,7 +872,11 @@ __global__ void k_refine_decide(const StepParams* sp, CondHandle cond, KrylovSca
     }
     ks->prev_scaled = scaled;
   }
+  ks->refine_on = more ? 1 : 0;
   set_cond(cond, more);
+}
+__global__ void k_refine_decide(const StepParams* sp, CondHandle cond, KrylovScalars* ks) {
+  refine_decide_body(sp, cond, ks);
 }
 
 // Selects the inner solve of the next refinement sweep (mixed path).
@@ -878,6 +972,81 @@ int launch_check_finite(size_t n, const double* a, cudaStream_t st, Reduce red) 
   return 1;
 }
 
+// ------------------------------------------------------------------ batched step control
+// One block (one thread) per instance; CtlArgs[i] holds instance i's step data.
+__global__ void k_sched_begin_b(const CtlArgs* A) {
+  const CtlArgs a = A[blockIdx.x];
+  sched_begin_body(a.sched, a.kstep, a.sp, a.out, 0, a.ks);
+}
+__global__ void k_refine_decide_b(const CtlArgs* A, int gate) {
+  const CtlArgs a = A[blockIdx.x];
+  if (!gate_pass(gate, a.ks, a.sp)) return;
+  refine_decide_body(a.sp, 0, a.ks);
+}
+__global__ void k_after_inner_b(const CtlArgs* A, int gate) {
+  const CtlArgs a = A[blockIdx.x];
+  if (!gate_pass(gate, a.ks, a.sp)) return;
+  KrylovScalars* ks = a.ks;
+  ks->iters_total += ks->iters;
+  if (ks->use64) ks->iters64 += ks->iters;
+  ks->inner_done = ks->done;
+  if (ks->done == 3 && gate != G_32 && ks->failed == 0) ks->failed = -5;  // POLAR_ENONFINITE
+}
+__global__ void k_sched_end_b(const CtlArgs* A, int gate) {
+  const CtlArgs a = A[blockIdx.x];
+  if (!gate_pass(gate, a.ks, a.sp)) return;
+  KrylovScalars* ks = a.ks;
+  a.out[*a.kstep] = StepOut{ks->iters_total, ks->sweeps, ks->failed, ks->iters64, ks->scaled};
+  if (ks->failed) ks->halt = 1;
+}
+__global__ void k_sched_next_b(const CtlArgs* A) { *A[blockIdx.x].kstep_w += 1; }
+// iteration loop of a gate's instances: "continue" while any of them is still iterating
+// (refinement loop: while any is still refining)
+__global__ void k_any_b(const CtlArgs* A, int count, int gate, int need_running,
+                        CondHandle cond) {
+  __shared__ int any;
+  if (threadIdx.x == 0) any = 0;
+  __syncthreads();
+  for (int i = threadIdx.x; i < count; i += blockDim.x) {
+    const CtlArgs& a = A[i];
+    if (gate_pass(gate, a.ks, a.sp) && (!need_running || a.ks->done == 0)) any = 1;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) set_cond(cond, any != 0);
+}
+
+// vector helpers: w0 -> w1 copies (flag: only when the step converged), the scaled cast
+// w0 -> v0 and the FP64 correction w0 += rmax v0
+__device__ __forceinline__ void copy_if_body(const VecArgs<double>& a, int vb, int vg) {
+  const KrylovScalars* ks = a.red.ks;
+  if (ks->failed) return;
+  if (a.flag && !ks->converged) return;
+  for (size_t k = vb * (size_t)kVT + threadIdx.x; k < a.nv; k += (size_t)vg * kVT)
+    a.w1[k] = a.w0[k];
+}
+template <typename T>
+__device__ __forceinline__ void copy_if_body_t(const VecArgs<T>& a, int vb, int vg) {
+  copy_if_body(a, vb, vg);
+}
+template <typename T>
+__device__ __forceinline__ void scale_cast_body(const VecArgs<T>& a, int vb, int vg) {
+  const KrylovScalars* ks = a.red.ks;
+  const double inv = ks->rmax > 0.0 ? 1.0 / ks->rmax : 0.0;
+  for (size_t k = vb * (size_t)kVT + threadIdx.x; k < a.nv; k += (size_t)vg * kVT)
+    a.v0[k] = (T)(a.w0[k] * inv);
+}
+template <typename T>
+__device__ __forceinline__ void correct_body(const VecArgs<T>& a, int vb, int vg) {
+  const KrylovScalars* ks = a.red.ks;
+  if (ks->failed || ks->inner_done == 3) return;  // no non-finite correction reaches x
+  const double s = ks->rmax;
+  for (size_t k = vb * (size_t)kVT + threadIdx.x; k < a.nv; k += (size_t)vg * kVT)
+    a.w0[k] = fma(s, (double)a.v0[k], a.w0[k]);
+}
+POLAR_VEC_BATCHED(k_copy_b, copy_if_body_t)
+POLAR_VEC_BATCHED(k_scale_cast_b, scale_cast_body)
+POLAR_VEC_BATCHED(k_correct_b, correct_body)
+
 // ------------------------------------------------------------------ layout conversion
 // interface index q = 1 + j m + (i - 1) <-> split index sh.at(i, j); q = 0 is the origin
 __global__ void k_pack(Shape sh, const double* in, const double* scale, double* out) {
@@ -917,6 +1086,85 @@ int launch_unpack(const Shape& sh, const double* in, const double* div, double* 
   return 1;
 }
 
+
+// ------------------------------------------------------------------ batched launchers
+// Blocks of a persistent batched launch: per_sm blocks on each of the GPU's SMs, at most one
+// per work item.
+int persistent_grid(int nwork, int per_sm) {
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0)
+      sms = 152;
+  }
+  return std::max(1, std::min(nwork, sms * per_sm));
+}
+template <typename T>
+int launch_stencil_b(int mode, const StArgs<T>* A, const BWork* W, int nwork, int TK, int gate,
+                     cudaStream_t st) {
+  if (nwork <= 0) return 0;
+  const dim3 block(TK, 256 / TK);
+  const int g = persistent_grid(nwork, 8);
+  switch (mode) {
+    case M_APPLY: k_stencil_b<T, M_APPLY><<<g, block, 0, st>>>(A, W, nwork, gate); break;
+    case M_DOTV: k_stencil_b<T, M_DOTV><<<g, block, 0, st>>>(A, W, nwork, gate); break;
+    case M_DOTT: k_stencil_b<T, M_DOTT><<<g, block, 0, st>>>(A, W, nwork, gate); break;
+    default:
+      if constexpr (sizeof(T) == 8) {
+        k_stencil_b<T, M_RESID64><<<g, block, 0, st>>>(A, W, nwork, gate);
+      } else {
+        return -1;
+      }
+  }
+  return 1;
+}
+int launch_rhs_b(const RhsArgs* A, const BWork* W, int nwork, int TK, int gate, cudaStream_t st) {
+  if (nwork <= 0) return 0;
+  k_rhs_b<<<persistent_grid(nwork, 8), dim3(TK, 256 / TK), 0, st>>>(A, W, nwork, gate);
+  return 1;
+}
+template <typename T>
+int launch_vec_b(int kind, const VecArgs<T>* A, const BWork* W, int nwork, int gate,
+                 cudaStream_t st) {
+  if (nwork <= 0) return 0;
+  const int g = persistent_grid(nwork, 8);
+  switch (kind) {
+    case V_BICG_INIT: k_bicg_init<T><<<g, kVT, 0, st>>>(A, W, nwork, gate); break;
+    case V_BICG_S: k_bicg_s<T><<<g, kVT, 0, st>>>(A, W, nwork, gate); break;
+    case V_BICG_UPDATE: k_bicg_update<T><<<g, kVT, 0, st>>>(A, W, nwork, gate); break;
+    case V_BICG_P: k_bicg_p<T><<<g, kVT, 0, st>>>(A, W, nwork, gate); break;
+    case V_CG_RHO: k_cg_rho<T><<<g, kVT, 0, st>>>(A, W, nwork, gate); break;
+    case V_CG_P: k_cg_p<T><<<g, kVT, 0, st>>>(A, W, nwork, gate); break;
+    case V_CG_UPDATE: k_cg_update<T><<<g, kVT, 0, st>>>(A, W, nwork, gate); break;
+    case V_SCALE_CAST: k_scale_cast_b<T><<<g, kVT, 0, st>>>(A, W, nwork, gate); break;
+    case V_CORRECT: k_correct_b<T><<<g, kVT, 0, st>>>(A, W, nwork, gate); break;
+    default:
+      if constexpr (sizeof(T) == 8) {
+        k_copy_b<T><<<g, kVT, 0, st>>>(A, W, nwork, gate);
+      } else {
+        return -1;
+      }
+  }
+  return 1;
+}
+int launch_ctl_b(int kind, const CtlArgs* A, int count, int gate, cudaStream_t st) {
+  if (count <= 0) return 0;
+  switch (kind) {
+    case C_SCHED_BEGIN: k_sched_begin_b<<<count, 1, 0, st>>>(A); break;
+    case C_DECIDE: k_refine_decide_b<<<count, 1, 0, st>>>(A, gate); break;
+    case C_AFTER_INNER: k_after_inner_b<<<count, 1, 0, st>>>(A, gate); break;
+    case C_SCHED_END: k_sched_end_b<<<count, 1, 0, st>>>(A, gate); break;
+    default: k_sched_next_b<<<count, 1, 0, st>>>(A); break;
+  }
+  return 1;
+}
+int launch_any_b(const CtlArgs* A, int count, int gate, int need_running, CondHandle cond,
+                 cudaStream_t st) {
+  k_any_b<<<1, 256, 0, st>>>(A, count, gate, need_running, cond);
+  return 1;
+}
+
 // ------------------------------------------------------------------ instantiations
 #define POLAR_INST(T)                                                                          \
   template int launch_apply<T>(const LevelView<T>&, Params, const T*, T*, cudaStream_t,        \
@@ -935,7 +1183,10 @@ int launch_unpack(const Shape& sh, const double* in, const double* div, double* 
   template int launch_cg_update<T>(size_t, T*, const T*, T*, const T*, const T*, const double*, \
                                    CondHandle, cudaStream_t, Reduce);                          \
   template int launch_scale_cast<T>(size_t, const double*, T*, cudaStream_t, Reduce);          \
-  template int launch_correct<T>(size_t, double*, const T*, cudaStream_t, Reduce);
+  template int launch_correct<T>(size_t, double*, const T*, cudaStream_t, Reduce);          \
+  template int launch_stencil_b<T>(int, const StArgs<T>*, const BWork*, int, int, int,      \
+                                   cudaStream_t);                                           \
+  template int launch_vec_b<T>(int, const VecArgs<T>*, const BWork*, int, int, cudaStream_t);
 
 POLAR_INST(float)
 POLAR_INST(double)

@@ -26,6 +26,8 @@
 // values through distributed shared memory.
 #include <cooperative_groups.h>
 
+#include <algorithm>
+
 #include <vector>
 
 #include "polar_internal.h"
@@ -37,37 +39,6 @@ namespace polar {
 // ---------------------------------------------------------------------------------
 // per-step refresh
 
-struct RefreshLevel {
-  Shape sh;
-  const double* vol;
-  const double* rs;
-  const double* w;
-  const double* e;
-  const double* s;
-  const double* nn;
-  const double* o;
-  double* sc;
-  void* diag;
-  double* diag64;  // FP64 copy of diag when T is float (level 0 only), else null
-  double* dinv;    // level 0: 1 / diag in FP64 (both precisions), else null
-  void* rsum;      // row sums alpha vol + beta rs when T is float (level 0 only), else null
-  void* fl;
-  void* fui;
-  void* fcu;
-  void* fq;
-  void* fring;
-  void* fz;
-  double* ws;  // 2 nv doubles: forward values y and pivot reciprocals (FP64)
-  int ring0;   // first CTA of this level in the refresh grid
-};
-constexpr int kMaxLevels = 20;
-struct RefreshArgs {
-  RefreshLevel lv[kMaxLevels];
-  int nlev;
-  const StepParams* sp;
-  const double* stamp;  // null: refresh when sp->do_refresh; else refresh unless stamp
-                        // holds this step's (alpha, beta) (factors already current)
-};
 
 // Whether a refresh has work: the step's do_refresh flag, or, for factors kept beside the
 // step's own (the mixed path's FP64 factors, formed only when its FP64 solve runs), the
@@ -98,8 +69,6 @@ __device__ __forceinline__ bool refresh_due(const StepParams* sp, const double* 
 //   y = L^{-1} u forward and q = U^{-1} y backward are affine recurrences, scanned the
 //           same way (the backward one with the chunk order reversed).
 // All arithmetic is FP64; only the stored factors take the inner precision T.
-constexpr int RF = 4;     // rings per CTA
-constexpr int TF = 128;   // threads per ring
 
 struct M2 {  // [[a, b], [c, d]]
   double a, b, c, d;
@@ -163,17 +132,17 @@ __device__ V chunk_excl_scan(V v, const V& ident, V* sw) {
 }
 
 template <typename T>
-__global__ void __launch_bounds__(RF * TF) k_refresh(RefreshArgs A) {
+__device__ __forceinline__ void refresh_body(const RefreshArgs& A, int vb) {
   __shared__ M2 sm2[(RF * TF / 32) * RF];
   __shared__ A2 sa2[(RF * TF / 32) * RF];
   __shared__ double qend[2][RF];
   if (!refresh_due(A.sp, A.stamp)) return;
   // which level, parity block and group of RF rings this CTA takes
   int l = 0;
-  while (l + 1 < A.nlev && (int)blockIdx.x >= A.lv[l + 1].ring0) ++l;
+  while (l + 1 < A.nlev && vb >= A.lv[l + 1].ring0) ++l;
   const RefreshLevel& L = A.lv[l];
   const Shape sh = L.sh;
-  int g = blockIdx.x - L.ring0;
+  int g = vb - L.ring0;
   const int godd = (sh.no + RF - 1) / RF;
   const int parity = g < godd ? 1 : 0;
   if (!parity) g -= godd;
@@ -316,6 +285,37 @@ __global__ void __launch_bounds__(RF * TF) k_refresh(RefreshArgs A) {
 }
 
 template <typename T>
+__global__ void __launch_bounds__(RF * TF) k_refresh(RefreshArgs A) {
+  refresh_body<T>(A, blockIdx.x);
+}
+
+// Copies an instance's argument struct into shared memory (once per CTA): the batched
+// launches of the large-argument kernels read their fields from there.
+template <typename A>
+__device__ __forceinline__ void stage_args(A& dst, const A& src) {
+  static_assert(sizeof(A) % sizeof(int) == 0, "argument structs are whole words");
+  const int nt = blockDim.x * blockDim.y;
+  const int tid = threadIdx.x + blockDim.x * threadIdx.y;
+  int* d = reinterpret_cast<int*>(&dst);
+  const int* s = reinterpret_cast<const int*>(&src);
+  for (int k = tid; k < (int)(sizeof(A) / sizeof(int)); k += nt) d[k] = s[k];
+  __syncthreads();
+}
+
+template <typename T>
+__global__ void __launch_bounds__(RF * TF) k_refresh_b(const RefreshArgs* AA, const BWork* W,
+                                                     int nwork, int gate) {
+  __shared__ RefreshArgs sA;
+  for (int it = blockIdx.x; it < nwork; it += gridDim.x) {
+    const BWork w = W[it];
+    if (!gate_pass(gate, w.ks, w.sp)) continue;
+    stage_args(sA, AA[w.inst]);
+    refresh_body<T>(sA, w.vb);
+    __syncthreads();  // sA is restaged for the next item
+  }
+}
+
+template <typename T>
 static int launch_schur(const LevelView<T>& L, const StepParams* sp, const double* stamp,
                         cudaStream_t st);
 
@@ -324,10 +324,19 @@ __global__ void k_stamp(const StepParams* sp, double* stamp) {
   stamp[0] = sp->alpha;
   stamp[1] = sp->beta;
 }
+// batched: one thread per instance (w.inst), stamp array given per instance
+__global__ void k_stamp_b(const BWork* W, double* const* stamps, int nwork, int gate) {
+  for (int it = blockIdx.x * blockDim.x + threadIdx.x; it < nwork; it += gridDim.x * blockDim.x) {
+    const BWork w = W[it];
+    if (!gate_pass(gate, w.ks, w.sp)) continue;
+    stamps[w.inst][0] = w.sp->alpha;
+    stamps[w.inst][1] = w.sp->beta;
+  }
+}
 
 template <typename T>
-int launch_refresh(const LevelView<double>* L64, LevelView<T>* LT, int nlev,
-                   const StepParams* sp, double* ws, cudaStream_t st, double* stamp) {
+RefreshArgs make_refresh_args(const LevelView<double>* L64, LevelView<T>* LT, int nlev,
+                              const StepParams* sp, double* ws, double* stamp, int* nblocks) {
   RefreshArgs A{};
   A.nlev = nlev;
   A.sp = sp;
@@ -361,6 +370,15 @@ int launch_refresh(const LevelView<double>* L64, LevelView<T>* LT, int nlev,
     r.ring0 = rings;  // first CTA of this level (groups of RF rings, odd block first)
     rings += (d.sh.no + RF - 1) / RF + (d.sh.ne + RF - 1) / RF;
   }
+  *nblocks = rings;
+  return A;
+}
+
+template <typename T>
+int launch_refresh(const LevelView<double>* L64, LevelView<T>* LT, int nlev,
+                   const StepParams* sp, double* ws, cudaStream_t st, double* stamp) {
+  int rings = 0;
+  const RefreshArgs A = make_refresh_args<T>(L64, LT, nlev, sp, ws, stamp, &rings);
   k_refresh<T><<<rings, dim3(RF, TF), 0, st>>>(A);
   int k = 1 + launch_schur<T>(LT[nlev - 1], sp, stamp, st);
   if (stamp) {
@@ -378,18 +396,6 @@ constexpr int kSchurSlot = sizeof(T) == 8 ? 6 : 1;
 // ---------------------------------------------------------------------------------
 // ring solves
 
-template <typename T>
-struct RingArgs {
-  LevelView<T> L;   // level being smoothed
-  LevelView<T> C;   // next coarser level (RING_POST, even rings)
-  const T* b;       // right-hand side of this level
-  T* x;             // solution of this level (updated in place)
-  const T* X;       // solution of the coarser level (RING_POST)
-  Params par;
-  const int* done;
-  int parity;       // 1: odd rings, 0: even rings (+ origin)
-  int mode;
-};
 
 // A radial position of a level, addressed along the angle: entry j at base + j * ld.
 struct Line {
@@ -797,19 +803,41 @@ __global__ void __launch_bounds__(512, 2) k_ring_staged(RingArgs<T> a) {
   if (a.parity == 0 && blockIdx.x == 0 && blockIdx.y == 0) relax_origin(a, beta);
 }
 
+// Batched half-sweeps: CTA column blockIdx.x works on the RW lines from w.aux of instance
+// w.inst (w.vb: its line group, 0 relaxes the origin with the even rings).  The gate and
+// the instance's `done` flag are read before the cluster's first barrier; every CTA of a
+// cluster reads the same work item, so a cluster returns as a whole.
+template <typename T, int P, bool STAGED>
+__device__ __forceinline__ void ring_batched(const RingArgs<T>* A, const BWork* W, int nwork,
+                                             int gate) {
+  __shared__ RingArgs<T> sa;
+  for (int it = blockIdx.x; it < nwork; it += gridDim.x) {
+    const BWork w = W[it];
+    if (!gate_pass(gate, w.ks, w.sp)) continue;
+    stage_args(sa, A[w.inst]);
+    if (!(sa.done && *sa.done)) {
+      const T beta = (T)sa.par[1];
+      ring_body<T, P, STAGED>(sa, beta, w.aux);
+      if (sa.parity == 0 && w.vb == 0 && blockIdx.y == 0) relax_origin(sa, beta);
+    }
+    __syncthreads();  // sa is restaged for the next item
+  }
+}
+template <typename T, int P>
+__global__ void __launch_bounds__(512) k_ring_b(const RingArgs<T>* A, const BWork* W, int nwork,
+                                                int gate) {
+  ring_batched<T, P, false>(A, W, nwork, gate);
+}
+template <typename T, int P>
+__global__ void __launch_bounds__(512, 2) k_ring_staged_b(const RingArgs<T>* A, const BWork* W,
+                                                         int nwork, int gate) {
+  ring_batched<T, P, true>(A, W, nwork, gate);
+}
+
 // residual of the odd rings after the pre-smoothing sweep, restricted to the coarser
 // level: B_I = ib_{2I-1} r_{2I-1} + ia_{2I+1} r_{2I+1} and B_0 = sum_j ia_{1,j} r_{1,j}
 // (the even rings and the origin have zero residual after their relaxation; an odd
 // ring's residual is what its even neighbours changed: r_q = -beta (w x_{q-1} + e x_{q+1})).
-template <typename T>
-struct RestrictArgs {
-  LevelView<T> L;
-  LevelView<T> C;
-  const T* x;
-  T* B;
-  Params par;
-  const int* done;
-};
 
 template <typename T>
 __device__ __forceinline__ T odd_resid(const LevelView<T>& L, const T* x, T beta, int q, int j) {
@@ -860,6 +888,20 @@ __global__ void __launch_bounds__(256) k_restrict(RestrictArgs<T> a) {
   restrict_body(a, beta, blockIdx.x * (size_t)blockDim.x + threadIdx.x,
                 (size_t)gridDim.x * blockDim.x, blockIdx.x == 0);
 }
+template <typename T>
+__global__ void __launch_bounds__(256) k_restrict_b(const RestrictArgs<T>* A, const BWork* W,
+                                                    int nwork, int gate) {
+  for (int it = blockIdx.x; it < nwork; it += gridDim.x) {
+    const BWork w = W[it];
+    if (!gate_pass(gate, w.ks, w.sp)) continue;
+    const RestrictArgs<T> a = A[w.inst];
+    if (a.done && *a.done) continue;
+    const T beta = (T)a.par[1];
+    restrict_body(a, beta, w.vb * (size_t)blockDim.x + threadIdx.x, (size_t)w.vg * blockDim.x,
+                  w.vb == 0);
+    __syncthreads();  // the origin part's shared reduction buffer is reused
+  }
+}
 
 // coarsest level (origin + ring 1): y = T_1^{-1} b_1, x_0 = (b_0 - beta o.y) / denom,
 // x_1 = y - z x_0 with z = T_1^{-1} (beta w_1) from the refresh.  One CTA (any RW: only
@@ -903,12 +945,25 @@ __global__ void __launch_bounds__(512) k_coarsest(LevelView<T> L, const T* b, T*
   if (done && *done) return;
   coarsest_body<T, P>(L, b, x, (T)par[1]);
 }
+// batched: one CTA per instance (w.inst), its coarsest level, right-hand side and solution
+template <typename T, int P>
+__global__ void __launch_bounds__(512) k_coarsest_b(const CoarsestArgs<T>* A, const BWork* W,
+                                                    int nwork, int gate) {
+  __shared__ CoarsestArgs<T> sa;
+  for (int it = blockIdx.x; it < nwork; it += gridDim.x) {
+    const BWork w = W[it];
+    if (!gate_pass(gate, w.ks, w.sp)) continue;
+    stage_args(sa, A[w.inst]);
+    if (!(sa.done && *sa.done)) coarsest_body<T, P>(sa.L, sa.b, sa.x, (T)sa.par[1]);
+    __syncthreads();
+  }
+}
 
 // Schur data of the coarsest level (after k_refresh): z = T_1^{-1} (beta w_1) by a ring
 // solve, and the origin row's denominator diag0 - beta sum_j o_j z_j.
 template <typename T, int P>
-__global__ void __launch_bounds__(512) k_schur(LevelView<T> L, const StepParams* sp,
-                                               const double* stamp) {
+__device__ __forceinline__ void schur_body(const LevelView<T>& L, const StepParams* sp,
+                                           const double* stamp) {
   if (!refresh_due(sp, stamp)) return;
   const T beta = (T)sp->beta;
   const Shape& sh = L.sh;
@@ -932,6 +987,23 @@ __global__ void __launch_bounds__(512) k_schur(LevelView<T> L, const StepParams*
     double tot = 0.0;
     for (int k = 0; k < (nt + 31) / 32; ++k) tot += red[k];
     L.sc[kSchurSlot<T>] = L.sc[0] - sp->beta * tot;
+  }
+}
+template <typename T, int P>
+__global__ void __launch_bounds__(512) k_schur(LevelView<T> L, const StepParams* sp,
+                                               const double* stamp) {
+  schur_body<T, P>(L, sp, stamp);
+}
+template <typename T, int P>
+__global__ void __launch_bounds__(512) k_schur_b(const CoarsestArgs<T>* A, const BWork* W,
+                                                 int nwork, int gate) {
+  __shared__ CoarsestArgs<T> sa;
+  for (int it = blockIdx.x; it < nwork; it += gridDim.x) {
+    const BWork w = W[it];
+    if (!gate_pass(gate, w.ks, w.sp)) continue;
+    stage_args(sa, A[w.inst]);
+    schur_body<T, P>(sa.L, sa.sp, sa.stamp);
+    __syncthreads();
   }
 }
 
@@ -1105,6 +1177,116 @@ static int launch_schur(const LevelView<T>& L, const StepParams* sp, const doubl
   return 1;
 }
 
+
+// ---------------------------------------------------------------------------------
+// batched launchers
+
+template <typename T>
+int launch_refresh_b(const RefreshArgs* A, const BWork* W, int nwork, int gate, cudaStream_t st) {
+  if (nwork <= 0) return 0;
+  k_refresh_b<T><<<persistent_grid(nwork, 2), dim3(RF, TF), 0, st>>>(A, W, nwork, gate);
+  return 1;
+}
+
+template <typename T, int P>
+static int launch_ring_bp(const RingShape& s, const RingArgs<T>* A, const BWork* W, int nwork,
+                          int gate, cudaStream_t st) {
+  void (*kern)(const RingArgs<T>*, const BWork*, int, int) =
+      s.ST ? k_ring_staged_b<T, P> : k_ring_b<T, P>;
+  // persistent: CTA columns (clusters of CS CTAs) walk the line groups of all instances;
+  // enough columns for the SMs to hold a few CTAs each
+  const int per = std::max(1, 4 * 512 / (s.RW * s.TW));
+  const int cols = std::max(1, std::min(nwork, persistent_grid(nwork, per) / s.CS));
+  if (s.CS == 1) {
+    kern<<<cols, dim3(s.RW, s.TW), ring_smem<T>(s), st>>>(A, W, nwork, gate);
+    return 1;
+  }
+  if (s.CS > kMaxCluster) return -1;
+  static bool allowed = false;
+  if (!allowed && s.CS > 8) {
+    cudaFuncSetAttribute(k_ring_b<T, P>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    cudaFuncSetAttribute(k_ring_staged_b<T, P>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    allowed = true;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(cols, s.CS, 1);
+  cfg.blockDim = dim3(s.RW, s.TW, 1);
+  cfg.dynamicSmemBytes = ring_smem<T>(s);
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = 1;
+  attr[0].val.clusterDim.y = s.CS;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, A, W, nwork, gate) == cudaSuccess ? 1 : -1;
+}
+
+template <typename T>
+int launch_ring_b(const RingShape& s, const RingArgs<T>* A, const BWork* W, int nwork, int gate,
+                  cudaStream_t st) {
+  if (nwork <= 0) return 0;
+  switch (s.P) {
+    case 4: return launch_ring_bp<T, 4>(s, A, W, nwork, gate, st);
+    case 8: return launch_ring_bp<T, 8>(s, A, W, nwork, gate, st);
+    case 16: return launch_ring_bp<T, 16>(s, A, W, nwork, gate, st);
+    default: return launch_ring_bp<T, 32>(s, A, W, nwork, gate, st);
+  }
+}
+
+template <typename T>
+int launch_restrict_b(const RestrictArgs<T>* A, const BWork* W, int nwork, int gate,
+                      cudaStream_t st) {
+  if (nwork <= 0) return 0;
+  k_restrict_b<T><<<persistent_grid(nwork, 8), 256, 0, st>>>(A, W, nwork, gate);
+  return 1;
+}
+
+template <typename T>
+void coarsest_shape(int n, int* P, int* TW) {
+  int p = 8;
+  while (p < 32 && (n + p - 1) / p > kRingThreads) p <<= 1;
+  int tw = 32;
+  while (tw < (n + p - 1) / p) tw <<= 1;
+  *P = p;
+  *TW = tw;
+}
+
+template <typename T>
+int launch_coarsest_b(int P, int TW, int schur, const CoarsestArgs<T>* A, const BWork* W,
+                      int nwork, int gate, cudaStream_t st) {
+  if (nwork <= 0) return 0;
+  RingShape s{};
+  s.RW = 1;
+  s.TW = TW;
+  s.P = P;
+  const size_t smem = ring_smem<T>(s);
+  const dim3 block(1, TW);
+  const int g = persistent_grid(nwork, std::max(1, 1024 / TW));
+  switch (P) {
+    case 8:
+      if (schur) k_schur_b<T, 8><<<g, block, smem, st>>>(A, W, nwork, gate);
+      else k_coarsest_b<T, 8><<<g, block, smem, st>>>(A, W, nwork, gate);
+      break;
+    case 16:
+      if (schur) k_schur_b<T, 16><<<g, block, smem, st>>>(A, W, nwork, gate);
+      else k_coarsest_b<T, 16><<<g, block, smem, st>>>(A, W, nwork, gate);
+      break;
+    default:
+      if (schur) k_schur_b<T, 32><<<g, block, smem, st>>>(A, W, nwork, gate);
+      else k_coarsest_b<T, 32><<<g, block, smem, st>>>(A, W, nwork, gate);
+      break;
+  }
+  return 1;
+}
+
+int launch_stamp_b(const BWork* W, double* const* stamps, int nwork, int gate, cudaStream_t st) {
+  if (nwork <= 0) return 0;
+  k_stamp_b<<<(nwork + 127) / 128, 128, 0, st>>>(W, stamps, nwork, gate);
+  return 1;
+}
+
 // The ring kernels use dynamic shared memory only for the scan buffers
 // (2 RW TW + 4 RW words): at most 16.1 KB, below the default 48 KB limit.
 
@@ -1119,7 +1301,17 @@ static int launch_schur(const LevelView<T>& L, const StepParams* sp, const doubl
   template int launch_restrict<T>(const LevelView<T>&, const LevelView<T>&, const T*, T*,      \
                                   Params, const int*, cudaStream_t);                          \
   template int launch_coarsest<T>(const LevelView<T>&, const T*, T*, Params, const int*,       \
-                                  cudaStream_t);
+                                  cudaStream_t);                                              \
+  template RefreshArgs make_refresh_args<T>(const LevelView<double>*, LevelView<T>*, int,     \
+                                            const StepParams*, double*, double*, int*);       \
+  template int launch_refresh_b<T>(const RefreshArgs*, const BWork*, int, int, cudaStream_t); \
+  template int launch_ring_b<T>(const RingShape&, const RingArgs<T>*, const BWork*, int, int,  \
+                                cudaStream_t);                                                \
+  template int launch_restrict_b<T>(const RestrictArgs<T>*, const BWork*, int, int,            \
+                                    cudaStream_t);                                            \
+  template void coarsest_shape<T>(int, int*, int*);                                           \
+  template int launch_coarsest_b<T>(int, int, int, const CoarsestArgs<T>*, const BWork*, int,  \
+                                    int, cudaStream_t);
 
 POLAR_MG_INST(float)
 POLAR_MG_INST(double)
