@@ -644,19 +644,21 @@ def run_batch(args):
         failed = [mine[i] for i, row in enumerate(stats) if any(s["status"] != 0 for s in row)]
         ok = [s for row in stats for s in row if s["status"] == 0]
         iters = float(np.mean([s["iters"] for s in ok])) if ok else 0.0
+        # the batch's loops run as long as the slowest instance: mean over steps of the max
+        imax = float(np.mean([max(row[k]["iters"] for row in stats) for k in range(K)]))
         # only the steps an instance completed count as updates (a failed step halts the
         # rest of that instance's schedule; its state stays at the last committed level)
         updates = sum_over_ranks(dist, [sum(p.N * d for p, d in zip(probs, done))])[0]
         launches = P.polar_batch_kernel_launches(batch) - launches0
-        return ms, K, states, iters, clk, launches, updates, failed
+        return ms, K, states, (iters, imax), clk, launches, updates, failed
 
-    ms, K, st_main, iters, clk, launches, updates, failed = run(precision)
+    ms, K, st_main, (iters, imax), clk, launches, updates, failed = run(precision)
     pts = sum_over_ranks(dist, [sum(p.N for p in probs)])[0]
     value = updates / (ms * 1e-3)
     compare = None
     if args.compare:
         other = P.POLAR_FP64 if precision == P.POLAR_MIXED else P.POLAR_MIXED
-        ms2, _, st2, it2, _, _, up2, failed2 = run(other)
+        ms2, _, st2, (it2, _), _, _, up2, failed2 = run(other)
         bad = set(failed) | set(failed2)
         diff = max([float(np.max(np.abs(a - b)) / np.max(np.abs(b)))
                     for i, a, b in zip(mine, st_main, st2) if i not in bad] or [0.0])
@@ -676,7 +678,8 @@ def run_batch(args):
                        "sum_N": pts, "precision": args.precision,
                        "l2": "inputs larger than L2 (several GB of instance data)",
                        "parallelism": f"replicas x{world}"},
-            "krylov_iters_per_step": iters, "failed_instances": failed, "compare": compare,
+            "krylov_iters_per_step": iters, "krylov_iters_max_per_step": imax,
+            "failed_instances": failed, "compare": compare,
             "gpu_launches": int(launches),
             "clocks": clk, "setup_s": gen_s}
     if rank == 0:

@@ -225,11 +225,13 @@ int polar_advance(polar_ctx* ctx, int32_t nsteps, const double* t, double theta,
  * time), theta[i] its implicit weight, w[i] its (nsteps+1) x nsrc source weights (w may be
  * NULL when no instance has sources).  One CUDA graph advances every instance by one step
  * and is launched nsteps times on `stream`: each kernel class of the step runs as one
- * launch per phase over a work list of (instance, block) -- every instance keeps the
+ * launch per phase over the blocks of every active instance -- each instance keeps the
  * block partition of its own launches, so its result equals that of advancing it alone
  * bit for bit -- and the refinement and Krylov loops run while any instance still needs
- * them, the instances that are done masked out.  Launches whose block or cluster shape
- * differs between instances (ring-solve tiles, coarsest-level solves) run once per shape.
+ * them.  Per-instance masks, rewritten on the device wherever instances start or stop
+ * (step start, refinement decisions, Krylov iterations), leave the finished instances out
+ * of a launch's work.  Launches whose block or cluster shape differs between instances
+ * (ring-solve tiles, coarsest-level solves) run once per shape.  count <= 1024.
  * The graph is rebuilt when a context changed.  stats
  * (count x nsteps, instance-major) or NULL.  An instance stops at its first failing step
  * (state kept at its last committed level, later entries POLAR_ESTATE); the others go on.

@@ -137,6 +137,8 @@ struct polar_ctx {
   int64_t graph_kernels_fixed = 0, graph_kernels_sweep = 0, graph_kernels_iter = 0;
   int64_t graph_kernels_iter64 = 0;  // mixed path: an FP64 Krylov iteration over the FP32 V-cycle
   bool symmetric = false;  // S is symmetric (no drift): CG instead of BiCGStab
+  bool steady = false;     // the running advance solves the steady problem (alpha = 0)
+  double* mesh_dev = nullptr;  // r (m+2), theta (n), boundary values (n): face fields
   // direct solve of separable operators (Fourier in theta, tridiagonal in r)
   bool separable = false;     // the current coefficients are separable
   bool direct_now = false;    // the current advance uses the direct inner solve
@@ -1136,7 +1138,7 @@ int make_params(polar_ctx* c, double t0, double t1, double theta, const double* 
   const double dt = t1 - t0;
   if (!(dt > 0.0) || !std::isfinite(dt)) return fail(POLAR_EINVAL, "dt must be positive and finite");
   p = StepParams{};
-  p.alpha = 1.0 / dt;
+  p.alpha = c->steady ? 0.0 : 1.0 / dt;  // steady solve: L U = f (no time derivative)
   p.beta = theta;
   p.omt = 1.0 - theta;
   for (int q = 0; q < c->nsrc; ++q) {
@@ -1440,12 +1442,16 @@ int setup_direct(polar_ctx* c, const HLevel& H) {
 // ---- batched execution: one launch per kernel class and phase for all instances.
 //
 // A batch step graph is built in two passes of the same code: the plan pass collects every
-// launch's per-instance argument table and work list in a host image; the image goes to
-// the device in one copy; the capture pass records the launches, whose tables now sit at
-// the same offsets of the device arena.  Every instance keeps its own grid partition
-// (BWork: block vb of its lone grid vg), so its arithmetic -- and its result -- is the same
-// as when it runs alone.  Gates and per-instance `done` flags mask the instances a launch
-// does not serve at that moment; WHILE nodes loop while any instance is still active.
+// launch's per-slot argument table and slot list in a host image; the image goes to the
+// device in one copy; the capture pass records the launches, whose tables now sit at the
+// same offsets of the device arena.  Every instance keeps its own grid partition (a slot's
+// virtual blocks), so its arithmetic -- and its result -- is the same as when it runs alone.
+// Active-instance masks, written between launches by k_mask_b at the points where instances
+// start or stop (step start, refinement decisions, Krylov iterations), decide which slots a
+// launch serves; WHILE nodes loop while any instance is still active.
+
+// the masks of a batch step (one int per instance each)
+enum { MK_STEP, MK_REF, MK_32, MK_64, MK_DIR, MK_IT32, MK_IT64, MK_COUNT };
 
 struct BatchBuild {
   polar_batch* b = nullptr;
@@ -1455,6 +1461,8 @@ struct BatchBuild {
   size_t off = 0;
   cudaStream_t cs = nullptr;         // capture stream
   int64_t launches = 0;              // kernels captured so far
+  int sms = 152;                     // SMs of the device (grid sizes)
+  int* mask[MK_COUNT] = {};
 
   // a table in the arena: appended in the plan pass, its device address in the capture pass
   template <class A>
@@ -1483,30 +1491,19 @@ struct BatchBuild {
     launches += k;
     return POLAR_OK;
   }
+  // grid of a launch with `items` work items: per_sm blocks per SM at most
+  int grid(int64_t items, int per_sm) const {
+    return (int)std::max<int64_t>(1, std::min<int64_t>(items, (int64_t)sms * per_sm));
+  }
 };
 
 // per-instance facts the planner groups by
 struct BInst {
   polar_ctx* c;
-  int idx;          // position in the batch
+  int idx;          // position in the batch (and in the masks)
   bool mixed;       // FP32 inner solves (and the FP64 fallback)
   bool direct;      // separable: the direct inner solve
 };
-
-BWork bwork(const polar_ctx* c, int inst, int vb, int vg, int aux) {
-  return BWork{inst, vb, vg, aux, c->ks, c->sp};
-}
-
-// Work list of a grid-stride launch: instance k of `list` gets vg = grid_of(c) blocks.
-template <class G>
-std::vector<BWork> grid_work(const std::vector<const BInst*>& list, G grid_of) {
-  std::vector<BWork> w;
-  for (int k = 0; k < (int)list.size(); ++k) {
-    const int vg = grid_of(list[k]->c);
-    for (int vb = 0; vb < vg; ++vb) w.push_back(bwork(list[k]->c, k, vb, vg, 0));
-  }
-  return w;
-}
 
 int stencil_grid(const Shape& sh) {
   const Tiling t = make_tiling(sh);
@@ -1536,41 +1533,54 @@ VecArgs<T> vargs(const polar_ctx* c) {
   return a;
 }
 
+int64_t slot_items(const std::vector<BSlot>& s) {
+  int64_t t = 0;
+  for (const BSlot& x : s) t += x.vg;
+  return t;
+}
+
 // Stencil launches: instances grouped by their tiling's TK (the block shape).
 template <typename T, class MakeArgs>
-int batch_stencil(BatchBuild& B, int mode, const std::vector<const BInst*>& list, int gate,
+int batch_stencil(BatchBuild& B, int mode, const std::vector<const BInst*>& list, int mk,
                   MakeArgs make) {
   for (int TK = 32; TK <= 256; TK <<= 1) {
-    std::vector<const BInst*> sub;
+    std::vector<BSlot> slots;
     std::vector<StArgs<T>> args;
     for (const BInst* i : list)
       if (make_tiling(i->c->sh0()).TK == TK) {
-        sub.push_back(i);
+        slots.push_back(BSlot{i->idx, stencil_grid(i->c->sh0())});
         args.push_back(make(i->c));
       }
-    if (sub.empty()) continue;
-    const std::vector<BWork> w = grid_work(sub, [](const polar_ctx* c) { return stencil_grid(c->sh0()); });
+    if (slots.empty()) continue;
     const StArgs<T>* A = B.put(args);
-    const BWork* W = B.put(w);
-    TRY(B.launch([&] { return launch_stencil_b<T>(mode, A, W, (int)w.size(), TK, gate, B.cs); }));
+    const BSlot* S = B.put(slots);
+    const int g = B.grid(slot_items(slots), 8);
+    const int* M = B.mask[mk];
+    TRY(B.launch([&] { return launch_stencil_b<T>(mode, A, S, (int)slots.size(), M, g, TK, B.cs); }));
   }
   return POLAR_OK;
 }
 
 // Vector-kernel launch over `list` (grid_for(nv) blocks each).
 template <typename T, class MakeArgs>
-int batch_vec(BatchBuild& B, int kind, const std::vector<const BInst*>& list, int gate,
+int batch_vec(BatchBuild& B, int kind, const std::vector<const BInst*>& list, int mk,
               MakeArgs make) {
   if (list.empty()) return POLAR_OK;
   std::vector<VecArgs<T>> args;
-  for (const BInst* i : list) args.push_back(make(i->c));
-  const std::vector<BWork> w = grid_work(list, [](const polar_ctx* c) { return grid_for(c->nv(), 256); });
+  std::vector<BSlot> slots;
+  for (const BInst* i : list) {
+    args.push_back(make(i->c));
+    slots.push_back(BSlot{i->idx, grid_for(i->c->nv(), 256)});
+  }
   const VecArgs<T>* A = B.put(args);
-  const BWork* W = B.put(w);
-  return B.launch([&] { return launch_vec_b<T>(kind, A, W, (int)w.size(), gate, B.cs); });
+  const BSlot* S = B.put(slots);
+  const int g = B.grid(slot_items(slots), 8);
+  const int* M = B.mask[mk];
+  return B.launch([&] { return launch_vec_b<T>(kind, A, S, (int)slots.size(), M, g, B.cs); });
 }
 
-CtlArgs ctl_args(polar_ctx* c) {
+CtlArgs ctl_args(const BInst* i) {
+  polar_ctx* c = i->c;
   CtlArgs a{};
   a.sched = c->sched;
   a.kstep = c->kstep;
@@ -1578,23 +1588,29 @@ CtlArgs ctl_args(polar_ctx* c) {
   a.sp = c->sp;
   a.out = c->dout;
   a.ks = c->ks;
+  a.inst = i->idx;
   return a;
 }
 
 int batch_ctl(BatchBuild& B, int kind, const std::vector<const BInst*>& list, int gate) {
   if (list.empty()) return POLAR_OK;
   std::vector<CtlArgs> args;
-  for (const BInst* i : list) args.push_back(ctl_args(i->c));
+  for (const BInst* i : list) args.push_back(ctl_args(i));
   const CtlArgs* A = B.put(args);
   return B.launch([&] { return launch_ctl_b(kind, A, (int)args.size(), gate, B.cs); });
 }
 
-int batch_any(BatchBuild& B, const std::vector<const BInst*>& list, int gate, int need_running,
-              CondHandle cond) {
+// mask `mk` of the instances of `list` (the others keep 0); cond (if any) = any active
+int batch_mask(BatchBuild& B, const std::vector<const BInst*>& list, int gate, int need_running,
+               int mk, CondHandle cond) {
+  if (list.empty() && !cond) return POLAR_OK;
   std::vector<CtlArgs> args;
-  for (const BInst* i : list) args.push_back(ctl_args(i->c));
+  for (const BInst* i : list) args.push_back(ctl_args(i));
   const CtlArgs* A = B.put(args);
-  return B.launch([&] { return launch_any_b(A, (int)args.size(), gate, need_running, cond, B.cs); });
+  int* M = B.mask[mk];
+  return B.launch([&] {
+    return launch_mask_b(A, (int)args.size(), gate, need_running, M, cond, B.cs);
+  });
 }
 
 // Inputs and outputs of one V-cycle per instance (level 0 vectors in precision T).
@@ -1611,7 +1627,7 @@ struct VIO {
 // launch).  Each instance checks its own `done` flag, as its lone cycle does.
 template <typename T>
 int batch_vcycle(BatchBuild& B, const std::vector<const BInst*>& list,
-                 const std::vector<VIO<T>>& io, int gate) {
+                 const std::vector<VIO<T>>& io, int mk) {
   int lmax = 0;
   for (const BInst* i : list) lmax = std::max(lmax, i->c->nlev() - 1);
   auto bof = [&](int k, int l) { return l == 0 ? io[k].b : static_cast<const T*>(coarse_b<T>(list[k]->c, l)); };
@@ -1638,7 +1654,7 @@ int batch_vcycle(BatchBuild& B, const std::vector<const BInst*>& list,
     for (auto& g : groups) {
       const RingShape& s = g.first;
       std::vector<RingArgs<T>> args;
-      std::vector<BWork> w;
+      std::vector<BSlot> slots;
       for (int k : g.second) {
         polar_ctx* c = list[k]->c;
         const std::vector<LevelView<T>>& L = views<T>(c);
@@ -1653,20 +1669,24 @@ int batch_vcycle(BatchBuild& B, const std::vector<const BInst*>& list,
         a.parity = parity;
         a.mode = mode;
         const int nl = parity ? L[l].sh.no : L[l].sh.ne;
-        const int ng = (nl + s.RW - 1) / s.RW;
-        for (int q = 0; q < ng; ++q) w.push_back(bwork(c, (int)args.size(), q, ng, q * s.RW));
+        slots.push_back(BSlot{list[k]->idx, (nl + s.RW - 1) / s.RW});
         args.push_back(a);
       }
       const RingArgs<T>* A = B.put(args);
-      const BWork* W = B.put(w);
-      TRY(B.launch([&] { return launch_ring_b<T>(s, A, W, (int)w.size(), gate, B.cs); }));
+      const BSlot* S = B.put(slots);
+      // columns of CS CTAs (one work item each): a few CTAs per SM in all
+      const int per = std::max(1, 2048 / (s.RW * s.TW));
+      const int cols = (int)std::max<int64_t>(
+          1, std::min<int64_t>(slot_items(slots), (int64_t)B.sms * per / s.CS));
+      const int* M = B.mask[mk];
+      TRY(B.launch([&] { return launch_ring_b<T>(s, A, S, (int)slots.size(), M, cols, B.cs); }));
     }
     return POLAR_OK;
   };
   for (int l = 0; l < lmax; ++l) {
     TRY(ring_phase(l, RING_PRE, 1));
     TRY(ring_phase(l, RING_PRE, 0));
-    std::vector<const BInst*> sub;
+    std::vector<BSlot> slots;
     std::vector<RestrictArgs<T>> args;
     for (int k = 0; k < (int)list.size(); ++k) {
       polar_ctx* c = list[k]->c;
@@ -1674,17 +1694,14 @@ int batch_vcycle(BatchBuild& B, const std::vector<const BInst*>& list,
       const std::vector<LevelView<T>>& L = views<T>(c);
       args.push_back(RestrictArgs<T>{L[l], L[l + 1], xof(k, l), coarse_b<T>(c, l + 1), c->par(),
                                      &c->ks->done});
-      sub.push_back(list[k]);
+      slots.push_back(BSlot{list[k]->idx, grid_for((size_t)L[l + 1].sh.m * L[l].sh.n, 256)});
     }
-    if (!sub.empty()) {
-      const int lv = l;
-      const std::vector<BWork> w = grid_work(sub, [&](const polar_ctx* c) {
-        const std::vector<LevelView<T>>& L = views<T>(c);
-        return grid_for((size_t)L[lv + 1].sh.m * L[lv].sh.n, 256);
-      });
+    if (!slots.empty()) {
       const RestrictArgs<T>* A = B.put(args);
-      const BWork* W = B.put(w);
-      TRY(B.launch([&] { return launch_restrict_b<T>(A, W, (int)w.size(), gate, B.cs); }));
+      const BSlot* S = B.put(slots);
+      const int g = B.grid(slot_items(slots), 8);
+      const int* M = B.mask[mk];
+      TRY(B.launch([&] { return launch_restrict_b<T>(A, S, (int)slots.size(), M, g, B.cs); }));
     }
   }
   // coarsest levels, grouped by their launch shape
@@ -1703,7 +1720,7 @@ int batch_vcycle(BatchBuild& B, const std::vector<const BInst*>& list,
   }
   for (auto& g : cg) {
     std::vector<CoarsestArgs<T>> args;
-    std::vector<BWork> w;
+    std::vector<BSlot> slots;
     for (int k : g.second) {
       polar_ctx* c = list[k]->c;
       const int lc = c->nlev() - 1;
@@ -1713,13 +1730,15 @@ int batch_vcycle(BatchBuild& B, const std::vector<const BInst*>& list,
       a.x = xof(k, lc);
       a.par = c->par();
       a.done = &c->ks->done;
-      w.push_back(bwork(c, (int)args.size(), 0, 1, 0));
+      slots.push_back(BSlot{list[k]->idx, 1});
       args.push_back(a);
     }
     const CoarsestArgs<T>* A = B.put(args);
-    const BWork* W = B.put(w);
+    const BSlot* S = B.put(slots);
     const int P = g.first.first, TW = g.first.second;
-    TRY(B.launch([&] { return launch_coarsest_b<T>(P, TW, 0, A, W, (int)w.size(), gate, B.cs); }));
+    const int gr = B.grid(slot_items(slots), 2);
+    const int* M = B.mask[mk];
+    TRY(B.launch([&] { return launch_coarsest_b<T>(P, TW, 0, A, S, (int)slots.size(), M, gr, B.cs); }));
   }
   for (int l = lmax - 1; l >= 0; --l) {
     TRY(ring_phase(l, RING_POST, 0));
@@ -1732,60 +1751,63 @@ int batch_vcycle(BatchBuild& B, const std::vector<const BInst*>& list,
 // each instance's do_refresh, or its stamp when `stamped`), then the coarsest levels'
 // Schur data and, when stamped, the stamps.
 template <typename T>
-int batch_refresh(BatchBuild& B, const std::vector<const BInst*>& list, bool stamped, int gate) {
+int batch_refresh(BatchBuild& B, const std::vector<const BInst*>& list, bool stamped, int mk) {
   if (list.empty()) return POLAR_OK;
   std::vector<RefreshArgs> args;
-  std::vector<BWork> w;
-  for (int k = 0; k < (int)list.size(); ++k) {
-    polar_ctx* c = list[k]->c;
+  std::vector<BSlot> slots;
+  for (const BInst* i : list) {
+    polar_ctx* c = i->c;
     std::vector<LevelView<T>> vt = views<T>(c);
     int nb = 0;
     args.push_back(make_refresh_args<T>(c->v64.data(), vt.data(), c->nlev(), c->sp, c->ws,
                                         stamped ? c->stamp64 : nullptr, &nb));
-    for (int vb = 0; vb < nb; ++vb) w.push_back(bwork(c, k, vb, nb, 0));
+    slots.push_back(BSlot{i->idx, nb});
   }
   const RefreshArgs* A = B.put(args);
-  const BWork* W = B.put(w);
-  TRY(B.launch([&] { return launch_refresh_b<T>(A, W, (int)w.size(), gate, B.cs); }));
-  std::vector<std::pair<std::pair<int, int>, std::vector<int>>> cg;
-  for (int k = 0; k < (int)list.size(); ++k) {
+  const BSlot* S = B.put(slots);
+  const int g = B.grid(slot_items(slots), 2);
+  const int* M = B.mask[mk];
+  TRY(B.launch([&] { return launch_refresh_b<T>(A, S, (int)slots.size(), M, g, B.cs); }));
+  std::vector<std::pair<std::pair<int, int>, std::vector<const BInst*>>> cg;
+  for (const BInst* i : list) {
     int P = 0, TW = 0;
-    coarsest_shape<T>(views<T>(list[k]->c).back().sh.n, &P, &TW);
+    coarsest_shape<T>(views<T>(i->c).back().sh.n, &P, &TW);
     bool found = false;
-    for (auto& g : cg)
-      if (g.first == std::make_pair(P, TW)) {
-        g.second.push_back(k);
+    for (auto& g2 : cg)
+      if (g2.first == std::make_pair(P, TW)) {
+        g2.second.push_back(i);
         found = true;
       }
-    if (!found) cg.push_back({{P, TW}, {k}});
+    if (!found) cg.push_back({{P, TW}, {i}});
   }
-  for (auto& g : cg) {
+  for (auto& g2 : cg) {
     std::vector<CoarsestArgs<T>> sargs;
-    std::vector<BWork> sw;
-    for (int k : g.second) {
-      polar_ctx* c = list[k]->c;
+    std::vector<BSlot> ss;
+    for (const BInst* i : g2.second) {
+      polar_ctx* c = i->c;
       CoarsestArgs<T> a{};
       a.L = views<T>(c).back();
       a.sp = c->sp;
       a.stamp = stamped ? c->stamp64 : nullptr;
-      sw.push_back(bwork(c, (int)sargs.size(), 0, 1, 0));
+      ss.push_back(BSlot{i->idx, 1});
       sargs.push_back(a);
     }
     const CoarsestArgs<T>* A2 = B.put(sargs);
-    const BWork* W2 = B.put(sw);
-    const int P = g.first.first, TW = g.first.second;
-    TRY(B.launch([&] { return launch_coarsest_b<T>(P, TW, 1, A2, W2, (int)sw.size(), gate, B.cs); }));
+    const BSlot* S2 = B.put(ss);
+    const int P = g2.first.first, TW = g2.first.second;
+    const int gr = B.grid(slot_items(ss), 2);
+    TRY(B.launch([&] { return launch_coarsest_b<T>(P, TW, 1, A2, S2, (int)ss.size(), M, gr, B.cs); }));
   }
   if (stamped) {
     std::vector<double*> stamps;
-    std::vector<BWork> ow;
-    for (int k = 0; k < (int)list.size(); ++k) {
-      ow.push_back(bwork(list[k]->c, k, 0, 1, 0));
-      stamps.push_back(list[k]->c->stamp64);
+    std::vector<const StepParams*> sps;
+    for (const BInst* i : list) {
+      stamps.push_back(i->c->stamp64);
+      sps.push_back(i->c->sp);
     }
-    double* const* S = B.put(stamps);
-    const BWork* W3 = B.put(ow);
-    TRY(B.launch([&] { return launch_stamp_b(W3, S, (int)ow.size(), gate, B.cs); }));
+    double* const* ST = B.put(stamps);
+    const StepParams* const* SP = B.put(sps);
+    TRY(B.launch([&] { return launch_stamp_b(S, (int)slots.size(), M, ST, SP, B.cs); }));
   }
   return POLAR_OK;
 }
@@ -1793,7 +1815,7 @@ int batch_refresh(BatchBuild& B, const std::vector<const BInst*>& list, bool sta
 // One Krylov iteration of every instance of `list` in precision T: CG for the symmetric
 // ones, BiCGStab for the others (each instance's kernels in its lone order).
 template <typename T>
-int batch_iteration(BatchBuild& B, const std::vector<const BInst*>& list, int gate) {
+int batch_iteration(BatchBuild& B, const std::vector<const BInst*>& list, int mk) {
   std::vector<const BInst*> cgl, bil;
   for (const BInst* i : list) (i->c->symmetric ? cgl : bil).push_back(i);
   std::vector<VIO<T>> io;
@@ -1801,26 +1823,26 @@ int batch_iteration(BatchBuild& B, const std::vector<const BInst*>& list, int ga
     KVecs<T>& k = kvecs<T>(i->c);
     io.push_back(i->c->symmetric ? VIO<T>{k.r, k.phat} : VIO<T>{k.p, k.phat});
   }
-  TRY(batch_vcycle<T>(B, list, io, gate));
-  TRY(batch_vec<T>(B, V_CG_RHO, cgl, gate, [](polar_ctx* c) {
+  TRY(batch_vcycle<T>(B, list, io, mk));
+  TRY(batch_vec<T>(B, V_CG_RHO, cgl, mk, [](polar_ctx* c) {
     VecArgs<T> a = vargs<T>(c);
     a.v0 = kvecs<T>(c).r;
     a.v1 = kvecs<T>(c).phat;
     return a;
   }));
-  TRY(batch_vec<T>(B, V_CG_P, cgl, gate, [](polar_ctx* c) {
+  TRY(batch_vec<T>(B, V_CG_P, cgl, mk, [](polar_ctx* c) {
     VecArgs<T> a = vargs<T>(c);
     a.v0 = kvecs<T>(c).p;
     a.v1 = kvecs<T>(c).phat;
     return a;
   }));
   // q = S p (CG) and v = S phat (BiCGStab), both the stencil's DOTV mode
-  TRY(batch_stencil<T>(B, M_DOTV, list, gate, [](polar_ctx* c) {
+  TRY(batch_stencil<T>(B, M_DOTV, list, mk, [](polar_ctx* c) {
     KVecs<T>& k = kvecs<T>(c);
     return c->symmetric ? st_args<T>(c, k.p, k.v, k.p, nullptr)
                         : st_args<T>(c, k.phat, k.v, k.rhat, nullptr);
   }));
-  TRY(batch_vec<T>(B, V_CG_UPDATE, cgl, gate, [](polar_ctx* c) {
+  TRY(batch_vec<T>(B, V_CG_UPDATE, cgl, mk, [](polar_ctx* c) {
     KVecs<T>& k = kvecs<T>(c);
     VecArgs<T> a = vargs<T>(c);
     a.v0 = k.d;
@@ -1832,7 +1854,7 @@ int batch_iteration(BatchBuild& B, const std::vector<const BInst*>& list, int ga
     return a;
   }));
   if (bil.empty()) return POLAR_OK;
-  TRY(batch_vec<T>(B, V_BICG_S, bil, gate, [](polar_ctx* c) {
+  TRY(batch_vec<T>(B, V_BICG_S, bil, mk, [](polar_ctx* c) {
     KVecs<T>& k = kvecs<T>(c);
     VecArgs<T> a = vargs<T>(c);
     a.v0 = k.r;
@@ -1842,12 +1864,12 @@ int batch_iteration(BatchBuild& B, const std::vector<const BInst*>& list, int ga
   }));
   std::vector<VIO<T>> io2;
   for (const BInst* i : bil) io2.push_back(VIO<T>{kvecs<T>(i->c).s, kvecs<T>(i->c).shat});
-  TRY(batch_vcycle<T>(B, bil, io2, gate));
-  TRY(batch_stencil<T>(B, M_DOTT, bil, gate, [](polar_ctx* c) {
+  TRY(batch_vcycle<T>(B, bil, io2, mk));
+  TRY(batch_stencil<T>(B, M_DOTT, bil, mk, [](polar_ctx* c) {
     KVecs<T>& k = kvecs<T>(c);
     return st_args<T>(c, k.shat, k.t, k.s, nullptr);
   }));
-  TRY(batch_vec<T>(B, V_BICG_UPDATE, bil, gate, [](polar_ctx* c) {
+  TRY(batch_vec<T>(B, V_BICG_UPDATE, bil, mk, [](polar_ctx* c) {
     KVecs<T>& k = kvecs<T>(c);
     VecArgs<T> a = vargs<T>(c);
     a.v0 = k.d;
@@ -1861,7 +1883,7 @@ int batch_iteration(BatchBuild& B, const std::vector<const BInst*>& list, int ga
     a.sc = views<T>(c)[0].sc;
     return a;
   }));
-  TRY(batch_vec<T>(B, V_BICG_P, bil, gate, [](polar_ctx* c) {
+  TRY(batch_vec<T>(B, V_BICG_P, bil, mk, [](polar_ctx* c) {
     KVecs<T>& k = kvecs<T>(c);
     VecArgs<T> a = vargs<T>(c);
     a.v0 = k.p;
@@ -1873,19 +1895,20 @@ int batch_iteration(BatchBuild& B, const std::vector<const BInst*>& list, int ga
 }
 
 // Batched direct solves (separable instances): scaled cast, transform / modes / inverse.
-int batch_direct(BatchBuild& B, const std::vector<const BInst*>& list, int gate) {
+int batch_direct(BatchBuild& B, const std::vector<const BInst*>& list, int mk, int gate) {
   if (list.empty()) return POLAR_OK;
-  TRY(batch_vec<double>(B, V_SCALE_CAST, list, gate, [](polar_ctx* c) {
+  TRY(batch_vec<double>(B, V_SCALE_CAST, list, mk, [](polar_ctx* c) {
     VecArgs<double> a = vargs<double>(c);
     a.v0 = c->kv64.r;
     a.w0 = c->r64;
     return a;
   }));
   std::vector<DirectArgs> args;
-  std::vector<BWork> wr, wm, wo;
+  std::vector<BSlot> sr, sm;
+  std::vector<KrylovScalars*> ks;
   size_t smem = 0;
-  for (int k = 0; k < (int)list.size(); ++k) {
-    polar_ctx* c = list[k]->c;
+  for (const BInst* i : list) {
+    polar_ctx* c = i->c;
     DirectArgs a{};
     a.sh = c->sh0();
     a.P = c->plan;
@@ -1898,24 +1921,23 @@ int batch_direct(BatchBuild& B, const std::vector<const BInst*>& list, int gate)
     a.cp = c->fcp;
     a.z = c->fzv;
     const int rw = c->plan.rw;
-    const int groups = (a.sh.no + rw - 1) / rw + (a.sh.ne + rw - 1) / rw;
-    for (int q = 0; q < groups; ++q) wr.push_back(bwork(c, k, q, groups, 0));
-    const int mg = (c->plan.nh + 127) / 128;
-    for (int q = 0; q < mg; ++q) wm.push_back(bwork(c, k, q, mg, 0));
-    wo.push_back(bwork(c, k, 0, 1, 0));
+    sr.push_back(BSlot{i->idx, (a.sh.no + rw - 1) / rw + (a.sh.ne + rw - 1) / rw});
+    sm.push_back(BSlot{i->idx, (c->plan.nh + 127) / 128});
+    ks.push_back(c->ks);
     smem = std::max(smem, dft_smem(c->plan));
     args.push_back(a);
   }
   const DirectArgs* A = B.put(args);
-  const BWork* Wr = B.put(wr);
-  const BWork* Wm = B.put(wm);
-  const BWork* Wo = B.put(wo);
+  const BSlot* Sr = B.put(sr);
+  const BSlot* Sm = B.put(sm);
+  KrylovScalars* const* KS = B.put(ks);
+  const int gr = B.grid(slot_items(sr), 2), gm = B.grid(slot_items(sm), 8);
+  const int* M = B.mask[mk];
   TRY(B.launch([&] {
-    return launch_direct_b(A, Wr, (int)wr.size(), Wm, (int)wm.size(), Wo, (int)wo.size(), smem,
-                           gate, B.cs);
+    return launch_direct_b(A, Sr, Sm, (int)sr.size(), M, KS, gr, gm, smem, B.cs);
   }));
   TRY(batch_ctl(B, C_AFTER_INNER, list, gate));
-  return batch_vec<double>(B, V_CORRECT, list, gate, [](polar_ctx* c) {
+  return batch_vec<double>(B, V_CORRECT, list, mk, [](polar_ctx* c) {
     VecArgs<double> a = vargs<double>(c);
     a.v0 = c->kv64.d;
     a.w0 = c->X;
@@ -1961,13 +1983,13 @@ int bwhile(BatchBuild& B, cudaGraph_t g, const std::vector<cudaGraphNode_t>& dep
   return add_cond(g, deps, (cudaGraphConditionalHandle)h, cudaGraphCondTypeWhile, node, body);
 }
 
-// One inner Krylov solve of the instances of `list` in precision T (gate: the branch),
-// appended to graph g after `deps`: set-up, WHILE (any iterating) { iteration }, counts and
-// correction of X.  *sinks receives the last node.
+// One inner Krylov solve of the instances of `list` in precision T (gate: the branch, whose
+// mask mk_branch is set), appended to graph g after `deps`: set-up, WHILE (any iterating)
+// { iteration }, counts and correction of X.  *sinks receives the last node.
 template <typename T>
 int batch_inner(BatchBuild& B, cudaGraph_t g, std::vector<cudaGraphNode_t> deps,
-                const std::vector<const BInst*>& list, int gate, bool fp64_refresh,
-                std::vector<cudaGraphNode_t>* sinks, int64_t* per_iter) {
+                const std::vector<const BInst*>& list, int gate, int mk_branch, int mk_it,
+                bool fp64_refresh, std::vector<cudaGraphNode_t>* sinks, int64_t* per_iter) {
   CondHandle hit = 0;
   TRY(bcond(B, g, &hit));
   TRY(bcap_begin(B, g, deps));
@@ -1975,15 +1997,15 @@ int batch_inner(BatchBuild& B, cudaGraph_t g, std::vector<cudaGraphNode_t> deps,
     std::vector<const BInst*> mixed;
     for (const BInst* i : list)
       if (i->mixed) mixed.push_back(i);
-    TRY(batch_refresh<double>(B, mixed, true, gate));
+    TRY(batch_refresh<double>(B, mixed, true, mk_branch));
   }
-  TRY(batch_vec<T>(B, V_SCALE_CAST, list, gate, [](polar_ctx* c) {
+  TRY(batch_vec<T>(B, V_SCALE_CAST, list, mk_branch, [](polar_ctx* c) {
     VecArgs<T> a = vargs<T>(c);
     a.v0 = kvecs<T>(c).r;
     a.w0 = c->r64;
     return a;
   }));
-  TRY(batch_vec<T>(B, V_BICG_INIT, list, gate, [](polar_ctx* c) {
+  TRY(batch_vec<T>(B, V_BICG_INIT, list, mk_branch, [](polar_ctx* c) {
     KVecs<T>& k = kvecs<T>(c);
     VecArgs<T> a = vargs<T>(c);
     a.v0 = k.r;
@@ -1993,7 +2015,7 @@ int batch_inner(BatchBuild& B, cudaGraph_t g, std::vector<cudaGraphNode_t> deps,
     a.v4 = k.d;
     return a;
   }));
-  TRY(batch_any(B, list, gate, 1, hit));
+  TRY(batch_mask(B, list, gate, 1, mk_it, hit));
   std::vector<cudaGraphNode_t> s1;
   TRY(bcap_end(B, &s1));
   cudaGraphNode_t nit;
@@ -2001,13 +2023,13 @@ int batch_inner(BatchBuild& B, cudaGraph_t g, std::vector<cudaGraphNode_t> deps,
   TRY(bwhile(B, g, s1, hit, &nit, &bit));
   const int64_t a0 = B.launches;
   TRY(bcap_begin(B, bit, {}));
-  TRY(batch_iteration<T>(B, list, gate));
-  TRY(batch_any(B, list, gate, 1, hit));
+  TRY(batch_iteration<T>(B, list, mk_it));
+  TRY(batch_mask(B, list, gate, 1, mk_it, hit));
   TRY(bcap_end(B, nullptr));
   *per_iter = B.launches - a0;
   TRY(bcap_begin(B, g, std::vector<cudaGraphNode_t>{nit}));
   TRY(batch_ctl(B, C_AFTER_INNER, list, gate));
-  TRY(batch_vec<T>(B, V_CORRECT, list, gate, [](polar_ctx* c) {
+  TRY(batch_vec<T>(B, V_CORRECT, list, mk_branch, [](polar_ctx* c) {
     VecArgs<T> a = vargs<T>(c);
     a.v0 = kvecs<T>(c).d;
     a.w0 = c->X;
@@ -2018,10 +2040,21 @@ int batch_inner(BatchBuild& B, cudaGraph_t g, std::vector<cudaGraphNode_t> deps,
 }
 
 // The FP64 residual of the instances of `list` (r64 = e - S X with its max-norm reductions).
-int batch_resid(BatchBuild& B, const std::vector<const BInst*>& list, int gate) {
-  return batch_stencil<double>(B, M_RESID64, list, gate, [](polar_ctx* c) {
+int batch_resid(BatchBuild& B, const std::vector<const BInst*>& list, int mk) {
+  return batch_stencil<double>(B, M_RESID64, list, mk, [](polar_ctx* c) {
     return st_args<double>(c, c->X, c->r64, nullptr, c->e);
   });
+}
+
+// Masks after a refinement decision: the refining instances (and `cond` = any), then
+// those of each inner-solve branch.
+int batch_masks(BatchBuild& B, const std::vector<const BInst*>& all,
+                const std::vector<const BInst*>& krylov32, const std::vector<const BInst*>& krylov64,
+                const std::vector<const BInst*>& direct, CondHandle cond) {
+  TRY(batch_mask(B, all, G_REFINE, 0, MK_REF, cond));
+  TRY(batch_mask(B, krylov32, G_32, 0, MK_32, 0));
+  TRY(batch_mask(B, krylov64, G_64, 0, MK_64, 0));
+  return batch_mask(B, direct, G_64, 0, MK_DIR, 0);
 }
 
 // One theta-step of every instance of the batch as one graph:
@@ -2041,13 +2074,16 @@ int batch_step_graph(BatchBuild& B, cudaGraph_t g, const std::vector<BInst>& ins
     (i.mixed ? f32 : f64).push_back(&i);
   }
   polar_batch* b = B.b;
+  for (int k = 0; k < MK_COUNT; ++k)  // masks first: same arena offsets in both passes
+    B.mask[k] = const_cast<int*>(B.put(std::vector<int>(inst.size(), 0)));
   CondHandle hre = 0;
   TRY(bcond(B, g, &hre));
   const int64_t l0 = B.launches;
   TRY(bcap_begin(B, g, {}));
   TRY(batch_ctl(B, C_SCHED_BEGIN, all, G_ALL));
+  TRY(batch_mask(B, all, G_STEP, 0, MK_STEP, 0));
   for (int TK = 32; TK <= 256; TK <<= 1) {
-    std::vector<const BInst*> sub;
+    std::vector<BSlot> slots;
     std::vector<RhsArgs> args;
     for (const BInst* i : all) {
       polar_ctx* c = i->c;
@@ -2065,26 +2101,27 @@ int batch_step_graph(BatchBuild& B, cudaGraph_t g, const std::vector<BInst>& ins
       a.red = c->red();
       a.t = make_tiling(c->sh0());
       args.push_back(a);
-      sub.push_back(i);
+      slots.push_back(BSlot{i->idx, stencil_grid(c->sh0())});
     }
-    if (sub.empty()) continue;
-    const std::vector<BWork> w = grid_work(sub, [](const polar_ctx* c) { return stencil_grid(c->sh0()); });
+    if (slots.empty()) continue;
     const RhsArgs* A = B.put(args);
-    const BWork* W = B.put(w);
-    TRY(B.launch([&] { return launch_rhs_b(A, W, (int)w.size(), TK, G_STEP, B.cs); }));
+    const BSlot* S = B.put(slots);
+    const int gr = B.grid(slot_items(slots), 8);
+    const int* M = B.mask[MK_STEP];
+    TRY(B.launch([&] { return launch_rhs_b(A, S, (int)slots.size(), M, gr, TK, B.cs); }));
   }
-  TRY(batch_refresh<double>(B, f64, false, G_STEP));
-  TRY(batch_refresh<float>(B, f32, false, G_STEP));
-  TRY(batch_vec<double>(B, V_COPY, all, G_STEP, [](polar_ctx* c) {
+  TRY(batch_refresh<double>(B, f64, false, MK_STEP));
+  TRY(batch_refresh<float>(B, f32, false, MK_STEP));
+  TRY(batch_vec<double>(B, V_COPY, all, MK_STEP, [](polar_ctx* c) {
     VecArgs<double> a = vargs<double>(c);
     a.w0 = c->U;
     a.w1 = c->X;
     a.flag = 0;
     return a;
   }));
-  TRY(batch_resid(B, all, G_STEP));
+  TRY(batch_resid(B, all, MK_STEP));
   TRY(batch_ctl(B, C_DECIDE, all, G_STEP));
-  TRY(batch_any(B, all, G_REFINE, 0, hre));
+  TRY(batch_masks(B, all, krylov32, krylov64, direct, hre));
   std::vector<cudaGraphNode_t> sinks;
   TRY(bcap_end(B, &sinks));
   const int64_t l1 = B.launches;
@@ -2093,18 +2130,20 @@ int batch_step_graph(BatchBuild& B, cudaGraph_t g, const std::vector<BInst>& ins
   TRY(bwhile(B, g, sinks, hre, &nre, &bre));
   std::vector<cudaGraphNode_t> tail;
   int64_t it32 = 0, it64 = 0;
-  if (!krylov32.empty()) TRY(batch_inner<float>(B, bre, tail, krylov32, G_32, false, &tail, &it32));
+  if (!krylov32.empty())
+    TRY(batch_inner<float>(B, bre, tail, krylov32, G_32, MK_32, MK_IT32, false, &tail, &it32));
   if (!krylov64.empty())
-    TRY(batch_inner<double>(B, bre, tail, krylov64, G_64, !krylov32.empty(), &tail, &it64));
+    TRY(batch_inner<double>(B, bre, tail, krylov64, G_64, MK_64, MK_IT64, !krylov32.empty(), &tail,
+                            &it64));
   TRY(bcap_begin(B, bre, tail));
-  TRY(batch_direct(B, direct, G_64));
-  TRY(batch_resid(B, all, G_REFINE));
+  TRY(batch_direct(B, direct, MK_DIR, G_64));
+  TRY(batch_resid(B, all, MK_REF));
   TRY(batch_ctl(B, C_DECIDE, all, G_REFINE));
-  TRY(batch_any(B, all, G_REFINE, 0, hre));
+  TRY(batch_masks(B, all, krylov32, krylov64, direct, hre));
   TRY(bcap_end(B, nullptr));
   const int64_t l2 = B.launches;
   TRY(bcap_begin(B, g, std::vector<cudaGraphNode_t>{nre}));
-  TRY(batch_vec<double>(B, V_COPY, all, G_STEP, [](polar_ctx* c) {
+  TRY(batch_vec<double>(B, V_COPY, all, MK_STEP, [](polar_ctx* c) {
     VecArgs<double> a = vargs<double>(c);
     a.w0 = c->X;
     a.w1 = c->U;
@@ -2135,9 +2174,13 @@ int build_batch_graph(polar_batch* b) {
     polar_ctx* c = b->ctx[i];
     inst.push_back(BInst{c, i, c->precision == POLAR_MIXED && !c->direct_now, c->direct_now});
   }
+  int dev = 0, sms = 0;
+  CUDA_TRY(cudaGetDevice(&dev));
+  CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   BatchBuild plan;
   plan.b = b;
   plan.plan = true;
+  plan.sms = sms;
   TRY(batch_step_graph(plan, nullptr, inst));
   polar_ctx* c0 = b->ctx[0];
   if (plan.off > b->arena_bytes) {
@@ -2163,6 +2206,7 @@ int build_batch_graph(polar_batch* b) {
   cap.plan = false;
   cap.dev = static_cast<unsigned char*>(b->arena);
   cap.cs = b->cap;
+  cap.sms = sms;
   CUDA_TRY(cudaGraphCreate(&b->g, 0));
   const int rc = batch_step_graph(cap, b->g, inst);
   if (rc != POLAR_OK) {
@@ -2411,8 +2455,61 @@ int polar_advance(polar_ctx* c, int32_t nsteps, const double* t, double theta, c
   return advance(c, nsteps, t, theta, w, opts, stats);
 }
 
+int polar_solve_steady(polar_ctx* c, const double* w, const polar_solver_opts* opts,
+                       polar_step_stats* stats) {
+  if (!c) return fail(POLAR_EINVAL, "null context");
+  if (c->nsrc > 0 && !w) return fail(POLAR_EINVAL, "source weights required");
+  // one step of the theta-machinery with alpha = 0 and theta = 1: (V L) U = V f + Dirichlet
+  // terms, started from the current state; the time stays where it is
+  const double t0 = c->t;
+  const double t[2] = {t0, t0 + 1.0};
+  double ww[8];
+  for (int q = 0; q < c->nsrc; ++q) ww[q] = ww[c->nsrc + q] = w[q];
+  c->steady = true;
+  const int rc = advance(c, 1, t, 1.0, c->nsrc ? ww : nullptr, opts, stats);
+  c->steady = false;
+  c->t = t0;
+  return rc;
+}
+
+int polar_face_drift(polar_ctx* c, double mobility, const double* g, double* v_rface,
+                     double* v_tface, int32_t memory) {
+  if (!c || !g || !v_rface || !v_tface) return fail(POLAR_EINVAL, "null argument");
+  if (!c->have_state) return fail(POLAR_ESTATE, "no state set");
+  if (memory != POLAR_HOST && memory != POLAR_DEVICE) return fail(POLAR_EINVAL, "bad memory flag");
+  if (!std::isfinite(mobility)) return fail(POLAR_EINVAL, "non-finite mobility");
+  CUDA_TRY(cudaSetDevice(c->device));
+  const int m = c->m, n = c->n;
+  if (!c->mesh_dev) {
+    TRY(dalloc(c, &c->mesh_dev, (size_t)m + 2 + 2 * (size_t)n));
+    CUDA_TRY(cudaStreamSynchronize(c->st));
+    std::vector<double> mesh(c->r);
+    mesh.insert(mesh.end(), c->theta.begin(), c->theta.end());
+    CUDA_TRY(cudaMemcpy(c->mesh_dev, mesh.data(), mesh.size() * sizeof(double),
+                        cudaMemcpyHostToDevice));
+  }
+  double* gdev = c->mesh_dev + m + 2 + n;
+  CUDA_TRY(cudaMemcpyAsync(gdev, g, n * sizeof(double),
+                           memory == POLAR_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                           c->st));
+  const size_t nr = (size_t)(m + 1) * n, nt = (size_t)m * n;
+  // the faces are written to the Krylov work vectors first (they hold nv >= (m+1) n doubles)
+  double* vr = memory == POLAR_DEVICE ? v_rface : c->kv64.r;
+  double* vt = memory == POLAR_DEVICE ? v_tface : c->kv64.s;
+  LAUNCH(launch_unpack(c->sh0(), c->U, nullptr, c->io, c->st));
+  LAUNCH(launch_face_drift(m, n, c->io, c->mesh_dev, c->mesh_dev + m + 2, gdev, mobility, vr, vt,
+                           c->st));
+  if (memory == POLAR_HOST) {
+    CUDA_TRY(cudaMemcpyAsync(v_rface, vr, nr * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+    CUDA_TRY(cudaMemcpyAsync(v_tface, vt, nt * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+  }
+  CUDA_TRY(cudaStreamSynchronize(c->st));
+  return POLAR_OK;
+}
+
 int polar_batch_create(polar_ctx* const* ctxs, int32_t count, void* stream, polar_batch** out) {
   if (!ctxs || !out || count <= 0) return fail(POLAR_EINVAL, "need count > 0 contexts");
+  if (count > kMaxSlots) return fail(POLAR_EINVAL, "at most 1024 contexts in a batch");
   *out = nullptr;
   int dev = -1;
   for (int i = 0; i < count; ++i) {

@@ -278,37 +278,34 @@ __global__ void k_pre_direct(KrylovScalars* ks) {
 }
 
 // batched forms (per-instance DirectArgs; gate and work list as the other batched kernels)
-__global__ void k_pre_direct_b(const BWork* W, int nwork, int gate) {
-  for (int it = blockIdx.x * blockDim.x + threadIdx.x; it < nwork; it += gridDim.x * blockDim.x) {
-    const BWork w = W[it];
-    if (!gate_pass(gate, w.ks, w.sp)) continue;
-    w.ks->iters = 0;
-    w.ks->done = 0;
+// batched forms (per-slot DirectArgs; see BSlot): the set-up per active slot, the transforms
+// over the slots' ring groups, the mode solves over their mode blocks
+__global__ void k_pre_direct_b(const BSlot* S, int nslots, const int* mask,
+                               KrylovScalars* const* ks) {
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < nslots; s += gridDim.x * blockDim.x) {
+    if (!mask[S[s].inst]) continue;
+    ks[s]->iters = 0;
+    ks[s]->done = 0;
   }
 }
 template <bool INVERSE>
-__global__ void __launch_bounds__(kFftThreads) k_dft_rings_b(const DirectArgs* A, const BWork* W,
-                                                             int nwork, int gate) {
-  for (int it = blockIdx.x; it < nwork; it += gridDim.x) {
-    const BWork w = W[it];
-    if (!gate_pass(gate, w.ks, w.sp)) continue;
-    const DirectArgs& a = A[w.inst];
+__global__ void __launch_bounds__(kFftThreads) k_dft_rings_b(const DirectArgs* A, const BSlot* S,
+                                                             int nslots, const int* mask) {
+  POLAR_BATCH_LOOP({
+    const DirectArgs& a = A[s];
     const Shape sh = a.sh;
     const FftPlan P = a.P;
-    dft_rings_body<INVERSE>(sh, P, a.b, a.Xr, a.Xi, a.x, w.vb);
+    dft_rings_body<INVERSE>(sh, P, a.b, a.Xr, a.Xi, a.x, vb);
     __syncthreads();  // the transform's shared memory is reused by the next item
-  }
+  })
 }
-__global__ void __launch_bounds__(128) k_modes_b(const DirectArgs* A, const BWork* W, int nwork,
-                                                 int gate) {
-  for (int it = blockIdx.x; it < nwork; it += gridDim.x) {
-    const BWork w = W[it];
-    if (!gate_pass(gate, w.ks, w.sp)) continue;
-    const DirectArgs& a = A[w.inst];
-    modes_body(a.R, a.P, a.par, a.b, a.x, a.Xr, a.Xi, a.cp, a.z, w.ks, w.vb);
-  }
+__global__ void __launch_bounds__(128) k_modes_b(const DirectArgs* A, const BSlot* S, int nslots,
+                                                 const int* mask, KrylovScalars* const* ks) {
+  POLAR_BATCH_LOOP({
+    const DirectArgs& a = A[s];
+    modes_body(a.R, a.P, a.par, a.b, a.x, a.Xr, a.Xi, a.cp, a.z, ks[s], vb);
+  })
 }
-
 
 // Transform of the chirp filter b (b_k = conj c_k for |k| < n, circularly), once per mesh.
 __global__ void __launch_bounds__(kFftThreads) k_chirp_filter(FftPlan P, double* bhr, double* bhi) {
@@ -412,9 +409,9 @@ int launch_direct_solve(const Shape& sh, const FftPlan& P, const SepRings& R, Pa
 }
 
 
-int launch_direct_b(const DirectArgs* A, const BWork* Wrings, int nrings, const BWork* Wmodes,
-                    int nmodes, const BWork* Wone, int count, size_t smem, int gate,
-                    cudaStream_t st) {
+int launch_direct_b(const DirectArgs* A, const BSlot* Srings, const BSlot* Smodes, int nslots,
+                    const int* mask, KrylovScalars* const* ks, int grid_rings, int grid_modes,
+                    size_t smem, cudaStream_t st) {
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(k_dft_rings_b<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -423,11 +420,10 @@ int launch_direct_b(const DirectArgs* A, const BWork* Wrings, int nrings, const 
                          (int)kFftSmemCap);
     attr = true;
   }
-  k_pre_direct_b<<<(count + 127) / 128, 128, 0, st>>>(Wone, count, gate);
-  const int gr = persistent_grid(nrings, 2), gm = persistent_grid(nmodes, 8);
-  k_dft_rings_b<false><<<gr, kFftThreads, smem, st>>>(A, Wrings, nrings, gate);
-  k_modes_b<<<gm, 128, 0, st>>>(A, Wmodes, nmodes, gate);
-  k_dft_rings_b<true><<<gr, kFftThreads, smem, st>>>(A, Wrings, nrings, gate);
+  k_pre_direct_b<<<(nslots + 127) / 128, 128, 0, st>>>(Srings, nslots, mask, ks);
+  k_dft_rings_b<false><<<grid_rings, kFftThreads, smem, st>>>(A, Srings, nslots, mask);
+  k_modes_b<<<grid_modes, 128, 0, st>>>(A, Smodes, nslots, mask, ks);
+  k_dft_rings_b<true><<<grid_rings, kFftThreads, smem, st>>>(A, Srings, nslots, mask);
   return 4;
 }
 

@@ -49,12 +49,12 @@ void fft_host_tables(int n, int M, std::vector<double>& twr, std::vector<double>
                      std::vector<double>& lam);
 // Bhat = FFT_M(chirp filter), once per mesh (Bluestein plans only).
 int launch_chirp_filter(const FftPlan& P, double* bhr, double* bhi, cudaStream_t st);
-// Batched direct solves of `count` instances: work lists for the ring transforms (one
-// entry per ring group), the mode solves (per 128 modes) and the per-instance set-up
-// (Wone[i] for instance i); smem: the largest transform's shared memory.
-int launch_direct_b(const DirectArgs* A, const BWork* Wrings, int nrings, const BWork* Wmodes,
-                    int nmodes, const BWork* Wone, int count, size_t smem, int gate,
-                    cudaStream_t st);
+// Batched direct solves over `nslots` slots (see BSlot): Srings gives each slot's ring-group
+// count, Smodes its mode-block count (128 modes each); ks[s] the slot's solver scalars;
+// smem: the largest transform's shared memory.
+int launch_direct_b(const DirectArgs* A, const BSlot* Srings, const BSlot* Smodes, int nslots,
+                    const int* mask, KrylovScalars* const* ks, int grid_rings, int grid_modes,
+                    size_t smem, cudaStream_t st);
 // x = S^{-1} b for the separable S = alpha V + beta V L (split layout, FP64).  Work
 // arrays: Xr, Xi, cp of m * nh doubles, z of m.  Sets ks->iters = 0, ks->done = 1.
 int launch_direct_solve(const Shape& sh, const FftPlan& P, const SepRings& R, Params par,

@@ -158,16 +158,70 @@ struct StepParams {
 using CondHandle = unsigned long long;
 
 // ---- batched execution (many instances, one launch per kernel class and phase)
-// A block of a batched launch works as block `vb` of the `vg`-block grid that instance
-// `inst`'s own launch would have used, so every instance computes exactly what it computes
-// alone (same partition of its points, same reduction order).  `aux` carries a launch-
-// specific index (the first line of a ring-solve block).  The gate says which instances a
-// launch serves at this point of the step; the others' blocks return at once.
-struct BWork {
-  int inst, vb, vg, aux;
-  KrylovScalars* ks;
-  const StepParams* sp;
+// A batched launch serves a list of slots, one per instance it covers: slot s works on
+// argument table entry s, instance `inst` of the batch, whose own launch would use a grid of
+// vg blocks.  Which instances are active is read from a mask (one int per batch instance)
+// that small kernels write between launches -- at the start of a step, after each
+// refinement decision, after each Krylov iteration -- and that no kernel changes while a
+// launch reads it.  Every block of a launch therefore derives the same list of work items
+// (the active slots' virtual blocks, in slot order) and takes items blockIdx.x,
+// blockIdx.x + gridDim.x, ...: item g is block vb of the instance's own grid, so the
+// instance computes exactly what it computes alone (same partition, same reduction order).
+struct BSlot {
+  int inst;  // instance of the batch (position in the masks)
+  int vg;    // blocks of the instance's own launch
 };
+constexpr int kMaxSlots = 1024;  // slots of one batched launch
+
+// Prefix sums of the active slots' block counts in shared memory `pre` (nslots + 1
+// entries); returns the number of work items.  All threads of the block call it.
+__device__ __forceinline__ int batch_prefix(const BSlot* S, int nslots, const int* mask, int* pre) {
+  const int nt = blockDim.x * blockDim.y * blockDim.z;
+  const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
+  for (int s = tid; s < nslots; s += nt) pre[s + 1] = mask[S[s].inst] ? S[s].vg : 0;
+  __syncthreads();
+  if (tid < 32) {
+    // lane l sums slots [l c, (l + 1) c), a warp scan of the chunk sums, then the prefixes
+    const int c = (nslots + 31) / 32, s0 = tid * c, s1 = min(nslots, s0 + c);
+    int sum = 0;
+    for (int s = s0; s < s1; ++s) sum += pre[s + 1];
+    int inc = sum;
+    for (int off = 1; off < 32; off <<= 1) {
+      const int o = __shfl_up_sync(0xffffffffu, inc, off);
+      if (tid >= off) inc += o;
+    }
+    int run = inc - sum;
+    if (tid == 0) pre[0] = 0;
+    for (int s = s0; s < s1; ++s) {
+      run += pre[s + 1];
+      pre[s + 1] = run;
+    }
+  }
+  __syncthreads();
+  return pre[nslots];
+}
+// slot of work item g: the last s with pre[s] <= g
+__device__ __forceinline__ int batch_slot(const int* pre, int nslots, int g) {
+  int lo = 0, hi = nslots - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (pre[mid] <= g) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+// Work-item loop of a batched kernel (see BSlot): s is the slot, vb / vg the virtual block
+// of the instance's own grid.
+#define POLAR_BATCH_LOOP(...)                                          \
+  __shared__ int pre_[kMaxSlots + 1];                                  \
+  const int total_ = batch_prefix(S, nslots, mask, pre_);              \
+  for (int g_ = blockIdx.x; g_ < total_; g_ += gridDim.x) {            \
+    const int s = batch_slot(pre_, nslots, g_);                        \
+    const int vb = g_ - pre_[s], vg = S[s].vg;                         \
+    __VA_ARGS__;                                                       \
+  }
+
 enum {
   G_ALL = 0,     // every instance
   G_STEP = 1,    // instances running this step (not halted by an earlier failure)
@@ -183,7 +237,7 @@ struct CtlArgs {
   StepParams* sp;           // its current step's parameters
   StepOut* out;             // its per-step results
   KrylovScalars* ks;
-  int tolerant;             // after an inner solve: a non-finite FP32 solve does not fail
+  int inst;                 // position in the batch (and in its masks)
   int pad;
 };
 
@@ -414,41 +468,45 @@ int launch_coarsest(const LevelView<T>& L, const T* b, T* x, Params p, const int
 
 
 // ----------------------------------------------------------------- batched launchers
-// grid of a persistent batched launch: per_sm blocks per SM, at most nwork
+// Each launches `grid` blocks over the slots S[0, nslots) with per-slot arguments A (see
+// BSlot); the active instances are those with mask[inst] != 0.
 int persistent_grid(int nwork, int per_sm);
-// Each launches nwork blocks; block b works as W[b] says (instance, virtual block) and
-// returns at once unless its instance passes `gate`.  Per-instance arguments in A.
 template <typename T>
-int launch_stencil_b(int mode, const StArgs<T>* A, const BWork* W, int nwork, int TK, int gate,
-                     cudaStream_t st);
-int launch_rhs_b(const RhsArgs* A, const BWork* W, int nwork, int TK, int gate, cudaStream_t st);
+int launch_stencil_b(int mode, const StArgs<T>* A, const BSlot* S, int nslots, const int* mask,
+                     int grid, int TK, cudaStream_t st);
+int launch_rhs_b(const RhsArgs* A, const BSlot* S, int nslots, const int* mask, int grid, int TK,
+                 cudaStream_t st);
 enum { V_BICG_INIT, V_BICG_S, V_BICG_UPDATE, V_BICG_P, V_CG_RHO, V_CG_P, V_CG_UPDATE,
        V_SCALE_CAST, V_CORRECT, V_COPY };
 template <typename T>
-int launch_vec_b(int kind, const VecArgs<T>* A, const BWork* W, int nwork, int gate,
-                 cudaStream_t st);
+int launch_vec_b(int kind, const VecArgs<T>* A, const BSlot* S, int nslots, const int* mask,
+                 int grid, cudaStream_t st);
 enum { C_SCHED_BEGIN, C_DECIDE, C_AFTER_INNER, C_SCHED_END, C_SCHED_NEXT };
+// one thread per instance of A (count of them); the gate is read live (G_*)
 int launch_ctl_b(int kind, const CtlArgs* A, int count, int gate, cudaStream_t st);
-// sets `cond` to whether any of the `count` instances passes `gate` (and, with
-// need_running, still iterates: done == 0)
-int launch_any_b(const CtlArgs* A, int count, int gate, int need_running, CondHandle cond,
-                 cudaStream_t st);
+// mask[A[k].inst] = gate passes (and, with need_running, done == 0) for the count
+// instances of A; `cond` (if any) = whether any passes
+int launch_mask_b(const CtlArgs* A, int count, int gate, int need_running, int* mask,
+                  CondHandle cond, cudaStream_t st);
 template <typename T>
-int launch_refresh_b(const RefreshArgs* A, const BWork* W, int nwork, int gate, cudaStream_t st);
+int launch_refresh_b(const RefreshArgs* A, const BSlot* S, int nslots, const int* mask, int grid,
+                     cudaStream_t st);
 template <typename T>
-int launch_ring_b(const RingShape& s, const RingArgs<T>* A, const BWork* W, int nwork, int gate,
-                  cudaStream_t st);
+int launch_ring_b(const RingShape& s, const RingArgs<T>* A, const BSlot* S, int nslots,
+                  const int* mask, int grid, cudaStream_t st);
 template <typename T>
-int launch_restrict_b(const RestrictArgs<T>* A, const BWork* W, int nwork, int gate,
-                      cudaStream_t st);
+int launch_restrict_b(const RestrictArgs<T>* A, const BSlot* S, int nslots, const int* mask,
+                      int grid, cudaStream_t st);
 // coarsest-level solve (schur = 0) or its per-step Schur data (schur = 1), one CTA per
 // instance of the (P, TW) shape coarsest_shape gives for its n
 template <typename T>
-int launch_coarsest_b(int P, int TW, int schur, const CoarsestArgs<T>* A, const BWork* W,
-                      int nwork, int gate, cudaStream_t st);
+int launch_coarsest_b(int P, int TW, int schur, const CoarsestArgs<T>* A, const BSlot* S,
+                      int nslots, const int* mask, int grid, cudaStream_t st);
 template <typename T>
 void coarsest_shape(int n, int* P, int* TW);
-int launch_stamp_b(const BWork* W, double* const* stamps, int nwork, int gate, cudaStream_t st);
+// stamps[s] = (alpha, beta) of sps[s] for the active slots
+int launch_stamp_b(const BSlot* S, int nslots, const int* mask, double* const* stamps,
+                   const StepParams* const* sps, cudaStream_t st);
 // refresh arguments of one context's levels (as launch_refresh builds them); *nblocks:
 // the refresh grid of that context
 template <typename T>
@@ -505,6 +563,10 @@ int launch_correct(size_t nv, double* x, const T* d, cudaStream_t st, Reduce red
 int launch_copy(size_t n, const double* a, double* b, cudaStream_t st, Reduce red);
 int launch_to_float(size_t n, const double* a, float* b, cudaStream_t st);
 int launch_check_finite(size_t n, const double* a, cudaStream_t st, Reduce red);
+// v = -mobility grad u at the radial ((m+1) n) and angular (m n) faces, u in the interface
+// layout, r (m+2) and theta (n) the mesh, g (n) the values on r = 1
+int launch_face_drift(int m, int n, const double* u, const double* r, const double* th,
+                      const double* g, double mobility, double* vr, double* vt, cudaStream_t st);
 
 // interface layout (origin, then radial lines j = 0..n-1 of m values) <-> split layout;
 // `scale` (nullable, split layout) multiplies on the way in, `div` divides on the way out

@@ -265,17 +265,13 @@ template <typename T, int MODE>
 __global__ void __launch_bounds__(256) k_stencil(StArgs<T> a) {
   stencil_body<T, MODE>(a, blockIdx.x, gridDim.x);
 }
-// Batched kernels are persistent: a grid sized to fill the GPU walks the work list, and
-// items of instances the gate masks cost one load (late in a Krylov loop most are masked).
 template <typename T, int MODE>
-__global__ void __launch_bounds__(256) k_stencil_b(const StArgs<T>* A, const BWork* W, int nwork,
-                                                   int gate) {
-  for (int it = blockIdx.x; it < nwork; it += gridDim.x) {
-    const BWork w = W[it];
-    if (!gate_pass(gate, w.ks, w.sp)) continue;
-    const StArgs<T> a = A[w.inst];
-    stencil_body<T, MODE>(a, w.vb, w.vg);
-  }
+__global__ void __launch_bounds__(256) k_stencil_b(const StArgs<T>* A, const BSlot* S, int nslots,
+                                                   const int* mask) {
+  POLAR_BATCH_LOOP({
+    const StArgs<T> a = A[s];
+    stencil_body<T, MODE>(a, vb, vg);
+  })
 }
 
 template <typename T, int MODE>
@@ -375,14 +371,12 @@ __device__ __forceinline__ void rhs_body(const RhsArgs& a, int vb, int vg) {
 }
 
 __global__ void __launch_bounds__(256) k_rhs(RhsArgs a) { rhs_body(a, blockIdx.x, gridDim.x); }
-__global__ void __launch_bounds__(256) k_rhs_b(const RhsArgs* A, const BWork* W, int nwork,
-                                               int gate) {
-  for (int it = blockIdx.x; it < nwork; it += gridDim.x) {
-    const BWork w = W[it];
-    if (!gate_pass(gate, w.ks, w.sp)) continue;
-    const RhsArgs a = A[w.inst];
-    rhs_body(a, w.vb, w.vg);
-  }
+__global__ void __launch_bounds__(256) k_rhs_b(const RhsArgs* A, const BSlot* S, int nslots,
+                                               const int* mask) {
+  POLAR_BATCH_LOOP({
+    const RhsArgs a = A[s];
+    rhs_body(a, vb, vg);
+  })
 }
 
 int launch_rhs(const LevelView<double>& L, const StepParams* sp, const double* u, int nsrc,
@@ -416,14 +410,12 @@ __device__ __forceinline__ void set_cond(CondHandle cond, bool value) {
 // Batched wrapper of a vector-kernel body: block w.vb of instance w.inst's own grid.
 #define POLAR_VEC_BATCHED(NAME, BODY)                                                   \
   template <typename T>                                                                \
-  __global__ void __launch_bounds__(kVT) NAME(const VecArgs<T>* A, const BWork* W,     \
-                                              int nwork, int gate) {                   \
-    for (int it = blockIdx.x; it < nwork; it += gridDim.x) {                           \
-      const BWork w = W[it];                                                           \
-      if (!gate_pass(gate, w.ks, w.sp)) continue;                                      \
-      const VecArgs<T> a = A[w.inst];                                                  \
-      BODY<T>(a, w.vb, w.vg);                                                          \
-    }                                                                                  \
+  __global__ void __launch_bounds__(kVT) NAME(const VecArgs<T>* A, const BSlot* S,     \
+                                              int nslots, const int* mask) {           \
+    POLAR_BATCH_LOOP({                                                                 \
+      const VecArgs<T> a = A[s];                                                       \
+      BODY<T>(a, vb, vg);                                                              \
+    })                                                                                 \
   }                                                                                    \
   template <typename T>                                                                \
   __global__ void __launch_bounds__(kVT) NAME##_lone(VecArgs<T> a) {                   \
@@ -1000,16 +992,18 @@ __global__ void k_sched_end_b(const CtlArgs* A, int gate) {
   if (ks->failed) ks->halt = 1;
 }
 __global__ void k_sched_next_b(const CtlArgs* A) { *A[blockIdx.x].kstep_w += 1; }
-// iteration loop of a gate's instances: "continue" while any of them is still iterating
-// (refinement loop: while any is still refining)
-__global__ void k_any_b(const CtlArgs* A, int count, int gate, int need_running,
-                        CondHandle cond) {
+// Active-instance mask of a list (one thread block): mask[A[k].inst] = the gate passes
+// (and, with need_running, the instance's Krylov solve still runs); `cond` = any passes.
+__global__ void k_mask_b(const CtlArgs* A, int count, int gate, int need_running, int* mask,
+                         CondHandle cond) {
   __shared__ int any;
   if (threadIdx.x == 0) any = 0;
   __syncthreads();
   for (int i = threadIdx.x; i < count; i += blockDim.x) {
     const CtlArgs& a = A[i];
-    if (gate_pass(gate, a.ks, a.sp) && (!need_running || a.ks->done == 0)) any = 1;
+    const int on = gate_pass(gate, a.ks, a.sp) && (!need_running || a.ks->done == 0);
+    mask[a.inst] = on;
+    if (on) any = 1;
   }
   __syncthreads();
   if (threadIdx.x == 0) set_cond(cond, any != 0);
@@ -1046,6 +1040,38 @@ __device__ __forceinline__ void correct_body(const VecArgs<T>& a, int vb, int vg
 POLAR_VEC_BATCHED(k_copy_b, copy_if_body_t)
 POLAR_VEC_BATCHED(k_scale_cast_b, scale_cast_body)
 POLAR_VEC_BATCHED(k_correct_b, correct_body)
+
+// ------------------------------------------------------------------ face fields
+// v = -mobility grad u at the faces of the scheme (u in the interface layout): radial face
+// (i+1/2, j), i = 0..m, at j (m+1) + i:  -mobility (u_{i+1,j} - u_{i,j}) / h_{i+1} with
+// u_{0,j} the origin and u_{m+1,j} = g_j;  angular face (i, j+1/2), i = 1..m, at j m + i - 1:
+// -mobility (u_{i,j+1} - u_{i,j}) / (r_i mu_{j+1}), mu_n = 2 pi + theta_0 - theta_{n-1}.
+__global__ void k_face_drift(int m, int n, const double* u, const double* r, const double* th,
+                             const double* g, double mobility, double* vr, double* vt) {
+  const size_t nr = (size_t)(m + 1) * n, nt = (size_t)m * n;
+  for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < nr + nt;
+       q += (size_t)gridDim.x * blockDim.x) {
+    if (q < nr) {
+      const int j = (int)(q / (m + 1)), i = (int)(q - (size_t)j * (m + 1));
+      const double uin = (i == 0) ? u[0] : u[1 + (size_t)j * m + (i - 1)];
+      const double uout = (i == m) ? g[j] : u[1 + (size_t)j * m + i];
+      vr[q] = -mobility * (uout - uin) / (r[i + 1] - r[i]);
+    } else {
+      const size_t t = q - nr;
+      const int j = (int)(t / m), i = (int)(t - (size_t)j * m) + 1;
+      const int jn = (j + 1 < n) ? j + 1 : 0;
+      const double mu = (j + 1 < n) ? th[j + 1] - th[j] : 6.283185307179586 + th[0] - th[n - 1];
+      const double ua = u[1 + (size_t)j * m + (i - 1)], ub = u[1 + (size_t)jn * m + (i - 1)];
+      vt[t] = -mobility * (ub - ua) / (r[i] * mu);
+    }
+  }
+}
+int launch_face_drift(int m, int n, const double* u, const double* r, const double* th,
+                      const double* g, double mobility, double* vr, double* vt, cudaStream_t st) {
+  const size_t work = (size_t)(2 * m + 1) * n;
+  k_face_drift<<<grid_for(work, kVT), kVT, 0, st>>>(m, n, u, r, th, g, mobility, vr, vt);
+  return 1;
+}
 
 // ------------------------------------------------------------------ layout conversion
 // interface index q = 1 + j m + (i - 1) <-> split index sh.at(i, j); q = 0 is the origin
@@ -1101,47 +1127,46 @@ int persistent_grid(int nwork, int per_sm) {
   return std::max(1, std::min(nwork, sms * per_sm));
 }
 template <typename T>
-int launch_stencil_b(int mode, const StArgs<T>* A, const BWork* W, int nwork, int TK, int gate,
-                     cudaStream_t st) {
-  if (nwork <= 0) return 0;
+int launch_stencil_b(int mode, const StArgs<T>* A, const BSlot* S, int nslots, const int* mask,
+                     int grid, int TK, cudaStream_t st) {
+  if (nslots <= 0) return 0;
   const dim3 block(TK, 256 / TK);
-  const int g = persistent_grid(nwork, 8);
   switch (mode) {
-    case M_APPLY: k_stencil_b<T, M_APPLY><<<g, block, 0, st>>>(A, W, nwork, gate); break;
-    case M_DOTV: k_stencil_b<T, M_DOTV><<<g, block, 0, st>>>(A, W, nwork, gate); break;
-    case M_DOTT: k_stencil_b<T, M_DOTT><<<g, block, 0, st>>>(A, W, nwork, gate); break;
+    case M_APPLY: k_stencil_b<T, M_APPLY><<<grid, block, 0, st>>>(A, S, nslots, mask); break;
+    case M_DOTV: k_stencil_b<T, M_DOTV><<<grid, block, 0, st>>>(A, S, nslots, mask); break;
+    case M_DOTT: k_stencil_b<T, M_DOTT><<<grid, block, 0, st>>>(A, S, nslots, mask); break;
     default:
       if constexpr (sizeof(T) == 8) {
-        k_stencil_b<T, M_RESID64><<<g, block, 0, st>>>(A, W, nwork, gate);
+        k_stencil_b<T, M_RESID64><<<grid, block, 0, st>>>(A, S, nslots, mask);
       } else {
         return -1;
       }
   }
   return 1;
 }
-int launch_rhs_b(const RhsArgs* A, const BWork* W, int nwork, int TK, int gate, cudaStream_t st) {
-  if (nwork <= 0) return 0;
-  k_rhs_b<<<persistent_grid(nwork, 8), dim3(TK, 256 / TK), 0, st>>>(A, W, nwork, gate);
+int launch_rhs_b(const RhsArgs* A, const BSlot* S, int nslots, const int* mask, int grid, int TK,
+                 cudaStream_t st) {
+  if (nslots <= 0) return 0;
+  k_rhs_b<<<grid, dim3(TK, 256 / TK), 0, st>>>(A, S, nslots, mask);
   return 1;
 }
 template <typename T>
-int launch_vec_b(int kind, const VecArgs<T>* A, const BWork* W, int nwork, int gate,
-                 cudaStream_t st) {
-  if (nwork <= 0) return 0;
-  const int g = persistent_grid(nwork, 8);
+int launch_vec_b(int kind, const VecArgs<T>* A, const BSlot* S, int nslots, const int* mask,
+                 int grid, cudaStream_t st) {
+  if (nslots <= 0) return 0;
   switch (kind) {
-    case V_BICG_INIT: k_bicg_init<T><<<g, kVT, 0, st>>>(A, W, nwork, gate); break;
-    case V_BICG_S: k_bicg_s<T><<<g, kVT, 0, st>>>(A, W, nwork, gate); break;
-    case V_BICG_UPDATE: k_bicg_update<T><<<g, kVT, 0, st>>>(A, W, nwork, gate); break;
-    case V_BICG_P: k_bicg_p<T><<<g, kVT, 0, st>>>(A, W, nwork, gate); break;
-    case V_CG_RHO: k_cg_rho<T><<<g, kVT, 0, st>>>(A, W, nwork, gate); break;
-    case V_CG_P: k_cg_p<T><<<g, kVT, 0, st>>>(A, W, nwork, gate); break;
-    case V_CG_UPDATE: k_cg_update<T><<<g, kVT, 0, st>>>(A, W, nwork, gate); break;
-    case V_SCALE_CAST: k_scale_cast_b<T><<<g, kVT, 0, st>>>(A, W, nwork, gate); break;
-    case V_CORRECT: k_correct_b<T><<<g, kVT, 0, st>>>(A, W, nwork, gate); break;
+    case V_BICG_INIT: k_bicg_init<T><<<grid, kVT, 0, st>>>(A, S, nslots, mask); break;
+    case V_BICG_S: k_bicg_s<T><<<grid, kVT, 0, st>>>(A, S, nslots, mask); break;
+    case V_BICG_UPDATE: k_bicg_update<T><<<grid, kVT, 0, st>>>(A, S, nslots, mask); break;
+    case V_BICG_P: k_bicg_p<T><<<grid, kVT, 0, st>>>(A, S, nslots, mask); break;
+    case V_CG_RHO: k_cg_rho<T><<<grid, kVT, 0, st>>>(A, S, nslots, mask); break;
+    case V_CG_P: k_cg_p<T><<<grid, kVT, 0, st>>>(A, S, nslots, mask); break;
+    case V_CG_UPDATE: k_cg_update<T><<<grid, kVT, 0, st>>>(A, S, nslots, mask); break;
+    case V_SCALE_CAST: k_scale_cast_b<T><<<grid, kVT, 0, st>>>(A, S, nslots, mask); break;
+    case V_CORRECT: k_correct_b<T><<<grid, kVT, 0, st>>>(A, S, nslots, mask); break;
     default:
       if constexpr (sizeof(T) == 8) {
-        k_copy_b<T><<<g, kVT, 0, st>>>(A, W, nwork, gate);
+        k_copy_b<T><<<grid, kVT, 0, st>>>(A, S, nslots, mask);
       } else {
         return -1;
       }
@@ -1159,9 +1184,9 @@ int launch_ctl_b(int kind, const CtlArgs* A, int count, int gate, cudaStream_t s
   }
   return 1;
 }
-int launch_any_b(const CtlArgs* A, int count, int gate, int need_running, CondHandle cond,
-                 cudaStream_t st) {
-  k_any_b<<<1, 256, 0, st>>>(A, count, gate, need_running, cond);
+int launch_mask_b(const CtlArgs* A, int count, int gate, int need_running, int* mask,
+                  CondHandle cond, cudaStream_t st) {
+  k_mask_b<<<1, 256, 0, st>>>(A, count, gate, need_running, mask, cond);
   return 1;
 }
 
@@ -1184,9 +1209,10 @@ int launch_any_b(const CtlArgs* A, int count, int gate, int need_running, CondHa
                                    CondHandle, cudaStream_t, Reduce);                          \
   template int launch_scale_cast<T>(size_t, const double*, T*, cudaStream_t, Reduce);          \
   template int launch_correct<T>(size_t, double*, const T*, cudaStream_t, Reduce);          \
-  template int launch_stencil_b<T>(int, const StArgs<T>*, const BWork*, int, int, int,      \
-                                   cudaStream_t);                                           \
-  template int launch_vec_b<T>(int, const VecArgs<T>*, const BWork*, int, int, cudaStream_t);
+  template int launch_stencil_b<T>(int, const StArgs<T>*, const BSlot*, int, const int*, int, \
+                                   int, cudaStream_t);                                      \
+  template int launch_vec_b<T>(int, const VecArgs<T>*, const BSlot*, int, const int*, int,    \
+                               cudaStream_t);
 
 POLAR_INST(float)
 POLAR_INST(double)

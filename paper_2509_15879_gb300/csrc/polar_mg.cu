@@ -303,16 +303,14 @@ __device__ __forceinline__ void stage_args(A& dst, const A& src) {
 }
 
 template <typename T>
-__global__ void __launch_bounds__(RF * TF) k_refresh_b(const RefreshArgs* AA, const BWork* W,
-                                                     int nwork, int gate) {
+__global__ void __launch_bounds__(RF * TF) k_refresh_b(const RefreshArgs* AA, const BSlot* S,
+                                                     int nslots, const int* mask) {
   __shared__ RefreshArgs sA;
-  for (int it = blockIdx.x; it < nwork; it += gridDim.x) {
-    const BWork w = W[it];
-    if (!gate_pass(gate, w.ks, w.sp)) continue;
-    stage_args(sA, AA[w.inst]);
-    refresh_body<T>(sA, w.vb);
+  POLAR_BATCH_LOOP({
+    stage_args(sA, AA[s]);
+    refresh_body<T>(sA, vb);
     __syncthreads();  // sA is restaged for the next item
-  }
+  })
 }
 
 template <typename T>
@@ -325,12 +323,12 @@ __global__ void k_stamp(const StepParams* sp, double* stamp) {
   stamp[1] = sp->beta;
 }
 // batched: one thread per instance (w.inst), stamp array given per instance
-__global__ void k_stamp_b(const BWork* W, double* const* stamps, int nwork, int gate) {
-  for (int it = blockIdx.x * blockDim.x + threadIdx.x; it < nwork; it += gridDim.x * blockDim.x) {
-    const BWork w = W[it];
-    if (!gate_pass(gate, w.ks, w.sp)) continue;
-    stamps[w.inst][0] = w.sp->alpha;
-    stamps[w.inst][1] = w.sp->beta;
+__global__ void k_stamp_b(const BSlot* S, int nslots, const int* mask, double* const* stamps,
+                          const StepParams* const* sps) {
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < nslots; s += gridDim.x * blockDim.x) {
+    if (!mask[S[s].inst]) continue;
+    stamps[s][0] = sps[s]->alpha;
+    stamps[s][1] = sps[s]->beta;
   }
 }
 
@@ -808,30 +806,29 @@ __global__ void __launch_bounds__(512, 2) k_ring_staged(RingArgs<T> a) {
 // the instance's `done` flag are read before the cluster's first barrier; every CTA of a
 // cluster reads the same work item, so a cluster returns as a whole.
 template <typename T, int P, bool STAGED>
-__device__ __forceinline__ void ring_batched(const RingArgs<T>* A, const BWork* W, int nwork,
-                                             int gate) {
+__device__ __forceinline__ void ring_batched(const RingArgs<T>* A, const BSlot* S, int nslots,
+                                             const int* mask) {
+  // every CTA of a cluster (one column, same blockIdx.x) takes the same work items
   __shared__ RingArgs<T> sa;
-  for (int it = blockIdx.x; it < nwork; it += gridDim.x) {
-    const BWork w = W[it];
-    if (!gate_pass(gate, w.ks, w.sp)) continue;
-    stage_args(sa, A[w.inst]);
+  POLAR_BATCH_LOOP({
+    stage_args(sa, A[s]);
     if (!(sa.done && *sa.done)) {
       const T beta = (T)sa.par[1];
-      ring_body<T, P, STAGED>(sa, beta, w.aux);
-      if (sa.parity == 0 && w.vb == 0 && blockIdx.y == 0) relax_origin(sa, beta);
+      ring_body<T, P, STAGED>(sa, beta, vb * (int)blockDim.x);
+      if (sa.parity == 0 && vb == 0 && blockIdx.y == 0) relax_origin(sa, beta);
     }
     __syncthreads();  // sa is restaged for the next item
-  }
+  })
 }
 template <typename T, int P>
-__global__ void __launch_bounds__(512) k_ring_b(const RingArgs<T>* A, const BWork* W, int nwork,
-                                                int gate) {
-  ring_batched<T, P, false>(A, W, nwork, gate);
+__global__ void __launch_bounds__(512) k_ring_b(const RingArgs<T>* A, const BSlot* S, int nslots,
+                                                const int* mask) {
+  ring_batched<T, P, false>(A, S, nslots, mask);
 }
 template <typename T, int P>
-__global__ void __launch_bounds__(512, 2) k_ring_staged_b(const RingArgs<T>* A, const BWork* W,
-                                                         int nwork, int gate) {
-  ring_batched<T, P, true>(A, W, nwork, gate);
+__global__ void __launch_bounds__(512, 2) k_ring_staged_b(const RingArgs<T>* A, const BSlot* S,
+                                                         int nslots, const int* mask) {
+  ring_batched<T, P, true>(A, S, nslots, mask);
 }
 
 // residual of the odd rings after the pre-smoothing sweep, restricted to the coarser
@@ -889,18 +886,17 @@ __global__ void __launch_bounds__(256) k_restrict(RestrictArgs<T> a) {
                 (size_t)gridDim.x * blockDim.x, blockIdx.x == 0);
 }
 template <typename T>
-__global__ void __launch_bounds__(256) k_restrict_b(const RestrictArgs<T>* A, const BWork* W,
-                                                    int nwork, int gate) {
-  for (int it = blockIdx.x; it < nwork; it += gridDim.x) {
-    const BWork w = W[it];
-    if (!gate_pass(gate, w.ks, w.sp)) continue;
-    const RestrictArgs<T> a = A[w.inst];
-    if (a.done && *a.done) continue;
-    const T beta = (T)a.par[1];
-    restrict_body(a, beta, w.vb * (size_t)blockDim.x + threadIdx.x, (size_t)w.vg * blockDim.x,
-                  w.vb == 0);
+__global__ void __launch_bounds__(256) k_restrict_b(const RestrictArgs<T>* A, const BSlot* S,
+                                                    int nslots, const int* mask) {
+  POLAR_BATCH_LOOP({
+    const RestrictArgs<T> a = A[s];
+    if (!(a.done && *a.done)) {
+      const T beta = (T)a.par[1];
+      restrict_body(a, beta, vb * (size_t)blockDim.x + threadIdx.x, (size_t)vg * blockDim.x,
+                    vb == 0);
+    }
     __syncthreads();  // the origin part's shared reduction buffer is reused
-  }
+  })
 }
 
 // coarsest level (origin + ring 1): y = T_1^{-1} b_1, x_0 = (b_0 - beta o.y) / denom,
@@ -947,16 +943,14 @@ __global__ void __launch_bounds__(512) k_coarsest(LevelView<T> L, const T* b, T*
 }
 // batched: one CTA per instance (w.inst), its coarsest level, right-hand side and solution
 template <typename T, int P>
-__global__ void __launch_bounds__(512) k_coarsest_b(const CoarsestArgs<T>* A, const BWork* W,
-                                                    int nwork, int gate) {
+__global__ void __launch_bounds__(512) k_coarsest_b(const CoarsestArgs<T>* A, const BSlot* S,
+                                                    int nslots, const int* mask) {
   __shared__ CoarsestArgs<T> sa;
-  for (int it = blockIdx.x; it < nwork; it += gridDim.x) {
-    const BWork w = W[it];
-    if (!gate_pass(gate, w.ks, w.sp)) continue;
-    stage_args(sa, A[w.inst]);
+  POLAR_BATCH_LOOP({
+    stage_args(sa, A[s]);
     if (!(sa.done && *sa.done)) coarsest_body<T, P>(sa.L, sa.b, sa.x, (T)sa.par[1]);
     __syncthreads();
-  }
+  })
 }
 
 // Schur data of the coarsest level (after k_refresh): z = T_1^{-1} (beta w_1) by a ring
@@ -995,16 +989,14 @@ __global__ void __launch_bounds__(512) k_schur(LevelView<T> L, const StepParams*
   schur_body<T, P>(L, sp, stamp);
 }
 template <typename T, int P>
-__global__ void __launch_bounds__(512) k_schur_b(const CoarsestArgs<T>* A, const BWork* W,
-                                                 int nwork, int gate) {
+__global__ void __launch_bounds__(512) k_schur_b(const CoarsestArgs<T>* A, const BSlot* S,
+                                                 int nslots, const int* mask) {
   __shared__ CoarsestArgs<T> sa;
-  for (int it = blockIdx.x; it < nwork; it += gridDim.x) {
-    const BWork w = W[it];
-    if (!gate_pass(gate, w.ks, w.sp)) continue;
-    stage_args(sa, A[w.inst]);
+  POLAR_BATCH_LOOP({
+    stage_args(sa, A[s]);
     schur_body<T, P>(sa.L, sa.sp, sa.stamp);
     __syncthreads();
-  }
+  })
 }
 
 // ---------------------------------------------------------------------------------
@@ -1182,23 +1174,20 @@ static int launch_schur(const LevelView<T>& L, const StepParams* sp, const doubl
 // batched launchers
 
 template <typename T>
-int launch_refresh_b(const RefreshArgs* A, const BWork* W, int nwork, int gate, cudaStream_t st) {
-  if (nwork <= 0) return 0;
-  k_refresh_b<T><<<persistent_grid(nwork, 2), dim3(RF, TF), 0, st>>>(A, W, nwork, gate);
+int launch_refresh_b(const RefreshArgs* A, const BSlot* S, int nslots, const int* mask, int grid,
+                     cudaStream_t st) {
+  if (nslots <= 0) return 0;
+  k_refresh_b<T><<<grid, dim3(RF, TF), 0, st>>>(A, S, nslots, mask);
   return 1;
 }
 
 template <typename T, int P>
-static int launch_ring_bp(const RingShape& s, const RingArgs<T>* A, const BWork* W, int nwork,
-                          int gate, cudaStream_t st) {
-  void (*kern)(const RingArgs<T>*, const BWork*, int, int) =
+static int launch_ring_bp(const RingShape& s, const RingArgs<T>* A, const BSlot* S, int nslots,
+                          const int* mask, int grid, cudaStream_t st) {
+  void (*kern)(const RingArgs<T>*, const BSlot*, int, const int*) =
       s.ST ? k_ring_staged_b<T, P> : k_ring_b<T, P>;
-  // persistent: CTA columns (clusters of CS CTAs) walk the line groups of all instances;
-  // enough columns for the SMs to hold a few CTAs each
-  const int per = std::max(1, 4 * 512 / (s.RW * s.TW));
-  const int cols = std::max(1, std::min(nwork, persistent_grid(nwork, per) / s.CS));
   if (s.CS == 1) {
-    kern<<<cols, dim3(s.RW, s.TW), ring_smem<T>(s), st>>>(A, W, nwork, gate);
+    kern<<<grid, dim3(s.RW, s.TW), ring_smem<T>(s), st>>>(A, S, nslots, mask);
     return 1;
   }
   if (s.CS > kMaxCluster) return -1;
@@ -1208,8 +1197,9 @@ static int launch_ring_bp(const RingShape& s, const RingArgs<T>* A, const BWork*
     cudaFuncSetAttribute(k_ring_staged_b<T, P>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     allowed = true;
   }
+  // grid columns are clusters of CS CTAs along y, each column taking the same work items
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(cols, s.CS, 1);
+  cfg.gridDim = dim3(grid, s.CS, 1);
   cfg.blockDim = dim3(s.RW, s.TW, 1);
   cfg.dynamicSmemBytes = ring_smem<T>(s);
   cfg.stream = st;
@@ -1220,26 +1210,26 @@ static int launch_ring_bp(const RingShape& s, const RingArgs<T>* A, const BWork*
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, kern, A, W, nwork, gate) == cudaSuccess ? 1 : -1;
+  return cudaLaunchKernelEx(&cfg, kern, A, S, nslots, mask) == cudaSuccess ? 1 : -1;
 }
 
 template <typename T>
-int launch_ring_b(const RingShape& s, const RingArgs<T>* A, const BWork* W, int nwork, int gate,
-                  cudaStream_t st) {
-  if (nwork <= 0) return 0;
+int launch_ring_b(const RingShape& s, const RingArgs<T>* A, const BSlot* S, int nslots,
+                  const int* mask, int grid, cudaStream_t st) {
+  if (nslots <= 0) return 0;
   switch (s.P) {
-    case 4: return launch_ring_bp<T, 4>(s, A, W, nwork, gate, st);
-    case 8: return launch_ring_bp<T, 8>(s, A, W, nwork, gate, st);
-    case 16: return launch_ring_bp<T, 16>(s, A, W, nwork, gate, st);
-    default: return launch_ring_bp<T, 32>(s, A, W, nwork, gate, st);
+    case 4: return launch_ring_bp<T, 4>(s, A, S, nslots, mask, grid, st);
+    case 8: return launch_ring_bp<T, 8>(s, A, S, nslots, mask, grid, st);
+    case 16: return launch_ring_bp<T, 16>(s, A, S, nslots, mask, grid, st);
+    default: return launch_ring_bp<T, 32>(s, A, S, nslots, mask, grid, st);
   }
 }
 
 template <typename T>
-int launch_restrict_b(const RestrictArgs<T>* A, const BWork* W, int nwork, int gate,
-                      cudaStream_t st) {
-  if (nwork <= 0) return 0;
-  k_restrict_b<T><<<persistent_grid(nwork, 8), 256, 0, st>>>(A, W, nwork, gate);
+int launch_restrict_b(const RestrictArgs<T>* A, const BSlot* S, int nslots, const int* mask,
+                      int grid, cudaStream_t st) {
+  if (nslots <= 0) return 0;
+  k_restrict_b<T><<<grid, 256, 0, st>>>(A, S, nslots, mask);
   return 1;
 }
 
@@ -1254,36 +1244,36 @@ void coarsest_shape(int n, int* P, int* TW) {
 }
 
 template <typename T>
-int launch_coarsest_b(int P, int TW, int schur, const CoarsestArgs<T>* A, const BWork* W,
-                      int nwork, int gate, cudaStream_t st) {
-  if (nwork <= 0) return 0;
+int launch_coarsest_b(int P, int TW, int schur, const CoarsestArgs<T>* A, const BSlot* S,
+                      int nslots, const int* mask, int grid, cudaStream_t st) {
+  if (nslots <= 0) return 0;
   RingShape s{};
   s.RW = 1;
   s.TW = TW;
   s.P = P;
   const size_t smem = ring_smem<T>(s);
   const dim3 block(1, TW);
-  const int g = persistent_grid(nwork, std::max(1, 1024 / TW));
   switch (P) {
     case 8:
-      if (schur) k_schur_b<T, 8><<<g, block, smem, st>>>(A, W, nwork, gate);
-      else k_coarsest_b<T, 8><<<g, block, smem, st>>>(A, W, nwork, gate);
+      if (schur) k_schur_b<T, 8><<<grid, block, smem, st>>>(A, S, nslots, mask);
+      else k_coarsest_b<T, 8><<<grid, block, smem, st>>>(A, S, nslots, mask);
       break;
     case 16:
-      if (schur) k_schur_b<T, 16><<<g, block, smem, st>>>(A, W, nwork, gate);
-      else k_coarsest_b<T, 16><<<g, block, smem, st>>>(A, W, nwork, gate);
+      if (schur) k_schur_b<T, 16><<<grid, block, smem, st>>>(A, S, nslots, mask);
+      else k_coarsest_b<T, 16><<<grid, block, smem, st>>>(A, S, nslots, mask);
       break;
     default:
-      if (schur) k_schur_b<T, 32><<<g, block, smem, st>>>(A, W, nwork, gate);
-      else k_coarsest_b<T, 32><<<g, block, smem, st>>>(A, W, nwork, gate);
+      if (schur) k_schur_b<T, 32><<<grid, block, smem, st>>>(A, S, nslots, mask);
+      else k_coarsest_b<T, 32><<<grid, block, smem, st>>>(A, S, nslots, mask);
       break;
   }
   return 1;
 }
 
-int launch_stamp_b(const BWork* W, double* const* stamps, int nwork, int gate, cudaStream_t st) {
-  if (nwork <= 0) return 0;
-  k_stamp_b<<<(nwork + 127) / 128, 128, 0, st>>>(W, stamps, nwork, gate);
+int launch_stamp_b(const BSlot* S, int nslots, const int* mask, double* const* stamps,
+                   const StepParams* const* sps, cudaStream_t st) {
+  if (nslots <= 0) return 0;
+  k_stamp_b<<<(nslots + 127) / 128, 128, 0, st>>>(S, nslots, mask, stamps, sps);
   return 1;
 }
 
@@ -1304,14 +1294,15 @@ int launch_stamp_b(const BWork* W, double* const* stamps, int nwork, int gate, c
                                   cudaStream_t);                                              \
   template RefreshArgs make_refresh_args<T>(const LevelView<double>*, LevelView<T>*, int,     \
                                             const StepParams*, double*, double*, int*);       \
-  template int launch_refresh_b<T>(const RefreshArgs*, const BWork*, int, int, cudaStream_t); \
-  template int launch_ring_b<T>(const RingShape&, const RingArgs<T>*, const BWork*, int, int,  \
-                                cudaStream_t);                                                \
-  template int launch_restrict_b<T>(const RestrictArgs<T>*, const BWork*, int, int,            \
-                                    cudaStream_t);                                            \
+  template int launch_refresh_b<T>(const RefreshArgs*, const BSlot*, int, const int*, int,    \
+                                   cudaStream_t);                                             \
+  template int launch_ring_b<T>(const RingShape&, const RingArgs<T>*, const BSlot*, int,       \
+                                const int*, int, cudaStream_t);                               \
+  template int launch_restrict_b<T>(const RestrictArgs<T>*, const BSlot*, int, const int*,     \
+                                    int, cudaStream_t);                                       \
   template void coarsest_shape<T>(int, int*, int*);                                           \
-  template int launch_coarsest_b<T>(int, int, int, const CoarsestArgs<T>*, const BWork*, int,  \
-                                    int, cudaStream_t);
+  template int launch_coarsest_b<T>(int, int, int, const CoarsestArgs<T>*, const BSlot*, int,  \
+                                    const int*, int, cudaStream_t);
 
 POLAR_MG_INST(float)
 POLAR_MG_INST(double)
