@@ -593,8 +593,9 @@ def run_native(args):
 def run_batch(args):
     """The 256-instance sweep: continuity equation on uneven adaptive meshes (m log-uniform
     in [64, 1024], n in [128, 2048], D amplitude in [0.2, 5], Peclet in [0.1, 20]), 500-level
-    time stretch each, advanced together: one CUDA graph per step in which each kernel class
-    runs once per phase over all instances.  value = sum of N_i x steps / device time."""
+    time stretch each, advanced together: one CUDA graph per step whose parallel branches
+    are up to 8 size-sorted groups, in each of which a kernel class runs once per phase over
+    the group's active instances.  value = sum of N_i x steps / device time."""
     import torch
     import polar_inputs as pi
     import paper_2509_15879_gb300 as P
@@ -673,8 +674,9 @@ def run_batch(args):
             "dtype": "f64" if precision == P.POLAR_FP64 else "f32+f64", "data": "synthetic",
             "config": {"workload": f"batched sweep: {count} continuity instances, m in [64, 1024], "
                                    f"n in [128, 2048], 500-level time stretch; one CUDA graph "
-                                   f"per step, each kernel class launched once per phase over "
-                                   f"all instances", "instances": len(probs),
+                                   f"per step of up to 8 size-sorted groups as parallel "
+                                   f"branches, each kernel class launched once per phase over "
+                                   f"a group's active instances", "instances": len(probs),
                        "sum_N": pts, "precision": args.precision,
                        "l2": "inputs larger than L2 (several GB of instance data)",
                        "parallelism": f"replicas x{world}"},

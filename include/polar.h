@@ -224,8 +224,10 @@ int polar_advance(polar_ctx* ctx, int32_t nsteps, const double* t, double theta,
  * schedule of nsteps steps: t[i] holds nsteps+1 levels of instance i (t[i][0] its current
  * time), theta[i] its implicit weight, w[i] its (nsteps+1) x nsrc source weights (w may be
  * NULL when no instance has sources).  One CUDA graph advances every instance by one step
- * and is launched nsteps times on `stream`: each kernel class of the step runs as one
- * launch per phase over the blocks of every active instance -- each instance keeps the
+ * and is launched nsteps times on `stream`.  The instances are sorted by size into up to
+ * 8 groups of about equal total points; each group's step is a parallel branch of the
+ * graph, in which each kernel class runs as one launch per phase over the blocks of every
+ * active instance of the group -- each instance keeps the
  * block partition of its own launches, so its result equals that of advancing it alone
  * bit for bit -- and the refinement and Krylov loops run while any instance still needs
  * them.  Per-instance masks, rewritten on the device wherever instances start or stop

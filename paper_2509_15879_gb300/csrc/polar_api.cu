@@ -95,8 +95,13 @@ struct polar_batch {
   std::vector<int64_t> gens;   // context generations the graph was captured with
   void* arena = nullptr;       // argument tables and work lists of the batched launches
   size_t arena_bytes = 0;
-  // kernels per batch step: fixed, per refinement sweep, per FP32 / FP64 Krylov iteration
-  int64_t kernels_fixed = 0, kernels_sweep = 0, kernels_iter32 = 0, kernels_iter64 = 0;
+  // groups of instances of similar size, each a parallel branch of the step graph, with
+  // its kernels per step: fixed, per refinement sweep, per FP32 / FP64 Krylov iteration
+  struct Group {
+    std::vector<int> members;
+    int64_t fixed = 0, sweep = 0, iter32 = 0, iter64 = 0;
+  };
+  std::vector<Group> groups;
   int64_t launches = 0;        // kernels launched by the batch's graphs
 };
 
@@ -2057,25 +2062,23 @@ int batch_masks(BatchBuild& B, const std::vector<const BInst*>& all,
   return batch_mask(B, direct, G_64, 0, MK_DIR, 0);
 }
 
-// One theta-step of every instance of the batch as one graph:
+// One theta-step of the instances of a group, appended to the step graph as a branch:
 //   schedule step -> right-hand sides, refreshes, X = U, residuals, decisions ->
 //   WHILE (any refining) { FP32 solves | FP64 solves | direct solves, residuals,
 //                          decisions } -> commit, results, next step.
-int batch_step_graph(BatchBuild& B, cudaGraph_t g, const std::vector<BInst>& inst) {
+int batch_group_step(BatchBuild& B, cudaGraph_t g, const std::vector<const BInst*>& members,
+                     polar_batch::Group* grp) {
   std::vector<const BInst*> all, krylov32, krylov64, direct, f64, f32;
-  for (const BInst& i : inst) {
-    all.push_back(&i);
-    if (i.direct) {
-      direct.push_back(&i);
+  for (const BInst* i : members) {
+    all.push_back(i);
+    if (i->direct) {
+      direct.push_back(i);
     } else {
-      krylov64.push_back(&i);           // FP64 instances and the mixed ones' FP64 solve
-      if (i.mixed) krylov32.push_back(&i);
+      krylov64.push_back(i);           // FP64 instances and the mixed ones' FP64 solve
+      if (i->mixed) krylov32.push_back(i);
     }
-    (i.mixed ? f32 : f64).push_back(&i);
+    (i->mixed ? f32 : f64).push_back(i);
   }
-  polar_batch* b = B.b;
-  for (int k = 0; k < MK_COUNT; ++k)  // masks first: same arena offsets in both passes
-    B.mask[k] = const_cast<int*>(B.put(std::vector<int>(inst.size(), 0)));
   CondHandle hre = 0;
   TRY(bcond(B, g, &hre));
   const int64_t l0 = B.launches;
@@ -2154,11 +2157,48 @@ int batch_step_graph(BatchBuild& B, cudaGraph_t g, const std::vector<BInst>& ins
   TRY(batch_ctl(B, C_SCHED_NEXT, all, G_ALL));
   TRY(bcap_end(B, nullptr));
   const int64_t l3 = B.launches;
-  b->kernels_fixed = (l1 - l0) + (l3 - l2);
-  b->kernels_sweep = (l2 - l1) - it32 - it64;
-  b->kernels_iter32 = it32;
-  b->kernels_iter64 = it64;
+  grp->fixed = (l1 - l0) + (l3 - l2);
+  grp->sweep = (l2 - l1) - it32 - it64;
+  grp->iter32 = it32;
+  grp->iter64 = it64;
   return POLAR_OK;
+}
+
+// One theta-step of every instance as one graph: the groups' steps are parallel branches
+// (a group's latency-bound phases -- coarse levels, the last iterations of its slowest
+// instance -- overlap the other groups' work).
+int batch_step_graph(BatchBuild& B, cudaGraph_t g, const std::vector<BInst>& inst) {
+  for (int k = 0; k < MK_COUNT; ++k)  // masks first: same arena offsets in both passes
+    B.mask[k] = const_cast<int*>(B.put(std::vector<int>(inst.size(), 0)));
+  for (polar_batch::Group& grp : B.b->groups) {
+    std::vector<const BInst*> members;
+    for (int i : grp.members) members.push_back(&inst[i]);
+    TRY(batch_group_step(B, g, members, &grp));
+  }
+  return POLAR_OK;
+}
+
+// Groups of the batch: instances sorted by size, cut into up to kBatchGroups contiguous
+// groups of about equal total points.
+constexpr int kBatchGroups = 8;
+void make_batch_groups(polar_batch* b) {
+  const int count = (int)b->ctx.size();
+  std::vector<int> order(count);
+  for (int i = 0; i < count; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(),
+                   [&](int x, int y) { return b->ctx[x]->nv() < b->ctx[y]->nv(); });
+  double total = 0;
+  for (polar_ctx* c : b->ctx) total += (double)c->nv();
+  const int G = std::min(kBatchGroups, count);
+  b->groups.assign(1, polar_batch::Group{});
+  double acc = 0;
+  for (int i : order) {
+    if (acc > total * (double)b->groups.size() / G && (int)b->groups.size() < G &&
+        !b->groups.back().members.empty())
+      b->groups.emplace_back();
+    b->groups.back().members.push_back(i);
+    acc += (double)b->ctx[i]->nv();
+  }
 }
 
 // (Re)builds the batch's step graph: plan pass, arena upload, capture pass.
@@ -2169,6 +2209,7 @@ int build_batch_graph(polar_batch* b) {
   b->ex = nullptr;
   b->g = nullptr;
   if (!b->cap) CUDA_TRY(cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking));
+  make_batch_groups(b);
   std::vector<BInst> inst;
   for (int i = 0; i < (int)b->ctx.size(); ++i) {
     polar_ctx* c = b->ctx[i];
@@ -2581,19 +2622,21 @@ int polar_batch_advance(polar_batch* b, int32_t nsteps, const double* const* t, 
   }
   // kernels launched: per step the fixed ones, then every loop runs as long as its slowest
   // instance
-  for (int k = 0; k < nsteps; ++k) {
-    int sweeps = 0, it32 = 0, it64 = 0;
-    for (polar_ctx* c : b->ctx) {
-      const StepOut& r = c->out_host[k];
-      if (r.status == POLAR_ESTATE) continue;
-      sweeps = std::max(sweeps, r.sweeps - 1);
-      const int i64 = c->precision == POLAR_MIXED ? r.iters64 : r.iters;
-      it64 = std::max(it64, i64);
-      it32 = std::max(it32, r.iters - i64);
+  for (int k = 0; k < nsteps; ++k)
+    for (const polar_batch::Group& grp : b->groups) {
+      int sweeps = 0, it32 = 0, it64 = 0;
+      for (int i : grp.members) {
+        const polar_ctx* c = b->ctx[i];
+        const StepOut& r = c->out_host[k];
+        if (r.status == POLAR_ESTATE) continue;
+        sweeps = std::max(sweeps, r.sweeps - 1);
+        const int i64 = c->precision == POLAR_MIXED ? r.iters64 : r.iters;
+        it64 = std::max(it64, i64);
+        it32 = std::max(it32, r.iters - i64);
+      }
+      b->launches += grp.fixed + (int64_t)sweeps * grp.sweep + (int64_t)it32 * grp.iter32 +
+                     (int64_t)it64 * grp.iter64;
     }
-    b->launches += b->kernels_fixed + (int64_t)sweeps * b->kernels_sweep +
-                   (int64_t)it32 * b->kernels_iter32 + (int64_t)it64 * b->kernels_iter64;
-  }
   return rc;
 }
 
