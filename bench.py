@@ -64,6 +64,9 @@ WORKLOADS = {
                desc="continuity, adaptive polar mesh 2048 x 4096 (r graded 1.03 to both "
                     "ends), D in [0.5, 2], cell Peclet 10, Crank-Nicolson, 2000-level time "
                     "stretch"),
+    "c1": dict(gen="config1", K=100, sample=(None, None), check="full",
+               desc="parabolic u_t = Lap u + f, uniform polar mesh 32 x 64, Crank-Nicolson, "
+                    "dt = 0.01, 100 steps to T = 1 (separable: the direct FFT-in-theta solve)"),
     "c2": dict(gen="config2", K=1000, sample=(256, 512), check="full",
                desc="parabolic u_t = Lap u + f, adaptive polar mesh 512 x 1024 (r graded "
                     "1.03 to both ends, theta density 1 + 0.5 cos), Crank-Nicolson, "
@@ -280,6 +283,9 @@ def run_reference(args):
     cores = host_cores()
     m, n = w["sample"]
     pool = oracle_pool(args.workload, m, n, cores)
+    if m is None:  # the sample is the whole workload
+        full = make_problem(args.workload)
+        m, n = full.m, full.n
     levels, _ = step_levels(w["K"], 8 * cores)
     # one bench step = one oracle theta-step on every host core (levels spread over the
     # schedule) on the m x n sample of the workload
@@ -574,6 +580,8 @@ def run_native(args):
         pool.close()
         pool.join()
         m_s, n_s = w["sample"]
+        if m_s is None:  # the sample is the whole workload
+            m_s, n_s = prob.m, prob.n
         line["cpu_baseline"] = {
             "value": v_all, "unit": UNIT, "cores": cores, "kind": "oracle",
             "single_core_value": v_one,
@@ -735,9 +743,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--compare", type=int, default=1,
                     help="also time the other precision on the same steps")
-    ap.add_argument("--workload", choices=["c5", "c3", "c2", "batch"], default="c5",
+    ap.add_argument("--workload", choices=["c5", "c3", "c2", "c1", "batch"], default="c5",
                     help="c5 (default): continuity 8192 x 16384; c3: continuity 2048 x 4096; "
-                         "c2: parabolic 512 x 1024; batch: the 256-instance sweep")
+                         "c2: parabolic 512 x 1024; c1: parabolic 32 x 64 (direct solve); "
+                         "batch: the 256-instance sweep")
     ap.add_argument("--profile-step", action="store_true",
                     help="run one eager step of --workload inside a profiler range")
     ap.add_argument("--mesh", type=int, nargs=2, metavar=("M", "N"),

@@ -382,3 +382,67 @@ def config4_instance(i: int, K: int = 500, scale: float = 1.0) -> Problem:
 def config5(m: int = 8192, n: int = 16384, K: int = 200) -> Problem:
     return continuity_problem(m, n, K, SEED_BASE + 4, theta_w=0.6, two_sided=False,
                               name=f"C5_continuity_{m}x{n}")
+
+
+# ----------------------------------------------------------------------------------------
+# electron-hole pair with a self-consistent potential
+
+@dataclass
+class CoupledPair:
+    """Three problems on one mesh -- the potential, the electrons, the holes -- and the
+    coupling data: signed mobilities (drift v_c = -mobility[c] grad phi), the potential's
+    source slots that receive the densities, its source weights, the time levels and the
+    carriers' implicit weight."""
+    phi: Problem
+    electrons: Problem
+    holes: Problem
+    mobility: tuple
+    slots: tuple
+    w_phi: np.ndarray
+    t: np.ndarray
+    theta_w: float
+
+
+def coupled_pair(m: int = 24, n: int = 48, K: int = 3, seed: int = SEED_BASE + 31,
+                 scale: float = 1.0, mobility=(-2.0, 1.5)) -> CoupledPair:
+    """A drift-diffusion pair on a stretched adaptive mesh: the potential solves
+    -div(0.5 grad phi) = scale (p - n + C) with a doping bump C = 1.5 exp(-8 r^2) - 0.3
+    and phi = 0.3 scale cos(theta - theta1) on r = 1 (Gummel's iteration contracts by
+    about 0.2 per sweep at scale 1 and stops converging near scale 8 at this dt); the
+    carriers have face diffusivities drawn in [0.5, 2] and [0.3, 1.5], recombination rates
+    1 and 0.5, smooth generation and boundary densities, smooth positive initial
+    densities, dt = 0.02, theta = 0.5."""
+    rng = SplitMix64(seed)
+    theta0 = 2.0 * math.pi * rng.uniform()
+    theta1 = 2.0 * math.pi * rng.uniform()
+    r = meshes.sine_stretch(m, 0.8)
+    theta = meshes.density_theta(n, theta0)
+    t = meshes.uniform_time(0.02, K)
+    N = m * n + 1
+    R, TH = node_coords(r, theta)
+    nrf, ntf = (m + 1) * n, m * n
+
+    def draw(count, lo, hi):
+        return np.array([lo + (hi - lo) * rng.uniform() for _ in range(count)])
+
+    doping = 1.5 * np.exp(-8.0 * R ** 2) - 0.3
+    phi = Problem(
+        name=f"coupled_phi_{m}x{n}", r=r, theta=theta, t=t, theta_w=1.0,
+        scheme=SCHEME_CONSERVATIVE, d_rface=np.full(nrf, 0.5), d_tface=np.full(ntf, 0.5),
+        src=[np.zeros(N), np.zeros(N), doping],
+        bnd=[np.zeros(n), np.zeros(n), 0.3 * np.cos(theta - theta1)],
+        u0=np.zeros(N), weights=lambda tt: np.array([-scale, scale, scale]))
+
+    def carrier(name, dlo, dhi, b, g_amp, bnd_val, phase):
+        return Problem(
+            name=f"coupled_{name}_{m}x{n}", r=r, theta=theta, t=t, theta_w=0.5,
+            scheme=SCHEME_CONSERVATIVE, d_rface=draw(nrf, dlo, dhi), d_tface=draw(ntf, dlo, dhi),
+            src=[0.5 + g_amp * R ** 2 * np.cos(TH - phase)],
+            bnd=[bnd_val + 0.2 * np.sin(theta - phase)],
+            u0=bnd_val + 0.3 * (1.0 - R ** 2) * (1.0 + 0.5 * np.cos(TH - phase)),
+            weights=lambda tt: np.array([1.0]), b_const=b, b=np.full(N, b))
+
+    electrons = carrier("electrons", 0.5, 2.0, 1.0, 0.5, 1.0, theta0)
+    holes = carrier("holes", 0.3, 1.5, 0.5, 0.3, 0.8, theta1)
+    return CoupledPair(phi=phi, electrons=electrons, holes=holes, mobility=tuple(mobility),
+                       slots=(0, 1), w_phi=np.array([-scale, scale, scale]), t=t, theta_w=0.5)
