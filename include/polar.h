@@ -249,6 +249,67 @@ int polar_batch_advance(polar_batch* batch, int32_t nsteps, const double* const*
  * sweep and iteration counts). */
 int64_t polar_batch_kernel_launches(const polar_batch* batch);
 
+/* Steady problem L U = f (Eq. 2.1 / Eq. 3.1 without the time derivative): one solve of
+ * the implicit system with alpha = 0 and theta = 1, f and the Dirichlet data the sources
+ * weighted by w (nsrc values; NULL when nsrc = 0), started from the current state, which
+ * it replaces; the time is unchanged.  L must be nonsingular (Dirichlet data on r = 1
+ * make the diffusion operator so).  stats (one entry) or NULL.  Errors as polar_advance. */
+int polar_solve_steady(polar_ctx* ctx, const double* w, const polar_solver_opts* opts,
+                       polar_step_stats* stats);
+
+/* Face drift of a potential: v = -mobility grad u of the context's current state u, the
+ * radial component at the radial faces ((m+1) n values, layout of v_rface: (u_{i+1,j} -
+ * u_{i,j}) / (r_{i+1} - r_i), u_{0,j} the origin, u_{m+1,j} = g_j) and the angular one at
+ * the angular faces (m n values, layout of v_tface: (u_{i,j+1} - u_{i,j}) / (r_i
+ * (theta_{j+1} - theta_j)), periodic).  g: n values of u on r = 1.  `memory` says where
+ * g, v_rface and v_tface live.  Errors: POLAR_EINVAL, POLAR_ESTATE (no state), POLAR_ECUDA. */
+int polar_face_drift(polar_ctx* ctx, double mobility, const double* g, double* v_rface,
+                     double* v_tface, int32_t memory);
+
+/* Electron-hole drift-diffusion with a self-consistent field (the carrier pair of
+ * Section 3.1, both obeying Eq. 3.1, and the Poisson coupling of the outlook in
+ * Section 4).  Three contexts on one mesh (conservative scheme, coefficients and states
+ * set): the potential phi, whose operator is -div(eps grad phi) (D = eps, no drift) and
+ * two of whose source fields (slots src_electrons, src_holes) the step fills with the
+ * carrier densities, and the electrons and holes, whose drift the step sets to
+ * v_c = -mobility[c] grad phi (e.g. mobility = -mu_n for electrons, +mu_p for holes);
+ * their other coefficients stay as set.  One polar_gummel_step advances the pair from
+ * t[0] to t[1] by Gummel's iteration: phi from the current densities
+ * (polar_solve_steady, sources weighted by w_phi), the drifts from phi
+ * (polar_face_drift; the carriers' operators re-assembled on the host), both carriers one
+ * theta-step from their state at t[0] with that drift held over the step (one 2-instance
+ * polar_batch; w[c] holds 2 x nsrc weights of carrier c at t[0] and t[1]); repeated
+ * until max|phi_j - phi_{j-1}| / max|phi_j| <= tol (the absolute change when phi_j = 0),
+ * at most max_iter potential solves.  The carriers then hold t[1]'s densities and phi
+ * the potential of those densities.  The object's device buffers (3 N doubles) come from
+ * the potential's allocator and are freed with its context; destroy the object before
+ * any of its contexts.
+ * Errors: POLAR_EINVAL (mismatched meshes or scheme, bad slots, mobility, tol or
+ * max_iter), POLAR_ESTATE (coefficients or states missing), POLAR_ENOCONV (max_iter
+ * reached: the carriers hold the last iterate), errors of the solves. */
+typedef struct {
+  double mobility[2];      /* electrons, holes: v_c = -mobility[c] grad phi            */
+  int32_t src_electrons;   /* source slots of the potential filled with the densities  */
+  int32_t src_holes;
+  double tol;              /* on max|phi_j - phi_{j-1}| / max|phi_j|                   */
+  int32_t max_iter;        /* potential solves per step                                */
+  int32_t reserved;
+} polar_gummel_desc;
+typedef struct {
+  int32_t iters;                /* potential solves of the step                        */
+  int32_t status;
+  double change;                /* the last max|phi_j - phi_{j-1}| / max|phi_j|         */
+  polar_step_stats phi;         /* the last potential solve                            */
+  polar_step_stats carrier[2];  /* the last step of the electrons and of the holes     */
+} polar_gummel_stats;
+typedef struct polar_gummel polar_gummel;
+int polar_gummel_create(polar_ctx* phi, polar_ctx* electrons, polar_ctx* holes,
+                        const polar_gummel_desc* desc, polar_gummel** out);
+int polar_gummel_step(polar_gummel* g, const double* t, double theta, const double* const* w,
+                      const double* w_phi, const polar_solver_opts* opts,
+                      polar_gummel_stats* stats);
+int polar_gummel_destroy(polar_gummel* g);
+
 /* y = (alpha I + beta L) x for one vector x with homogeneous Dirichlet data
  * (g = 0): the matrix-free operator every kernel of the step is built on.
  * x and y hold N doubles in the interface layout, both on the host or both on the

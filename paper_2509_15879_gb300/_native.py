@@ -59,6 +59,22 @@ class polar_step_stats(C.Structure):
                     fp64_iters=self.fp64_iters, scaled_resid=self.scaled_resid)
 
 
+class polar_gummel_desc(C.Structure):
+    _fields_ = [("mobility", C.c_double * 2), ("src_electrons", C.c_int32),
+                ("src_holes", C.c_int32), ("tol", C.c_double), ("max_iter", C.c_int32),
+                ("reserved", C.c_int32)]
+
+
+class polar_gummel_stats(C.Structure):
+    _fields_ = [("iters", C.c_int32), ("status", C.c_int32), ("change", C.c_double),
+                ("phi", polar_step_stats), ("carrier", polar_step_stats * 2)]
+
+    def as_dict(self):
+        return dict(iters=self.iters, status=self.status, change=self.change,
+                    phi=self.phi.as_dict(),
+                    carrier=[self.carrier[0].as_dict(), self.carrier[1].as_dict()])
+
+
 class PolarError(RuntimeError):
     def __init__(self, code, msg):
         super().__init__(f"polar error {code}: {msg}")
@@ -89,6 +105,15 @@ EXPORTS = {
     "polar_batch_kernel_launches": (C.c_int64, [C.c_void_p]),
     "polar_batch_advance": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(_dp), _dp, C.POINTER(_dp),
                                       C.POINTER(polar_solver_opts), C.POINTER(polar_step_stats)]),
+    "polar_solve_steady": (C.c_int, [C.c_void_p, _dp, C.POINTER(polar_solver_opts),
+                                     C.POINTER(polar_step_stats)]),
+    "polar_face_drift": (C.c_int, [C.c_void_p, C.c_double, C.c_void_p, C.c_void_p, C.c_void_p,
+                                   C.c_int32]),
+    "polar_gummel_create": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p,
+                                      C.POINTER(polar_gummel_desc), C.POINTER(C.c_void_p)]),
+    "polar_gummel_step": (C.c_int, [C.c_void_p, _dp, C.c_double, C.POINTER(_dp), _dp,
+                                    C.POINTER(polar_solver_opts), C.POINTER(polar_gummel_stats)]),
+    "polar_gummel_destroy": (C.c_int, [C.c_void_p]),
     "polar_timing_enable": (C.c_int, [C.c_void_p, C.c_int32]),
     "polar_timing_query": (C.c_int, [C.c_void_p, C.c_int32, C.c_char_p, C.c_size_t,
                                      C.POINTER(C.c_int64), _dp, _dp]),
@@ -397,6 +422,76 @@ def polar_batch_advance(batch: Batch, ts, thetas, ws=None, opts=None, check=True
     if check:
         _check(rc)
     return [[stats[i * K + k].as_dict() for k in range(K)] for i in range(count)], rc
+
+
+def polar_solve_steady(ctx: Ctx, w=(), opts=None):
+    """Solves L U = f (sources weighted by w) into the context's state; returns the stats."""
+    w = _f64(w)
+    st = polar_step_stats()
+    _check(load().polar_solve_steady(ctx.handle, w.ctypes.data_as(_dp), _opts(opts),
+                                     C.byref(st)))
+    return st.as_dict()
+
+
+def polar_face_drift(ctx: Ctx, mobility, g, v_rface=None, v_tface=None):
+    """v = -mobility grad u of the state at the radial and angular faces; g holds u on
+    r = 1.  Host arrays unless all three are device tensors; returns (v_rface, v_tface)."""
+    m, n = ctx.m, ctx.n
+    if v_rface is None:
+        v_rface = np.empty((m + 1) * n, dtype=np.float64)
+    if v_tface is None:
+        v_tface = np.empty(m * n, dtype=np.float64)
+    ag = _Arr(g, n, "g")
+    ar = _Arr(v_rface, (m + 1) * n, "v_rface", out=True)
+    at = _Arr(v_tface, m * n, "v_tface", out=True)
+    if len({ag.device, ar.device, at.device}) > 1:
+        raise ValueError("g, v_rface and v_tface must live in the same memory")
+    _check(load().polar_face_drift(ctx.handle, float(mobility), ag.ptr, ar.ptr, at.ptr,
+                                   POLAR_DEVICE if ag.device else POLAR_HOST))
+    return v_rface, v_tface
+
+
+class Gummel:
+    """Handle of a polar_gummel (keeps its three contexts alive)."""
+
+    def __init__(self, handle, ctxs):
+        self.handle, self.ctxs = handle, ctxs
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None and not sys.is_finalizing():
+            _lib.polar_gummel_destroy(self.handle)
+            self.handle = None
+
+
+def polar_gummel_create(phi: Ctx, electrons: Ctx, holes: Ctx, mobility, src_electrons,
+                        src_holes, tol=1e-10, max_iter=50) -> Gummel:
+    d = polar_gummel_desc((C.c_double * 2)(*[float(x) for x in mobility]), int(src_electrons),
+                          int(src_holes), float(tol), int(max_iter), 0)
+    h = C.c_void_p()
+    _check(load().polar_gummel_create(phi.handle, electrons.handle, holes.handle, C.byref(d),
+                                      C.byref(h)))
+    return Gummel(h, (phi, electrons, holes))
+
+
+def polar_gummel_step(g: Gummel, t0, t1, theta, w_electrons=(), w_holes=(), w_phi=(),
+                      opts=None, check=True):
+    """One coupled step from t0 to t1; w_* hold the carriers' 2 x nsrc weights (levels t0,
+    t1) and the potential's nsrc weights.  Returns (stats dict, rc)."""
+    t = _f64([t0, t1])
+    we, wh, wp = _f64(w_electrons), _f64(w_holes), _f64(w_phi)
+    wptr = (_dp * 2)(we.ctypes.data_as(_dp), wh.ctypes.data_as(_dp))
+    st = polar_gummel_stats()
+    rc = load().polar_gummel_step(g.handle, t.ctypes.data_as(_dp), float(theta), wptr,
+                                  wp.ctypes.data_as(_dp), _opts(opts), C.byref(st))
+    if check:
+        _check(rc)
+    return st.as_dict(), rc
+
+
+def polar_gummel_destroy(g: Gummel):
+    if g.handle:
+        _check(load().polar_gummel_destroy(g.handle))
+        g.handle = None
 
 
 def polar_timing_enable(ctx: Ctx, on=True):

@@ -86,6 +86,17 @@ struct KernelStat {
 }  // namespace
 
 struct polar_ctx;
+struct polar_batch;
+// Electron-hole pair coupled to a Poisson potential (see polar_gummel_step).
+struct polar_gummel {
+  polar_ctx* phi = nullptr;
+  polar_ctx* car[2] = {nullptr, nullptr};  // electrons, holes
+  polar_batch* pair = nullptr;             // the carriers advanced as one batch
+  polar_gummel_desc d{};
+  double* save[2] = {nullptr, nullptr};    // carriers' states at the start of the step
+  double* phi_prev = nullptr;              // previous iterate of the potential
+  double* change = nullptr;                // max |phi - phi_prev|, max |phi|
+};
 struct polar_batch {
   std::vector<polar_ctx*> ctx;
   cudaStream_t st = nullptr;
@@ -122,6 +133,8 @@ struct polar_ctx {
   int nsrc = 0;
   double* vsrc[4] = {nullptr, nullptr, nullptr, nullptr};
   double* bnd[4] = {nullptr, nullptr, nullptr, nullptr};
+  std::vector<double> bnd_host[4];  // host copies of the Dirichlet fields
+  HostCoeffs hk;                    // the coefficients the levels were assembled from
   bool have_coeffs = false, have_state = false;
   double t = 0.0;
   double* U = nullptr;
@@ -2201,6 +2214,29 @@ void make_batch_groups(polar_batch* b) {
   }
 }
 
+// Assembles the fine level from c->hk, coarsens it, uploads every level and marks the
+// per-step parts and the step graphs stale.
+int reassemble(polar_ctx* c) {
+  std::vector<HLevel> H(c->nlev());
+  if (c->scheme == POLAR_SCHEME_CONSERVATIVE) {
+    assemble_conservative(c->r, c->theta, c->hk, H[0]);
+  } else {
+    assemble_paper(c->r, c->theta, c->hk, H[0]);
+  }
+  c->symmetric = is_symmetric(H[0]);
+  TRY(setup_direct(c, H[0]));
+  for (int l = 0; l + 1 < c->nlev(); ++l) coarsen(H[l], H[l + 1]);
+  for (int l = 0; l < c->nlev(); ++l) TRY(upload_level(c, l, H[l]));
+  c->cur_alpha = c->cur_beta = -1.0;  // the per-step parts must be refreshed
+  // new coefficients: the mixed path tries its FP32 solve again from the next step
+  CUDA_TRY(cudaMemsetAsync(&c->ks->sticky64, 0, sizeof(int), c->st));
+  if (c->stamp64) CUDA_TRY(cudaMemsetAsync(c->stamp64, 0, 2 * sizeof(double), c->st));
+  c->graph_ok = false;
+  c->generation += 1;
+  CUDA_TRY(cudaStreamSynchronize(c->st));
+  return POLAR_OK;
+}
+
 // (Re)builds the batch's step graph: plan pass, arena upload, capture pass.
 int build_batch_graph(polar_batch* b) {
   CUDA_TRY(cudaStreamSynchronize(b->st));  // no launch of the old graph still reads the arena
@@ -2406,17 +2442,8 @@ int polar_set_coeffs(polar_ctx* c, const polar_coeffs* k) {
     TRY(fetch(k->src[q], N, k->memory, srcs[q]));
     TRY(fetch(k->bnd[q], (size_t)n, k->memory, bnds[q]));
   }
-  // fine level and its radial hierarchy
-  std::vector<HLevel> H(c->nlev());
-  if (c->scheme == POLAR_SCHEME_CONSERVATIVE) {
-    assemble_conservative(c->r, c->theta, K, H[0]);
-  } else {
-    assemble_paper(c->r, c->theta, K, H[0]);
-  }
-  c->symmetric = is_symmetric(H[0]);
-  TRY(setup_direct(c, H[0]));
-  for (int l = 0; l + 1 < c->nlev(); ++l) coarsen(H[l], H[l + 1]);
-  for (int l = 0; l < c->nlev(); ++l) TRY(upload_level(c, l, H[l]));
+  c->hk = std::move(K);
+  TRY(reassemble(c));
   // sources in the split layout, scaled by the control volumes
   for (int q = 0; q < k->nsrc; ++q) {
     if (!c->vsrc[q]) {  // allocated on first use, reused by later set_coeffs calls
@@ -2427,14 +2454,10 @@ int polar_set_coeffs(polar_ctx* c, const polar_coeffs* k) {
     CUDA_TRY(cudaMemcpy(c->io, srcs[q].data(), N * sizeof(double), cudaMemcpyHostToDevice));
     LAUNCH(launch_pack(c->sh0(), c->io, c->lv[0].vol, c->vsrc[q], c->st));
     CUDA_TRY(cudaMemcpy(c->bnd[q], bnds[q].data(), n * sizeof(double), cudaMemcpyHostToDevice));
+    c->bnd_host[q] = std::move(bnds[q]);
   }
   c->nsrc = k->nsrc;
-  c->cur_alpha = c->cur_beta = -1.0;  // the per-step parts must be refreshed
-  // new coefficients: the mixed path tries its FP32 solve again from the next step
-  CUDA_TRY(cudaMemsetAsync(&c->ks->sticky64, 0, sizeof(int), c->st));
-  if (c->stamp64) CUDA_TRY(cudaMemsetAsync(c->stamp64, 0, 2 * sizeof(double), c->st));
   c->graph_ok = false;                // the step graph bakes in the source count
-  c->generation += 1;
   CUDA_TRY(cudaStreamSynchronize(c->st));
   c->have_coeffs = true;
   return POLAR_OK;
@@ -2545,6 +2568,141 @@ int polar_face_drift(polar_ctx* c, double mobility, const double* g, double* v_r
     CUDA_TRY(cudaMemcpyAsync(v_tface, vt, nt * sizeof(double), cudaMemcpyDeviceToHost, c->st));
   }
   CUDA_TRY(cudaStreamSynchronize(c->st));
+  return POLAR_OK;
+}
+
+int polar_gummel_create(polar_ctx* phi, polar_ctx* electrons, polar_ctx* holes,
+                        const polar_gummel_desc* d, polar_gummel** out) {
+  if (!phi || !electrons || !holes || !d || !out) return fail(POLAR_EINVAL, "null argument");
+  *out = nullptr;
+  if (phi == electrons || phi == holes || electrons == holes)
+    return fail(POLAR_EINVAL, "the potential and the two carriers need three contexts");
+  polar_ctx* cs[3] = {phi, electrons, holes};
+  for (polar_ctx* c : cs) {
+    if (c->m != phi->m || c->n != phi->n || c->r != phi->r || c->theta != phi->theta ||
+        c->device != phi->device)
+      return fail(POLAR_EINVAL, "the three contexts must share one mesh and device");
+    if (c->scheme != POLAR_SCHEME_CONSERVATIVE)
+      return fail(POLAR_EINVAL, "the coupled system runs on the conservative scheme");
+    if (!c->have_coeffs) return fail(POLAR_ESTATE, "set the coefficients of all three contexts first");
+  }
+  if (d->src_electrons < 0 || d->src_electrons >= phi->nsrc || d->src_holes < 0 ||
+      d->src_holes >= phi->nsrc || d->src_electrons == d->src_holes)
+    return fail(POLAR_EINVAL, "the carrier source slots must be two distinct sources of the potential");
+  if (!std::isfinite(d->mobility[0]) || !std::isfinite(d->mobility[1]) || !(d->tol > 0) ||
+      d->max_iter < 1)
+    return fail(POLAR_EINVAL, "bad mobility, tol or max_iter");
+  CUDA_TRY(cudaSetDevice(phi->device));
+  polar_gummel* G = new polar_gummel();
+  G->phi = phi;
+  G->car[0] = electrons;
+  G->car[1] = holes;
+  G->d = *d;
+  const size_t nv = phi->nv();
+  int rc = POLAR_OK;
+  if (rc == POLAR_OK) rc = dalloc(phi, &G->save[0], nv);
+  if (rc == POLAR_OK) rc = dalloc(phi, &G->save[1], nv);
+  if (rc == POLAR_OK) rc = dalloc(phi, &G->phi_prev, nv);
+  if (rc == POLAR_OK) rc = dalloc(phi, &G->change, 2);
+  if (rc == POLAR_OK) rc = polar_batch_create(G->car, 2, electrons->st, &G->pair);
+  if (rc != POLAR_OK) {
+    delete G;  // the buffers stay with the potential's context until it is destroyed
+    return rc;
+  }
+  *out = G;
+  return POLAR_OK;
+}
+
+int polar_gummel_destroy(polar_gummel* G) {
+  if (!G) return POLAR_OK;
+  polar_batch_destroy(G->pair);
+  delete G;
+  return POLAR_OK;
+}
+
+int polar_gummel_step(polar_gummel* G, const double* t, double theta, const double* const* w,
+                      const double* w_phi, const polar_solver_opts* opts,
+                      polar_gummel_stats* stats) {
+  if (!G || !t) return fail(POLAR_EINVAL, "null argument");
+  polar_ctx* phi = G->phi;
+  polar_ctx* const* car = G->car;
+  if (phi->nsrc > 0 && !w_phi) return fail(POLAR_EINVAL, "the potential's source weights are required");
+  for (int k = 0; k < 2; ++k)
+    if (car[k]->nsrc > 0 && (!w || !w[k])) return fail(POLAR_EINVAL, "carrier source weights required");
+  if (!phi->have_state || !car[0]->have_state || !car[1]->have_state)
+    return fail(POLAR_ESTATE, "set the states of all three contexts first");
+  if (!(t[1] > t[0]) || !std::isfinite(t[1])) return fail(POLAR_EINVAL, "need t[1] > t[0]");
+  CUDA_TRY(cudaSetDevice(phi->device));
+  polar_ctx* c = phi;  // the context the launch checks report on
+  const int m = phi->m, n = phi->n;
+  const size_t nv = phi->nv(), nf = (size_t)(m + 1) * n, nt = (size_t)m * n;
+  if (stats) *stats = polar_gummel_stats{};
+  for (int k = 0; k < 2; ++k) {
+    CUDA_TRY(cudaMemcpyAsync(G->save[k], car[k]->U, nv * sizeof(double), cudaMemcpyDeviceToDevice,
+                             car[k]->st));
+    CUDA_TRY(cudaStreamSynchronize(car[k]->st));
+  }
+  // potential on r = 1: the weighted Dirichlet fields of the potential's context
+  std::vector<double> g(n, 0.0);
+  for (int q = 0; q < phi->nsrc; ++q)
+    for (int j = 0; j < n; ++j) g[j] += w_phi[q] * phi->bnd_host[q][j];
+  const int src_slot[2] = {G->d.src_electrons, G->d.src_holes};
+  double change = 0.0;
+  int it = 0;
+  bool converged = false;
+  for (it = 0; it < G->d.max_iter; ++it) {
+    // the carrier densities as the potential's sources (split layout times volumes)
+    for (int k = 0; k < 2; ++k) {
+      LAUNCH(launch_unpack(car[k]->sh0(), car[k]->U, nullptr, phi->io, phi->st));
+      LAUNCH(launch_pack(phi->sh0(), phi->io, phi->lv[0].vol, phi->vsrc[src_slot[k]], phi->st));
+    }
+    CUDA_TRY(cudaStreamSynchronize(phi->st));
+    polar_step_stats ps{};
+    TRY(polar_solve_steady(phi, w_phi, opts, &ps));
+    if (stats) stats->phi = ps;
+    if (it > 0) {
+      LAUNCH(launch_max_change(nv, phi->U, G->phi_prev, G->change, phi->st));
+      double h[2];
+      CUDA_TRY(cudaMemcpyAsync(h, G->change, sizeof(h), cudaMemcpyDeviceToHost, phi->st));
+      CUDA_TRY(cudaStreamSynchronize(phi->st));
+      change = h[1] > 0 ? h[0] / h[1] : h[0];
+      if (change <= G->d.tol) {
+        converged = true;
+        ++it;
+        break;
+      }
+    }
+    CUDA_TRY(cudaMemcpyAsync(G->phi_prev, phi->U, nv * sizeof(double), cudaMemcpyDeviceToDevice,
+                             phi->st));
+    // drift of each carrier from the potential, the carriers re-assembled with it
+    for (int k = 0; k < 2; ++k) {
+      HostCoeffs& K = car[k]->hk;
+      K.vr.resize(nf);
+      K.vt.resize(nt);
+      TRY(polar_face_drift(phi, G->d.mobility[k], g.data(), K.vr.data(), K.vt.data(), POLAR_HOST));
+      TRY(reassemble(car[k]));
+      CUDA_TRY(cudaMemcpyAsync(car[k]->U, G->save[k], nv * sizeof(double), cudaMemcpyDeviceToDevice,
+                               car[k]->st));
+      CUDA_TRY(cudaStreamSynchronize(car[k]->st));
+      car[k]->t = t[0];
+    }
+    // both carriers one theta-step from the start of the step, as one batch
+    const double* ts[2] = {t, t};
+    const double th[2] = {theta, theta};
+    const double* ws[2] = {w ? w[0] : nullptr, w ? w[1] : nullptr};
+    polar_step_stats cst[2] = {};
+    TRY(polar_batch_advance(G->pair, 1, ts, th, ws, opts, cst));
+    if (stats) {
+      stats->carrier[0] = cst[0];
+      stats->carrier[1] = cst[1];
+    }
+  }
+  if (stats) {
+    stats->iters = it;
+    stats->change = change;
+    stats->status = converged ? POLAR_OK : POLAR_ENOCONV;
+  }
+  if (!converged) return fail(POLAR_ENOCONV, "Gummel iteration did not reach tol");
   return POLAR_OK;
 }
 

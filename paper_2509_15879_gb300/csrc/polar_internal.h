@@ -567,6 +567,9 @@ int launch_check_finite(size_t n, const double* a, cudaStream_t st, Reduce red);
 // layout, r (m+2) and theta (n) the mesh, g (n) the values on r = 1
 int launch_face_drift(int m, int n, const double* u, const double* r, const double* th,
                       const double* g, double mobility, double* vr, double* vt, cudaStream_t st);
+// out[0] = max_k |a_k - b_k|, out[1] = max_k |a_k| over n doubles (out zeroed first; NaN
+// counts as +inf)
+int launch_max_change(size_t n, const double* a, const double* b, double* out, cudaStream_t st);
 
 // interface layout (origin, then radial lines j = 0..n-1 of m values) <-> split layout;
 // `scale` (nullable, split layout) multiplies on the way in, `div` divides on the way out

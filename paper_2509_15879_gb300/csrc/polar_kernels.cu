@@ -1073,6 +1073,29 @@ int launch_face_drift(int m, int n, const double* u, const double* r, const doub
   return 1;
 }
 
+__global__ void k_max_change(size_t n, const double* a, const double* b,
+                             unsigned long long* out) {
+  unsigned long long d = 0, x = 0;
+  for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n;
+       k += (size_t)gridDim.x * blockDim.x) {
+    d = max(d, abs_bits(a[k] - b[k]));
+    x = max(x, abs_bits(a[k]));
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    d = max(d, __shfl_xor_sync(0xffffffffu, d, o));
+    x = max(x, __shfl_xor_sync(0xffffffffu, x, o));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicMax(out, d);
+    atomicMax(out + 1, x);
+  }
+}
+int launch_max_change(size_t n, const double* a, const double* b, double* out, cudaStream_t st) {
+  if (cudaMemsetAsync(out, 0, 2 * sizeof(double), st) != cudaSuccess) return -1;
+  k_max_change<<<grid_for(n, kVT), kVT, 0, st>>>(n, a, b, reinterpret_cast<unsigned long long*>(out));
+  return 1;
+}
+
 // ------------------------------------------------------------------ layout conversion
 // interface index q = 1 + j m + (i - 1) <-> split index sh.at(i, j); q = 0 is the origin
 __global__ void k_pack(Shape sh, const double* in, const double* scale, double* out) {
