@@ -76,3 +76,27 @@ def test_batch_longer_schedule_after_a_short_one():
         assert t == p.t[5]
         ref = po.run(p, 5)
         assert np.max(np.abs(U - ref)) / np.max(np.abs(ref)) < 1e-9
+
+
+def test_mixed_path_completes_the_hard_sweep_instances():
+    # instances 196 and 240 of the 256-instance sweep: once the mixed path's FP32 smoother
+    # could not finish steps 149 and 377 of their schedules; the mixed path now carries on
+    # in FP64 where the FP32 solve stalls.  Both advance as a batch, in mixed precision,
+    # through those steps; every step must succeed and the states must equal the FP64
+    # path's at the mixed bar (1e-9 relative; both stop at the same FP64 tolerance)
+    K = 380
+    probs = [pi.config4_instance(i, K=500) for i in (196, 240)]
+    states = {}
+    for precision in (P.POLAR_MIXED, P.POLAR_FP64):
+        ctxs = [driver.create(p, precision) for p in probs]
+        batch = P.polar_batch_create(ctxs)
+        stats, rc = driver.batch_advance(batch, probs, 0, K)
+        assert rc == 0
+        assert all(s["status"] == 0 for row in stats for s in row)
+        states[precision] = [P.polar_get_state(c)[0] for c in ctxs]
+        worst = [max(s["iters"] for s in row) for row in stats]
+        print(f"HARD instances precision {precision}: most Krylov iterations in a step {worst}")
+    for a, b in zip(states[P.POLAR_MIXED], states[P.POLAR_FP64]):
+        err = float(np.max(np.abs(a - b)) / np.max(np.abs(b)))
+        print(f"PARITY hard instance mixed vs FP64 after {K} steps: {err:.2e} (bar 1e-9)")
+        assert err < 1e-9
