@@ -411,7 +411,11 @@ __device__ __forceinline__ Line line_of(const Shape& sh, int i) {
 template <typename T>
 struct CoarseRef {
   Line ln;
-  T mul;
+  T mul;       // 1, or 0 for the zero ring
+  __device__ __forceinline__ T get(const T* X, int j) const {
+    // a select, not a product: no FP64 instruction (the ring kernels are bound by them)
+    return mul != T(0) ? X[ln.at(j)] : T(0);
+  }
 };
 template <typename T>
 __device__ __forceinline__ CoarseRef<T> coarse_ref(const Shape& C, int I) {
@@ -436,8 +440,8 @@ template <typename T>
 __device__ __forceinline__ T corrected(const OddRef<T>& o, const T* x, const T* ia, const T* ib,
                                        const T* X, int j) {
   const size_t p = o.ln.at(j);
-  const T xl = X[o.lo.ln.at(j)] * o.lo.mul;
-  const T xh = X[o.hi.ln.at(j)] * o.hi.mul;
+  const T xl = o.lo.get(X, j);
+  const T xh = o.hi.get(X, j);
   return fma(ia[p], xl, fma(ib[p], xh, x[p]));
 }
 
@@ -464,12 +468,13 @@ struct RingRhs {
     const T bv = b[p];
     if (kind == 0) return bv;
     T xw, xe;
+    const bool east = emul != T(0);  // the last ring's east neighbour is the zero ring
     if (kind == 1) {
       xw = x[wl.at(j)];
-      xe = x[el.at(j)] * emul;
+      xe = east ? x[el.at(j)] : T(0);
     } else {
       xw = corrected(wo, x, ia, ib, X, j);
-      xe = corrected(eo, x, ia, ib, X, j) * emul;
+      xe = east ? corrected(eo, x, ia, ib, X, j) : T(0);
     }
     return bv - beta * fma(w[p], xw, e[p] * xe);
   }
@@ -602,16 +607,20 @@ __device__ void solve_lines(int n, bool valid, Rhs rhs, Fac fac, T vf, T inv, Ou
   // the Sherman-Morrison vector is loaded with the rest when registers allow (short
   // chunks), so that the final correction waits on no memory access
   constexpr bool kPrefetchQ = !STAGED && (P * sizeof(T) <= 32);
-  // staged: fu / fc share the registers of fl (dead after the forward replay)
-  T v[P], fl[P], fu_[STAGED ? 1 : P], fc[P], fqv[kPrefetchQ ? P : 1];
-  T* fu = STAGED ? fl : fu_;
+  // 1/u and c/u arrive after the forward scan in the staged variant and for long chunks
+  // (P values of more than 64 bytes), whose four up-front operand arrays would not fit in
+  // the 128 registers a 512-thread CTA allows; fu then shares the registers of fl (dead
+  // after the forward replay)
+  constexpr bool kLate = STAGED || (P * sizeof(T) > 64);
+  T v[P], fl[P], fu_[kLate ? 1 : P], fc[P], fqv[kPrefetchQ ? P : 1];
+  T* fu = kLate ? fl : fu_;
 #pragma unroll
   for (int p = 0; p < P; ++p) {
     const int j = j0 + p;
     const bool in = valid && j < n;
     v[p] = in ? rhs(j) : T(0);
     fl[p] = in ? fac.l(j) : T(0);
-    if constexpr (!STAGED) {
+    if constexpr (!kLate) {
       fu_[p] = in ? fac.ui(j) : T(0);
       fc[p] = in ? fac.cu(j) : T(0);
     }
@@ -650,7 +659,7 @@ __device__ void solve_lines(int n, bool valid, Rhs rhs, Fac fac, T vf, T inv, Ou
       v[p] = prev;
     }
   }
-  if constexpr (STAGED) {
+  if constexpr (kLate) {
 #pragma unroll
     for (int p = 0; p < P; ++p) {
       const int j = j0 + p;
@@ -659,13 +668,15 @@ __device__ void solve_lines(int n, bool valid, Rhs rhs, Fac fac, T vf, T inv, Ou
       fc[p] = in ? fac.cu(j) : T(0);
     }
   }
-  // backward substitution x_j = ui_j y_j - cu_j x_{j+1}
+  // backward substitution x_j = ui_j y_j - cu_j x_{j+1}: ui_j y_j formed once, in v
+#pragma unroll
+  for (int p = 0; p < P; ++p) v[p] *= fu[p];
   A = T(1);
   B = T(0);
 #pragma unroll
   for (int p = P - 1; p >= 0; --p) {
     if (valid && j0 + p < n) {
-      B = fma(-fc[p], B, fu[p] * v[p]);
+      B = fma(-fc[p], B, v[p]);
       A = -fc[p] * A;
     }
   }
@@ -687,7 +698,7 @@ __device__ void solve_lines(int n, bool valid, Rhs rhs, Fac fac, T vf, T inv, Ou
 #pragma unroll
   for (int p = P - 1; p >= 0; --p) {
     if (valid && j0 + p < n) {
-      next = fma(-fc[p], next, fu[p] * v[p]);
+      next = fma(-fc[p], next, v[p]);
       v[p] = next;
     }
   }
