@@ -80,6 +80,10 @@ WORKLOADS = {
 # algorithmic bytes), scaled by the 16x level-0 points of the full mesh.
 NCU_TRAFFIC = {("c5", "ring_post_even@L0"): 411.6e6 * 16}
 
+# FP64 arithmetic rate of the GB300s: 528 G FMA/s from a probe of independent FMA
+# chains on every SM (the nominal figure is 1.25 TFLOP/s)
+FP64_PEAK_TFLOPS = 1.056
+
 
 def env_int(name, default):
     try:
@@ -546,6 +550,16 @@ def run_native(args):
                 "share_of_step": d["ms"] / prof["dev_ms"],
                 "timing": "CUDA events around every launch on the context's stream, eager "
                           "pass over the first timed steps"}
+        if d.get("flops") and not name.endswith(".f32"):
+            # the FP64 kernels are co-bound by GB300's FP64 pipe: their arithmetic rate
+            # (flops per point as the kernel's source performs them, FMA = 2) against the
+            # FP64 FMA rate measured on the GB300s
+            tf = d["flops"] / (d["ms"] * 1e-3) / 1e12
+            roof["fp64"] = {"achieved": tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                            "frac": tf / FP64_PEAK_TFLOPS,
+                            "peak_source": "measured FP64 FMA probe, 528 G FMA/s (nominal "
+                                           "1.25 TFLOP/s)",
+                            "flops_per_launch": d["flops"] / max(d["launches"], 1)}
 
     stats = main["stats"]
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
@@ -572,7 +586,9 @@ def run_native(args):
             "clocks": clk,
             "roofline": roof,
             "kernels": {k: {"launches": v["launches"], "ms": round(v["ms"], 3),
-                            "GBps": round(v["bytes"] / max(v["ms"], 1e-9) / 1e6, 1)}
+                            "GBps": round(v["bytes"] / max(v["ms"], 1e-9) / 1e6, 1),
+                            "GFLOPs": (round(v["flops"] / max(v["ms"], 1e-9) / 1e6, 1)
+                                       if v.get("flops") else None)}
                         for k, v in sorted(kstats.items(), key=lambda kv: -kv[1]["ms"])},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": prob.N * 8,
                     "d2h_bytes_per_step": prob.N * 8, "steps": len(ke)}}
@@ -727,7 +743,9 @@ def run_profile_step(args):
                       "precision": args.precision, "step": st[0],
                       "kernels": {k: {"launches": v["launches"], "us_per_launch":
                                       round(1e3 * v["ms"] / max(v["launches"], 1), 2),
-                                      "GBps": round(v["bytes"] / max(v["ms"], 1e-9) / 1e6, 1)}
+                                      "GBps": round(v["bytes"] / max(v["ms"], 1e-9) / 1e6, 1),
+                                      "GFLOPs": (round(v["flops"] / max(v["ms"], 1e-9) / 1e6, 1)
+                                                 if v.get("flops") else None)}
                                   for k, v in sorted(q.items(), key=lambda kv: -kv[1]["ms"])}}))
     return 0
 

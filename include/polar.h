@@ -363,6 +363,10 @@ int64_t polar_kernel_launches(const polar_ctx* ctx);
 int polar_timing_enable(polar_ctx* ctx, int32_t on);
 int polar_timing_query(polar_ctx* ctx, int32_t index, char* name, size_t name_len,
                        int64_t* launches, double* total_ms, double* bytes);
+/* The summed arithmetic of kernel class `index`'s timed launches: flops per point as the
+ * kernel's source performs them (an FMA counts two; 0 for classes without a model) times
+ * the points each launch covers.  POLAR_EINVAL past the last class. */
+int polar_timing_flops(polar_ctx* ctx, int32_t index, double* flops);
 
 const char* polar_last_error(void);
 

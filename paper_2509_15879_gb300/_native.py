@@ -115,6 +115,7 @@ EXPORTS = {
                                     C.POINTER(polar_solver_opts), C.POINTER(polar_gummel_stats)]),
     "polar_gummel_destroy": (C.c_int, [C.c_void_p]),
     "polar_timing_enable": (C.c_int, [C.c_void_p, C.c_int32]),
+    "polar_timing_flops": (C.c_int, [C.c_void_p, C.c_int32, _dp]),
     "polar_timing_query": (C.c_int, [C.c_void_p, C.c_int32, C.c_char_p, C.c_size_t,
                                      C.POINTER(C.c_int64), _dp, _dp]),
     "polar_last_error": (C.c_char_p, []),
@@ -499,7 +500,7 @@ def polar_timing_enable(ctx: Ctx, on=True):
 
 
 def polar_timing_query(ctx: Ctx):
-    """Returns {kernel class: dict(launches, ms, bytes)} of the timed launches."""
+    """Returns {kernel class: dict(launches, ms, bytes, flops)} of the timed launches."""
     lib, out, k = load(), {}, 0
     while True:
         name = C.create_string_buffer(64)
@@ -507,7 +508,10 @@ def polar_timing_query(ctx: Ctx):
         rc = lib.polar_timing_query(ctx.handle, k, name, 64, C.byref(nl), C.byref(ms), C.byref(by))
         if rc != POLAR_OK:
             break
-        out[name.value.decode()] = dict(launches=nl.value, ms=ms.value, bytes=by.value)
+        fl = C.c_double()
+        _check(lib.polar_timing_flops(ctx.handle, k, C.byref(fl)))
+        out[name.value.decode()] = dict(launches=nl.value, ms=ms.value, bytes=by.value,
+                                        flops=fl.value)
         k += 1
     return out
 

@@ -74,13 +74,14 @@ struct DevLevel {
 struct PendingTimer {
   int kind;
   cudaEvent_t a, b;
-  double bytes;
+  double bytes, flops;
 };
 struct KernelStat {
   std::string name;
   int64_t launches = 0;
   double ms = 0.0;
   double bytes = 0.0;
+  double flops = 0.0;
 };
 
 }  // namespace
@@ -272,6 +273,7 @@ int resolve_timers(polar_ctx* c) {
     k.launches += 1;
     k.ms += ms;
     k.bytes += p.bytes;
+    k.flops += p.flops;
     c->ev_free.push_back(p.a);
     c->ev_free.push_back(p.b);
   }
@@ -288,22 +290,25 @@ int timed_begin(polar_ctx* c, cudaEvent_t* e) {
   return POLAR_OK;
 }
 
-int timed_end(polar_ctx* c, cudaEvent_t a, const char* name, double bytes) {
+int timed_end(polar_ctx* c, cudaEvent_t a, const char* name, double bytes, double flops) {
   if (!a) return POLAR_OK;
   cudaEvent_t b = take_event(c);
   CUDA_TRY(cudaEventRecord(b, c->st));
-  c->pending.push_back(PendingTimer{kind_index(c, name), a, b, bytes});
+  c->pending.push_back(PendingTimer{kind_index(c, name), a, b, bytes, flops});
   return POLAR_OK;
 }
 
-// LAUNCH with event timing under a kernel-class name and the launch's algorithmic bytes.
-#define TLAUNCH(name, bytes, expr)                 \
-  do {                                             \
-    cudaEvent_t ev_;                               \
-    TRY(timed_begin(c, &ev_));                     \
-    LAUNCH(expr);                                  \
-    TRY(timed_end(c, ev_, name, (double)(bytes))); \
+// LAUNCH with event timing under a kernel-class name, the launch's algorithmic bytes and
+// its arithmetic (flops per point as the kernel's source performs them, an FMA counting
+// two, times the points it covers; 0 where not modelled).
+#define TLAUNCHF(name, bytes, flops, expr)                             \
+  do {                                                                 \
+    cudaEvent_t ev_;                                                   \
+    TRY(timed_begin(c, &ev_));                                         \
+    LAUNCH(expr);                                                      \
+    TRY(timed_end(c, ev_, name, (double)(bytes), (double)(flops)));    \
   } while (0)
+#define TLAUNCH(name, bytes, expr) TLAUNCHF(name, bytes, 0.0, expr)
 
 void release(polar_ctx* c) {
   for (const PendingTimer& p : c->pending) {
@@ -539,7 +544,8 @@ int launch_refresh_all(polar_ctx* c, double* stamp = nullptr) {
   double pts = 0.0;
   for (const DevLevel& d : c->lv) pts += (double)d.sh.m * d.sh.n;
   // reads 6 FP64 coefficient arrays, writes diag and 4 factor arrays
-  TLAUNCH(stamp ? "refresh64" : "refresh", pts * (6.0 * 8 + 5.0 * sizeof(T)),
+  // about 47 flops per point (diagonal, pivot matrices, the three recurrences)
+  TLAUNCHF(stamp ? "refresh64" : "refresh", pts * (6.0 * 8 + 5.0 * sizeof(T)), 47.0 * pts,
           launch_refresh<T>(c->v64.data(), vt.data(), c->nlev(), c->sp, c->ws, c->cs, stamp));
   return POLAR_OK;
 }
@@ -596,14 +602,17 @@ int vcycle(polar_ctx* c, const T* b, T* x) {
     const double po = (double)s.no * s.n, pe = (double)s.ne * s.n;
     // algorithmic words: odd line solve reads b and 4 factors, writes x (6 per point);
     // even: b, w, e, the odd neighbours, 4 factors, writes x (9); restriction reads
-    // w, e, ia, ib of the odd rings and x of the even ones, writes the coarse rhs
-    TLAUNCH(nm("ring_pre_odd", l), 6 * B * po,
+    // w, e, ia, ib of the odd rings and x of the even ones, writes the coarse rhs.
+    // Flops per point: the line solve 13 (forward 3 + replay 2, 1/u y 1, backward 3 +
+    // replay 2, Sherman-Morrison 2), the right-hand side 0 / 5 / 13 (b only / plain
+    // neighbours / corrected odd neighbours); restriction 11 per coarse point
+    TLAUNCHF(nm("ring_pre_odd", l), 6 * B * po, 13.0 * po,
             launch_ring<T>(L[l], L[l + 1], bof(l), xof(l), nullptr, par, 1, RING_PRE, done, c->cs,
                            tile<T>(c, l, RING_PRE, 1)));
-    TLAUNCH(nm("ring_pre_even", l), 9 * B * pe,
+    TLAUNCHF(nm("ring_pre_even", l), 9 * B * pe, 18.0 * pe,
             launch_ring<T>(L[l], L[l + 1], bof(l), xof(l), nullptr, par, 0, RING_PRE, done, c->cs,
                            tile<T>(c, l, RING_PRE, 0)));
-    TLAUNCH(nm("restrict", l), B * (4 * po + 2 * pe),
+    TLAUNCHF(nm("restrict", l), B * (4 * po + 2 * pe), 11.0 * L[l + 1].sh.m * s.n,
             launch_restrict<T>(L[l], L[l + 1], xof(l), coarse_b<T>(c, l + 1), par, done,
                                c->cs));
   }
@@ -614,10 +623,10 @@ int vcycle(polar_ctx* c, const T* b, T* x) {
     const double po = (double)s.no * s.n, pe = (double)s.ne * s.n;
     // even rings after the correction also read x, ia, ib of the odd rings and the
     // coarse solution (8 per even point + 3 per odd point + 1 per coarse point)
-    TLAUNCH(nm("ring_post_even", l), B * (8 * pe + 3 * po + pe),
+    TLAUNCHF(nm("ring_post_even", l), B * (8 * pe + 3 * po + pe), 26.0 * pe,
             launch_ring<T>(L[l], L[l + 1], bof(l), xof(l), coarse_x<T>(c, l + 1),
                            par, 0, RING_POST, done, c->cs, tile<T>(c, l, RING_POST, 0)));
-    TLAUNCH(nm("ring_post_odd", l), 9 * B * po,
+    TLAUNCHF(nm("ring_post_odd", l), 9 * B * po, 18.0 * po,
             launch_ring<T>(L[l], L[l + 1], bof(l), xof(l), nullptr, par, 1, RING_POST, done, c->cs,
                            tile<T>(c, l, RING_POST, 1)));
   }
@@ -742,15 +751,16 @@ int bicg_iteration(polar_ctx* c, CondHandle cond) {
   const size_t nv = c->nv();
   const double B = sizeof(T), pts = (double)c->m * c->n;
   TRY(vcycle<T>(c, k.p, k.phat));
-  // stencil with dot: reads x, diag, 4 couplings, d1; writes y (8 words per point)
-  TLAUNCH(tname<T>("stencil_dot"), 8 * B * pts, launch_apply_dot<T>(L0, c->par(), k.phat, k.v, k.rhat, 0, c->cs, red));
-  TLAUNCH(tname<T>("bicg_s"), 3 * B * nv, launch_bicg_s<T>(nv, k.r, k.v, k.s, c->cs, red));
+  // stencil with dot: reads x, diag, 4 couplings, d1; writes y (8 words per point);
+  // 12 flops per point (the 5-point row 10, the dot 2)
+  TLAUNCHF(tname<T>("stencil_dot"), 8 * B * pts, 12.0 * pts, launch_apply_dot<T>(L0, c->par(), k.phat, k.v, k.rhat, 0, c->cs, red));
+  TLAUNCHF(tname<T>("bicg_s"), 3 * B * nv, 2.0 * pts, launch_bicg_s<T>(nv, k.r, k.v, k.s, c->cs, red));
   TRY(vcycle<T>(c, k.s, k.shat));
-  TLAUNCH(tname<T>("stencil_dot"), 8 * B * pts, launch_apply_dot<T>(L0, c->par(), k.shat, k.t, k.s, 1, c->cs, red));
-  TLAUNCH(tname<T>("bicg_update"), 9 * B * nv,
+  TLAUNCHF(tname<T>("stencil_dot"), 8 * B * pts, 12.0 * pts, launch_apply_dot<T>(L0, c->par(), k.shat, k.t, k.s, 1, c->cs, red));
+  TLAUNCHF(tname<T>("bicg_update"), 9 * B * nv, 9.0 * pts,
           launch_bicg_update<T>(nv, k.d, k.phat, k.shat, k.r, k.s, k.t, k.rhat, L0.diag,
                                 L0.sc, c->cs, red));
-  TLAUNCH(tname<T>("bicg_p"), 4 * B * nv, launch_bicg_p<T>(nv, k.p, k.r, k.v, cond, c->cs, red));
+  TLAUNCHF(tname<T>("bicg_p"), 4 * B * nv, 4.0 * pts, launch_bicg_p<T>(nv, k.p, k.r, k.v, cond, c->cs, red));
   return POLAR_OK;
 }
 
@@ -765,11 +775,11 @@ int cg_iteration(polar_ctx* c, CondHandle cond) {
   const size_t nv = c->nv();
   const double B = sizeof(T), pts = (double)c->m * c->n;
   TRY(vcycle<T>(c, k.r, k.phat));
-  TLAUNCH(tname<T>("cg_rho"), 2 * B * nv, launch_cg_rho<T>(nv, k.r, k.phat, c->cs, red));
-  TLAUNCH(tname<T>("cg_p"), 3 * B * nv, launch_cg_p<T>(nv, k.p, k.phat, c->cs, red));
+  TLAUNCHF(tname<T>("cg_rho"), 2 * B * nv, 2.0 * pts, launch_cg_rho<T>(nv, k.r, k.phat, c->cs, red));
+  TLAUNCHF(tname<T>("cg_p"), 3 * B * nv, 2.0 * pts, launch_cg_p<T>(nv, k.p, k.phat, c->cs, red));
   // stencil with dot: reads p, diag, 4 couplings; writes q (7 words per point)
-  TLAUNCH(tname<T>("stencil_dot"), 7 * B * pts, launch_apply_dot<T>(L0, c->par(), k.p, k.v, k.p, 0, c->cs, red));
-  TLAUNCH(tname<T>("cg_update"), 7 * B * nv,
+  TLAUNCHF(tname<T>("stencil_dot"), 7 * B * pts, 12.0 * pts, launch_apply_dot<T>(L0, c->par(), k.p, k.v, k.p, 0, c->cs, red));
+  TLAUNCHF(tname<T>("cg_update"), 7 * B * nv, 5.0 * pts,
           launch_cg_update<T>(nv, k.d, k.p, k.r, k.v, L0.diag, L0.sc, cond, c->cs, red));
   return POLAR_OK;
 }
@@ -793,7 +803,8 @@ int bicg_begin(polar_ctx* c, CondHandle cond) {
 
 int resid(polar_ctx* c) {
   const double pts = (double)c->m * c->n;
-  TLAUNCH("resid64", 8.0 * 8 * pts, launch_resid64(c->v64[0], c->par(), c->X, c->e, c->r64, c->cs, c->red()));
+  // 12 flops per point: the 5-point row, the difference from e, the Jacobi scaling
+  TLAUNCHF("resid64", 8.0 * 8 * pts, 12.0 * pts, launch_resid64(c->v64[0], c->par(), c->X, c->e, c->r64, c->cs, c->red()));
   return POLAR_OK;
 }
 
@@ -807,7 +818,8 @@ int correct(polar_ctx* c) {
 int rhs(polar_ctx* c) {
   const double* srcs[4] = {c->vsrc[0], c->vsrc[1], c->vsrc[2], c->vsrc[3]};
   const double* bnds[4] = {c->bnd[0], c->bnd[1], c->bnd[2], c->bnd[3]};
-  TLAUNCH("rhs", (8.0 + c->nsrc) * 8 * c->m * c->n,
+  // flops per point: the explicit half 12, the sources and boundary terms of both levels
+  TLAUNCHF("rhs", (8.0 + c->nsrc) * 8 * c->m * c->n, (12.0 + 4.0 * c->nsrc) * c->m * c->n,
           launch_rhs(c->v64[0], c->sp, c->U, c->nsrc, srcs, bnds, c->e, c->cs, c->red()));
   return POLAR_OK;
 }
@@ -2842,6 +2854,15 @@ int polar_timing_enable(polar_ctx* c, int32_t on) {
   TRY(resolve_timers(c));
   c->kstats.clear();
   c->timing = on != 0;
+  return POLAR_OK;
+}
+
+int polar_timing_flops(polar_ctx* c, int32_t index, double* flops) {
+  if (!c || !flops) return fail(POLAR_EINVAL, "null argument");
+  CUDA_TRY(cudaSetDevice(c->device));
+  TRY(resolve_timers(c));
+  if (index < 0 || index >= (int32_t)c->kstats.size()) return fail(POLAR_EINVAL, "no such kernel class");
+  *flops = c->kstats[index].flops;
   return POLAR_OK;
 }
 
