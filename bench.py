@@ -497,9 +497,15 @@ def run_native(args):
         pool_full.close()
         pool_full.join()
         err["kind"] = ("relative max-norm difference from the oracle's step (sparse LU + "
-                       "extended-precision refinement) from the same state")
+                       "extended-precision refinement) from the same state; v_weighted_l2: "
+                       "the same difference in the L2 norm weighted by the control volumes")
+        from oracle import polar_oracle as po
+        V = po.Geometry(prob.r, prob.theta).V
         for nm, states in acc.items():
             err[nm] = {str(k): rel_max(states[k], ref[k]) for k in acc_levels}
+            err[nm + "_v_weighted_l2"] = {
+                str(k): float(np.sqrt(np.sum(V * (states[k] - ref[k]) ** 2) /
+                                      np.sum(V * ref[k] ** 2))) for k in acc_levels}
     elif w["check"] == "rows":
         rows = sample_rows(prob)
         err["kind"] = (f"Jacobi-scaled residual max|(e - A U)_i| / A_ii / max|U| of the GPU's "

@@ -23,6 +23,12 @@ def _rel(a, b):
     return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
 
 
+def _rel_wl2(prob, a, b):
+    """Relative L2 difference weighted by the control volumes V (origin disk included)."""
+    V = po.Geometry(prob.r, prob.theta).V
+    return float(np.sqrt(np.sum(V * (a - b) ** 2) / max(np.sum(V * b ** 2), 1e-300)))
+
+
 def _small_continuity(m, n, K=4, seed=21, pe=6.0, theta_w=0.5):
     return pi.continuity_problem(m, n, K, seed, theta_w=theta_w, pe_target=pe, d_amp=1.3,
                                  delta=0.2)
@@ -79,7 +85,8 @@ def test_config1_full_run(precision, tol):
     assert all(s["status"] == 0 for s in stats)
     U, t = P.polar_get_state(ctx)
     assert abs(t - 1.0) < 1e-15
-    print(f"PARITY C1 32x64 100 steps precision {precision}: {_rel(U, ref):.2e} (bar {tol:g})")
+    print(f"PARITY C1 32x64 100 steps precision {precision}: {_rel(U, ref):.2e} (bar {tol:g}), "
+          f"V-weighted L2 {_rel_wl2(prob, U, ref):.2e}")
     assert _rel(U, ref) < tol
 
 
@@ -95,14 +102,15 @@ def test_steps_match_oracle(name, make, K, precision, tol):
     prob = make()
     refs = _oracle_levels(prob, K)
     ctx = driver.create(prob, precision)
-    worst = 0.0
+    worst = worst_l2 = 0.0
     for k in range(K):
         driver.advance(ctx, prob, k, k + 1)
         U, _ = P.polar_get_state(ctx)
         worst = max(worst, _rel(U, refs[k]))
+        worst_l2 = max(worst_l2, _rel_wl2(prob, U, refs[k]))
         assert _rel(U, refs[k]) < tol, (name, k, _rel(U, refs[k]))
     print(f"PARITY {name} {prob.m}x{prob.n} {K} steps precision {precision}: worst {worst:.2e} "
-          f"(bar {tol:g})")
+          f"(bar {tol:g}), V-weighted L2 {worst_l2:.2e}")
 
 
 def _stiff_rings():
