@@ -276,14 +276,16 @@ int polar_face_drift(polar_ctx* ctx, double mobility, const double* g, double* v
  * their other coefficients stay as set.  One polar_gummel_step advances the pair from
  * t[0] to t[1] by Gummel's iteration: phi from the current densities
  * (polar_solve_steady, sources weighted by w_phi), the drifts from phi
- * (polar_face_drift; the carriers' operators re-assembled on the host), both carriers one
+ * (the face-drift kernel; the carriers' operators and multigrid hierarchies re-assembled
+ * on the device, after which they take the Krylov inner solve), both carriers one
  * theta-step from their state at t[0] with that drift held over the step (one 2-instance
  * polar_batch; w[c] holds 2 x nsrc weights of carrier c at t[0] and t[1]); repeated
  * until max|phi_j - phi_{j-1}| / max|phi_j| <= tol (the absolute change when phi_j = 0),
  * at most max_iter potential solves.  The carriers then hold t[1]'s densities and phi
- * the potential of those densities.  The object's device buffers (3 N doubles) come from
- * the potential's allocator and are freed with its context; destroy the object before
- * any of its contexts.
+ * the potential of those densities.  The object's device buffers (3 N doubles from the
+ * potential's allocator; each carrier's face D, reaction and drift faces from its own)
+ * are freed with those contexts; destroy the object before any of its contexts.  The
+ * carriers' face D and reaction are those set when the object was created.
  * Errors: POLAR_EINVAL (mismatched meshes or scheme, bad slots, mobility, tol or
  * max_iter), POLAR_ESTATE (coefficients or states missing), POLAR_ENOCONV (max_iter
  * reached: the carriers hold the last iterate), errors of the solves. */

@@ -15,7 +15,7 @@ ROOT = os.path.dirname(HERE)
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libpolar.so")
 SOURCES = ["polar_kernels.cu", "polar_mg.cu", "polar_api.cu", "polar_host.cpp",
-           "polar_noalloc.cu", "polar_fft.cu"]
+           "polar_noalloc.cu", "polar_fft.cu", "polar_assemble.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
          "-I", os.path.join(ROOT, "include")]

@@ -97,6 +97,12 @@ struct polar_gummel {
   double* save[2] = {nullptr, nullptr};    // carriers' states at the start of the step
   double* phi_prev = nullptr;              // previous iterate of the potential
   double* change = nullptr;                // max |phi - phi_prev|, max |phi|
+  // per carrier: its D faces and reaction on the device, the drift faces
+  double* dr[2] = {nullptr, nullptr};
+  double* dt[2] = {nullptr, nullptr};
+  double* b[2] = {nullptr, nullptr};
+  double* vr[2] = {nullptr, nullptr};
+  double* vt[2] = {nullptr, nullptr};
 };
 struct polar_batch {
   std::vector<polar_ctx*> ctx;
@@ -2249,6 +2255,50 @@ int reassemble(polar_ctx* c) {
   return POLAR_OK;
 }
 
+// The same from coefficients already on the device (conservative scheme): level 0 and
+// the radial hierarchy assembled by kernels on the context's stream.  The operator is
+// taken as non-separable (Krylov inner solve); `symmetric` says whether it has no drift.
+int reassemble_device(polar_ctx* c, const AsmIn& in, bool symmetric) {
+  auto lev = [&](int l) {
+    DevLevel& d = c->lv[l];
+    return CoarsenLevel{d.sh, d.w, d.e, d.s, d.nn, d.rs, d.vol, d.o, d.ia, d.ib, d.sc};
+  };
+  DevLevel& d0 = c->lv[0];
+  LAUNCH(launch_assemble_level0(in, d0.sh, d0.vol, d0.w, d0.e, d0.s, d0.nn, d0.rs, d0.o, d0.sc,
+                                c->st));
+  for (int l = 0; l + 1 < c->nlev(); ++l) LAUNCH(launch_coarsen(lev(l), lev(l + 1), c->st));
+  if (c->precision == POLAR_MIXED) {
+    for (DevLevel& d : c->lv) {
+      const double* s64[] = {d.w, d.e, d.s, d.nn, d.ia, d.ib};
+      float* s32[] = {d.w32, d.e32, d.s32, d.nn32, d.ia32, d.ib32};
+      for (int a = 0; a < 6; ++a) LAUNCH(launch_to_float(d.sh.nv, s64[a], s32[a], c->st));
+      LAUNCH(launch_to_float((size_t)c->n, d.o, d.o32, c->st));
+    }
+  }
+  c->symmetric = symmetric;
+  c->separable = false;
+  c->cur_alpha = c->cur_beta = -1.0;
+  CUDA_TRY(cudaMemsetAsync(&c->ks->sticky64, 0, sizeof(int), c->st));
+  if (c->stamp64) CUDA_TRY(cudaMemsetAsync(c->stamp64, 0, 2 * sizeof(double), c->st));
+  c->graph_ok = false;
+  c->generation += 1;
+  CUDA_TRY(cudaStreamSynchronize(c->st));
+  return POLAR_OK;
+}
+
+// Radii and angles of the mesh on the device (r, then theta, then n scratch values).
+int ensure_mesh_dev(polar_ctx* c) {
+  if (c->mesh_dev) return POLAR_OK;
+  const int m = c->m, n = c->n;
+  TRY(dalloc(c, &c->mesh_dev, (size_t)m + 2 + 2 * (size_t)n));
+  CUDA_TRY(cudaStreamSynchronize(c->st));
+  std::vector<double> mesh(c->r);
+  mesh.insert(mesh.end(), c->theta.begin(), c->theta.end());
+  CUDA_TRY(cudaMemcpy(c->mesh_dev, mesh.data(), mesh.size() * sizeof(double),
+                      cudaMemcpyHostToDevice));
+  return POLAR_OK;
+}
+
 // (Re)builds the batch's step graph: plan pass, arena upload, capture pass.
 int build_batch_graph(polar_batch* b) {
   CUDA_TRY(cudaStreamSynchronize(b->st));  // no launch of the old graph still reads the arena
@@ -2556,14 +2606,7 @@ int polar_face_drift(polar_ctx* c, double mobility, const double* g, double* v_r
   if (!std::isfinite(mobility)) return fail(POLAR_EINVAL, "non-finite mobility");
   CUDA_TRY(cudaSetDevice(c->device));
   const int m = c->m, n = c->n;
-  if (!c->mesh_dev) {
-    TRY(dalloc(c, &c->mesh_dev, (size_t)m + 2 + 2 * (size_t)n));
-    CUDA_TRY(cudaStreamSynchronize(c->st));
-    std::vector<double> mesh(c->r);
-    mesh.insert(mesh.end(), c->theta.begin(), c->theta.end());
-    CUDA_TRY(cudaMemcpy(c->mesh_dev, mesh.data(), mesh.size() * sizeof(double),
-                        cudaMemcpyHostToDevice));
-  }
+  TRY(ensure_mesh_dev(c));
   double* gdev = c->mesh_dev + m + 2 + n;
   CUDA_TRY(cudaMemcpyAsync(gdev, g, n * sizeof(double),
                            memory == POLAR_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
@@ -2616,6 +2659,27 @@ int polar_gummel_create(polar_ctx* phi, polar_ctx* electrons, polar_ctx* holes,
   if (rc == POLAR_OK) rc = dalloc(phi, &G->save[1], nv);
   if (rc == POLAR_OK) rc = dalloc(phi, &G->phi_prev, nv);
   if (rc == POLAR_OK) rc = dalloc(phi, &G->change, 2);
+  if (rc == POLAR_OK) rc = ensure_mesh_dev(phi);
+  const size_t nf = (size_t)(phi->m + 1) * phi->n, nt = (size_t)phi->m * phi->n;
+  for (int k = 0; k < 2 && rc == POLAR_OK; ++k) {
+    polar_ctx* c = G->car[k];
+    const HostCoeffs& K = c->hk;
+    rc = dalloc(c, &G->vr[k], nf);
+    if (rc == POLAR_OK) rc = dalloc(c, &G->vt[k], nt);
+    if (rc == POLAR_OK && !K.dr.empty()) rc = dalloc(c, &G->dr[k], nf);
+    if (rc == POLAR_OK && !K.dt.empty()) rc = dalloc(c, &G->dt[k], nt);
+    if (rc == POLAR_OK && !K.b.empty()) rc = dalloc(c, &G->b[k], K.b.size());
+    if (rc == POLAR_OK) {
+      cudaError_t e = cudaStreamSynchronize(c->st);  // zeroed before the copies
+      if (e == cudaSuccess && G->dr[k])
+        e = cudaMemcpy(G->dr[k], K.dr.data(), nf * sizeof(double), cudaMemcpyHostToDevice);
+      if (e == cudaSuccess && G->dt[k])
+        e = cudaMemcpy(G->dt[k], K.dt.data(), nt * sizeof(double), cudaMemcpyHostToDevice);
+      if (e == cudaSuccess && G->b[k])
+        e = cudaMemcpy(G->b[k], K.b.data(), K.b.size() * sizeof(double), cudaMemcpyHostToDevice);
+      if (e != cudaSuccess) rc = fail(POLAR_ECUDA, cudaGetErrorString(e));
+    }
+  }
   if (rc == POLAR_OK) rc = polar_batch_create(G->car, 2, electrons->st, &G->pair);
   if (rc != POLAR_OK) {
     delete G;  // the buffers stay with the potential's context until it is destroyed
@@ -2658,6 +2722,8 @@ int polar_gummel_step(polar_gummel* G, const double* t, double theta, const doub
   std::vector<double> g(n, 0.0);
   for (int q = 0; q < phi->nsrc; ++q)
     for (int j = 0; j < n; ++j) g[j] += w_phi[q] * phi->bnd_host[q][j];
+  double* gdev = phi->mesh_dev + m + 2 + n;
+  CUDA_TRY(cudaMemcpy(gdev, g.data(), n * sizeof(double), cudaMemcpyHostToDevice));
   const int src_slot[2] = {G->d.src_electrons, G->d.src_holes};
   double change = 0.0;
   int it = 0;
@@ -2686,13 +2752,18 @@ int polar_gummel_step(polar_gummel* G, const double* t, double theta, const doub
     }
     CUDA_TRY(cudaMemcpyAsync(G->phi_prev, phi->U, nv * sizeof(double), cudaMemcpyDeviceToDevice,
                              phi->st));
-    // drift of each carrier from the potential, the carriers re-assembled with it
+    // drift of each carrier from the potential (face kernel), the carriers' operators and
+    // hierarchies re-assembled with it on the device
+    LAUNCH(launch_unpack(phi->sh0(), phi->U, nullptr, phi->io, phi->st));
+    for (int k = 0; k < 2; ++k)
+      LAUNCH(launch_face_drift(m, n, phi->io, phi->mesh_dev, phi->mesh_dev + m + 2, gdev,
+                               G->d.mobility[k], G->vr[k], G->vt[k], phi->st));
+    CUDA_TRY(cudaStreamSynchronize(phi->st));
     for (int k = 0; k < 2; ++k) {
-      HostCoeffs& K = car[k]->hk;
-      K.vr.resize(nf);
-      K.vt.resize(nt);
-      TRY(polar_face_drift(phi, G->d.mobility[k], g.data(), K.vr.data(), K.vt.data(), POLAR_HOST));
-      TRY(reassemble(car[k]));
+      const HostCoeffs& K = car[k]->hk;
+      const AsmIn in{m, n, phi->mesh_dev, phi->mesh_dev + m + 2, G->dr[k], G->dt[k], K.d_const,
+                     G->vr[k], G->vt[k], G->b[k], 0.0};
+      TRY(reassemble_device(car[k], in, G->d.mobility[k] == 0.0));
       CUDA_TRY(cudaMemcpyAsync(car[k]->U, G->save[k], nv * sizeof(double), cudaMemcpyDeviceToDevice,
                                car[k]->st));
       CUDA_TRY(cudaStreamSynchronize(car[k]->st));

@@ -567,6 +567,33 @@ int launch_check_finite(size_t n, const double* a, cudaStream_t st, Reduce red);
 // layout, r (m+2) and theta (n) the mesh, g (n) the values on r = 1
 int launch_face_drift(int m, int n, const double* u, const double* r, const double* th,
                       const double* g, double mobility, double* vr, double* vt, cudaStream_t st);
+// Device assembly of the conservative operator (polar_assemble.cu).  Coefficients in the
+// caller's face layouts (any pointer may be null: D = d_const, no drift, b = b_const).
+struct AsmIn {
+  int m, n;
+  const double* r;   // m + 2 radii
+  const double* th;  // n angles
+  const double* dr;  // (m+1) n radial-face D
+  const double* dt;  // m n angular-face D
+  double d_const;
+  const double* vr;  // (m+1) n radial-face drift
+  const double* vt;  // m n angular-face drift
+  const double* b;   // N node reaction (interface order)
+  double b_const;
+};
+// level 0: couplings w, e, s, nn and row sums rs of every ring node (split layout), the
+// origin couplings o (n) and scalars sc[2] = sum_j o_j, sc[4] = rs0 (vol and sc[3] static)
+int launch_assemble_level0(const AsmIn& in, const Shape& sh, const double* vol, double* w,
+                           double* e, double* s, double* nn, double* rs, double* o, double* sc,
+                           cudaStream_t st);
+// one level of the radial hierarchy: the fine level's odd-ring weights ia, ib, then the
+// coarse level's couplings, row sums, volumes, origin couplings and scalars
+struct CoarsenLevel {
+  Shape sh;
+  double *w, *e, *s, *nn, *rs, *vol, *o, *ia, *ib, *sc;
+};
+int launch_coarsen(const CoarsenLevel& f, const CoarsenLevel& c, cudaStream_t st);
+
 // out[0] = max_k |a_k - b_k|, out[1] = max_k |a_k| over n doubles (out zeroed first; NaN
 // counts as +inf)
 int launch_max_change(size_t n, const double* a, const double* b, double* out, cudaStream_t st);

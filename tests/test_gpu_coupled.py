@@ -134,3 +134,50 @@ def test_gummel_rejects_bad_setups():
     g = P.polar_gummel_create(ph, el, ho, cp.mobility, 0, 1, max_iter=1)
     with pytest.raises(P.PolarError):        # one potential solve cannot test convergence
         P.polar_gummel_step(g, 0.0, 0.02, 0.5, [1.0, 1.0], [1.0, 1.0], cp.w_phi)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_device_assembly_matches_host_assembly(precision):
+    # A Gummel step with an enormous tol stops after its second potential solve, so the
+    # carriers keep the operators the step assembled on the device from phi_0, the
+    # potential of the initial densities.  The same drift, built here through the host
+    # path (polar_face_drift to host arrays, polar_set_coeffs), must give the same
+    # operator and the same next step
+    P, driver = _lib()
+    cp = pi.coupled_pair(m=24, n=48, K=3)
+    prec = P.POLAR_FP64 if precision == "fp64" else P.POLAR_MIXED
+    ph = driver.create(cp.phi, prec)
+    el = driver.create(cp.electrons, prec)
+    ho = driver.create(cp.holes, prec)
+    P.polar_set_state(ph, np.zeros(cp.phi.N), 0.0)
+    g = P.polar_gummel_create(ph, el, ho, cp.mobility, cp.slots[0], cp.slots[1], tol=1e300,
+                              max_iter=5)
+    w1 = [1.0, 1.0]
+    st, _ = P.polar_gummel_step(g, cp.t[0], cp.t[1], cp.theta_w, w1, w1, cp.w_phi)
+    assert st["iters"] == 2
+    # phi_0 from the initial densities, through the host upload of the sources
+    src = [cp.electrons.u0, cp.holes.u0, cp.phi.src[2]]
+    phi0 = driver.create(replace(cp.phi, src=src), prec)
+    P.polar_set_state(phi0, np.zeros(cp.phi.N), 0.0)
+    P.polar_solve_steady(phi0, cp.w_phi)
+    gb = sum(wq * bq for wq, bq in zip(cp.w_phi, cp.phi.bnd))
+    rng = np.random.default_rng(11)
+    x = rng.standard_normal(cp.phi.N)
+    for k, (ctx, prob) in enumerate(((el, cp.electrons), (ho, cp.holes))):
+        vr, vt = P.polar_face_drift(phi0, cp.mobility[k], gb)
+        host = driver.create(replace(prob, v_rface=vr, v_tface=vt), prec)
+        y_dev = P.polar_apply_operator(ctx, 50.0, 0.5, x)
+        y_host = P.polar_apply_operator(host, 50.0, 0.5, x)
+        op_err = _rel(y_dev, y_host)
+        # one more step of both from the same state
+        P.polar_set_state(ctx, prob.u0, cp.t[0])
+        P.polar_set_state(host, prob.u0, cp.t[0])
+        sd, _ = P.polar_advance(ctx, cp.t[0:2], cp.theta_w, np.ones((2, 1)))
+        sh, _ = P.polar_advance(host, cp.t[0:2], cp.theta_w, np.ones((2, 1)))
+        st_err = _rel(P.polar_get_state(ctx)[0], P.polar_get_state(host)[0])
+        print(f"PARITY device vs host assembly {precision} carrier {k}: operator {op_err:.2e}, "
+              f"step {st_err:.2e}, iterations {sd[0]['iters']} / {sh[0]['iters']}")
+        assert op_err <= 1e-13
+        assert st_err <= (1e-12 if precision == "fp64" else 1e-9)
+        assert abs(sd[0]["iters"] - sh[0]["iters"]) <= 1
+    P.polar_gummel_destroy(g)
