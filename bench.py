@@ -620,6 +620,98 @@ def run_native(args):
     return 0
 
 
+# ------------------------------------------------------------------------- carrier pair
+def _pair_oracle_step(args_):
+    """One coupled oracle step of the pair recipe on an m x n mesh (timing sample)."""
+    m, n = args_
+    os.environ.setdefault("OMP_NUM_THREADS", "1")
+    import polar_inputs as pi
+    from oracle import coupled as oc
+    cp = pi.coupled_pair(m=m, n=n, K=1)
+    w = [np.array([1.0, 1.0]), np.array([1.0, 1.0])]
+    t0 = time.perf_counter()
+    _, _, iters, _, ok = oc.gummel_step(cp.phi, [cp.electrons, cp.holes],
+                                        [cp.electrons.u0, cp.holes.u0], cp.t[0], cp.t[1],
+                                        cp.theta_w, w, cp.w_phi, cp.mobility, cp.slots, 1e-10, 60)
+    return 2 * cp.electrons.N, time.perf_counter() - t0, iters
+
+
+def run_pair(args):
+    """The electron-hole pair with a self-consistent potential (Gummel's iteration per
+    theta-step, stop at a potential change of 1e-10): the coupled-pair recipe on a 512 x 1024
+    mesh (or --mesh M N).  value = carrier updates (2 N per step) / device time."""
+    import torch
+    import polar_inputs as pi
+    import paper_2509_15879_gb300 as P
+    from paper_2509_15879_gb300 import driver
+    rank = env_int("RANK", 0)
+    if rank != 0:  # one pair per job: the other ranks have nothing to shard
+        return 0
+    m, n = args.mesh or (512, 1024)
+    cores = host_cores()
+    sample = (64, 128)
+    pool = None
+    if not args.no_cpu_baseline:  # spawn before this process touches the GPU
+        pool = mp.get_context("spawn").Pool(cores)
+        pool.map(_noop, range(cores), chunksize=1)
+    torch.cuda.set_device(env_int("LOCAL_RANK", 0))
+    K, W = args.steps, args.warmup
+    cp = pi.coupled_pair(m=m, n=n, K=K + W)
+    precision = P.POLAR_MIXED if args.precision == "mixed" else P.POLAR_FP64
+    stream = torch.cuda.current_stream()
+    ph = driver.create(cp.phi, precision, stream=stream.cuda_stream)
+    el = driver.create(cp.electrons, precision, stream=stream.cuda_stream)
+    ho = driver.create(cp.holes, precision, stream=stream.cuda_stream)
+    P.polar_set_state(ph, np.zeros(cp.phi.N), 0.0)
+    g = P.polar_gummel_create(ph, el, ho, cp.mobility, cp.slots[0], cp.slots[1], tol=1e-10,
+                              max_iter=60)
+    w = [1.0, 1.0]
+    for k in range(W):
+        P.polar_gummel_step(g, cp.t[k], cp.t[k + 1], cp.theta_w, w, w, cp.w_phi)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(env_int("LOCAL_RANK", 0))
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    iters = []
+    e0.record(stream)
+    for k in range(W, W + K):
+        st, _ = P.polar_gummel_step(g, cp.t[k], cp.t[k + 1], cp.theta_w, w, w, cp.w_phi)
+        iters.append(st["iters"])
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    updates = 2 * cp.electrons.N * K
+    line = {"metric": METRIC, "value": updates / (ms * 1e-3), "unit": UNIT, "n_gpus": 1,
+            "steps": K, "warmup": W, "ms_per_step": ms / K, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if precision == P.POLAR_FP64 else "f32+f64", "data": "synthetic",
+            "config": {"workload": f"electron-hole pair with a Poisson potential, {m} x {n} "
+                                   f"stretched adaptive mesh, Gummel's iteration to a "
+                                   f"potential change of 1e-10 per theta-step; updates = "
+                                   f"both carriers' unknowns per step",
+                       "m": m, "n": n, "N": cp.electrons.N, "precision": args.precision},
+            "potential_solves_per_step": float(np.mean(iters)), "clocks": clk}
+    if pool is not None:
+        t0 = time.perf_counter()
+        res, rounds = [], 0
+        while rounds == 0 or time.perf_counter() - t0 < args.cpu_budget:
+            res += pool.map(_pair_oracle_step, [sample] * cores, chunksize=1)
+            rounds += 1
+        wall = time.perf_counter() - t0
+        pool.close()
+        pool.join()
+        upd = sum(r[0] for r in res)
+        line["cpu_baseline"] = {
+            "value": upd / wall, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "single_core_value": upd / sum(r[1] for r in res),
+            "sample": f"{len(res)} coupled oracle steps (sparse LU per potential and carrier "
+                      f"solve, {np.mean([r[2] for r in res]):.0f} potential solves each) on "
+                      f"the {sample[0]} x {sample[1]} version of the recipe, {cores} workers"}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 # ------------------------------------------------------------------------- batch
 def run_batch(args):
     """The 256-instance sweep: continuity equation on uneven adaptive meshes (m log-uniform
@@ -768,14 +860,16 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--compare", type=int, default=1,
                     help="also time the other precision on the same steps")
-    ap.add_argument("--workload", choices=["c5", "c3", "c2", "c1", "batch"], default="c5",
+    ap.add_argument("--workload", choices=["c5", "c3", "c2", "c1", "batch", "pair"], default="c5",
                     help="c5 (default): continuity 8192 x 16384; c3: continuity 2048 x 4096; "
                          "c2: parabolic 512 x 1024; c1: parabolic 32 x 64 (direct solve); "
-                         "batch: the 256-instance sweep")
+                         "batch: the 256-instance sweep; pair: the electron-hole pair "
+                         "with a Poisson potential")
     ap.add_argument("--profile-step", action="store_true",
                     help="run one eager step of --workload inside a profiler range")
     ap.add_argument("--mesh", type=int, nargs=2, metavar=("M", "N"),
-                    help="with --profile-step: the workload's recipe on an M x N mesh")
+                    help="with --profile-step: the workload's recipe on an M x N mesh; with "
+                         "--workload pair: the pair's mesh (default 512 x 1024)")
     ap.add_argument("--instances", type=int, default=256)
     args = ap.parse_args()
     if args.impl == "reference":
@@ -784,6 +878,8 @@ def main():
         return run_profile_step(args)
     if args.workload == "batch":
         return run_batch(args)
+    if args.workload == "pair":
+        return run_pair(args)
     return run_native(args)
 
 

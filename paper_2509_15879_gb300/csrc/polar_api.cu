@@ -2275,13 +2275,19 @@ int reassemble_device(polar_ctx* c, const AsmIn& in, bool symmetric) {
       LAUNCH(launch_to_float((size_t)c->n, d.o, d.o32, c->st));
     }
   }
-  c->symmetric = symmetric;
+  // The arrays keep their addresses, so the captured graphs stay valid unless the solver's
+  // structure changes (CG for a symmetric operator, BiCGStab otherwise; a separable
+  // operator's direct solve is left through choose_method).  The next step refreshes the
+  // factors: cur_alpha is reset, and so are the mixed path's FP64 stamp and countdown.
+  if (symmetric != c->symmetric) {
+    c->symmetric = symmetric;
+    c->graph_ok = false;
+    c->generation += 1;
+  }
   c->separable = false;
   c->cur_alpha = c->cur_beta = -1.0;
   CUDA_TRY(cudaMemsetAsync(&c->ks->sticky64, 0, sizeof(int), c->st));
   if (c->stamp64) CUDA_TRY(cudaMemsetAsync(c->stamp64, 0, 2 * sizeof(double), c->st));
-  c->graph_ok = false;
-  c->generation += 1;
   CUDA_TRY(cudaStreamSynchronize(c->st));
   return POLAR_OK;
 }
