@@ -20,13 +20,19 @@ component at radial face (i+1/2, j) is -s (phi_{i+1,j} - phi_{i,j}) / h_{i+1}, w
 phi_{0,j} the origin value and phi_{m+1,j} the Dirichlet value; the angular component at
 angular face (i, j+1/2) is -s (phi_{i,j+1} - phi_{i,j}) / (r_i mu_{j+1}), periodic in j.
 
-Gummel's iteration for one theta-step t0 -> t1 (the drift held over the step):
-    phi_0 = Poisson(n^k, p^k)
+Gummel's iteration for one theta-step t0 -> t1 (the drift held over the step), as a
+fixed-point map G on the potential, G(x) = Poisson(densities advanced with the drift of x):
+    x_0 = Poisson(n^k, p^k)
     for j = 0, 1, ...:
-        (n, p) = theta-steps from (n^k, p^k) with the drift of phi_j
-        phi_{j+1} = Poisson(n, p)
-        stop when max|phi_{j+1} - phi_j| / max|phi_{j+1}| <= tol
-(the absolute change when phi_{j+1} = 0).
+        g_j = G(x_j), f_j = g_j - x_j
+        stop when max|f_j| / max|g_j| <= tol (the absolute change when g_j = 0); phi = g_j
+        x_{j+1} = g_j                                   (depth 0: plain Gummel)
+        x_{j+1} = g_j - sum_a gamma_a (dX_a + dF_a)     (Anderson acceleration, depth d)
+where dX_a, dF_a are the last min(d, j) differences of consecutive x and f, and gamma
+minimises |f_j - dF gamma|_2 through the normal equations (dF^T dF) gamma = dF^T f_j by
+Cholesky; if a pivot is not above 1e-13 times the largest diagonal entry the oldest
+difference is dropped and the solve repeated (Anderson 1965; Walker and Ni 2011 for the
+form with g).
 """
 from dataclasses import replace
 
@@ -66,16 +72,54 @@ def face_drift(r, theta, u, g, mobility):
     return vr.ravel(), vt.ravel()
 
 
+def anderson_gamma(dF, f):
+    """gamma of the Anderson step: the normal equations (dF^T dF) gamma = dF^T f by
+    Cholesky, the oldest column dropped while a pivot is not above 1e-13 times the largest
+    diagonal entry.  dF: list of columns, oldest first.  Returns (gamma, columns kept)."""
+    cols = list(dF)
+    while cols:
+        A = np.array([[float(a @ b) for b in cols] for a in cols])
+        rhs = np.array([float(a @ f) for a in cols])
+        k = len(cols)
+        Lc = np.zeros((k, k))
+        ok = True
+        top = max(A[i, i] for i in range(k))
+        for i in range(k):
+            for j in range(i + 1):
+                acc = A[i, j] - sum(Lc[i, q] * Lc[j, q] for q in range(j))
+                if i == j:
+                    if not acc > 1e-13 * top:
+                        ok = False
+                        break
+                    Lc[i, i] = np.sqrt(acc)
+                else:
+                    Lc[i, j] = acc / Lc[j, j]
+            if not ok:
+                break
+        if ok:
+            y = np.zeros(k)
+            for i in range(k):
+                y[i] = (rhs[i] - sum(Lc[i, q] * y[q] for q in range(i))) / Lc[i, i]
+            gam = np.zeros(k)
+            for i in reversed(range(k)):
+                gam[i] = (y[i] - sum(Lc[q, i] * gam[q] for q in range(i + 1, k))) / Lc[i, i]
+            return gam, len(cols)
+        cols = cols[1:]
+    return np.zeros(0), 0
+
+
 def gummel_step(phi_prob, car_probs, U_car, t0, t1, theta, w_car, w_phi, mobility, slots,
-                tol, max_iter):
+                tol, max_iter, depth=0):
     """One coupled theta-step.  car_probs / U_car / w_car / mobility: electrons then
     holes (w_car[c] = weights at t0 followed by those at t1); slots: the potential's
-    source slots that receive the electron and the hole densities.  Returns
-    (densities, phi, potential solves, last change, converged)."""
+    source slots that receive the electron and the hole densities; depth: Anderson depth
+    (0: plain Gummel).  Returns (densities, phi, potential solves, last change,
+    converged)."""
     g_phi = po.source_w(phi_prob, w_phi)[1]
     start = [np.asarray(u, dtype=np.float64).copy() for u in U_car]
     U = [u.copy() for u in start]
     phi_prev, change = None, 0.0
+    dX, dF, x_last, f_last = [], [], None, None      # Anderson histories
     for it in range(max_iter):
         src = list(phi_prob.src)
         src[slots[0]], src[slots[1]] = U[0], U[1]
@@ -85,6 +129,18 @@ def gummel_step(phi_prob, car_probs, U_car, t0, t1, theta, w_car, w_phi, mobilit
             change = diff / size if size > 0 else diff     # phi = 0: the absolute change
             if change <= tol:
                 return U, phi, it + 1, change, True
+            if depth > 0:
+                f = phi - phi_prev
+                if f_last is not None:
+                    dF = (dF + [f - f_last])[-depth:]
+                    dX = (dX + [phi_prev - x_last])[-depth:]
+                x_last, f_last = phi_prev, f
+                gam, kept = anderson_gamma(dF, f)
+                x = phi.copy()
+                for a, ga in enumerate(gam):
+                    col = len(dF) - kept + a
+                    x = x - ga * (dX[col] + dF[col])
+                phi = x
         phi_prev = phi
         for c in range(2):
             vr, vt = face_drift(phi_prob.r, phi_prob.theta, phi, g_phi, mobility[c])

@@ -6,7 +6,9 @@ by node from the printed formulas; the face drift to closed forms (linear in r:
 exact; r cos(theta) on uniform angles: the angular difference quotient equals
 sin(theta_{j+1/2}) sin(dtheta/2) / (dtheta/2)); the Gummel step to special cases whose
 answer is known without it (zero mobility decouples the carriers; a symmetric pair has
-zero net charge and so zero field) and to the direction of the drift each sign selects.
+zero net charge and so zero field) and to the direction of the drift each sign selects;
+the Anderson-accelerated step to a least-squares solve, to the plain iteration's fixed
+point, and to convergence where the plain iteration fails (a fixed point of the map).
 """
 import math
 from dataclasses import replace
@@ -179,3 +181,47 @@ def test_gummel_result_is_a_fixed_point():
         again = _plain_step(replace(prob, v_rface=vr, v_tface=vt), prob.u0, cp.t[0], cp.t[1],
                             cp.theta_w)
         assert np.max(np.abs(again - U[c])) / np.max(np.abs(U[c])) < 1e-11
+
+
+def test_anderson_gamma_is_the_least_squares_solution():
+    rng = np.random.default_rng(5)
+    cols = [rng.standard_normal(200) for _ in range(3)]
+    f = rng.standard_normal(200)
+    gam, kept = oc.anderson_gamma(cols, f)
+    want, *_ = np.linalg.lstsq(np.stack(cols, 1), f, rcond=None)
+    assert kept == 3 and np.max(np.abs(gam - want)) < 1e-12
+    # a column that repeats an older one makes the Gram matrix singular: the oldest goes
+    gam, kept = oc.anderson_gamma([cols[0], cols[1], cols[0].copy()], f)
+    want, *_ = np.linalg.lstsq(np.stack([cols[1], cols[0]], 1), f, rcond=None)
+    assert kept == 2 and np.max(np.abs(gam - want)) < 1e-12
+
+
+def _step(cp, depth, tol=1e-12, max_iter=60):
+    w = [np.array([1.0, 1.0]), np.array([1.0, 1.0])]
+    return oc.gummel_step(cp.phi, [cp.electrons, cp.holes], [cp.electrons.u0, cp.holes.u0],
+                          cp.t[0], cp.t[1], cp.theta_w, w, cp.w_phi, cp.mobility, cp.slots,
+                          tol, max_iter, depth=depth)
+
+
+@pytest.mark.parametrize("scale", [1.0, 4.0])
+def test_anderson_reaches_the_plain_fixed_point(scale):
+    cp = pi.coupled_pair(m=16, n=32, scale=scale)
+    U0, phi0, it0, _, ok0 = _step(cp, 0)
+    U3, phi3, it3, _, ok3 = _step(cp, 3)
+    assert ok0 and ok3 and it3 < it0
+    assert np.max(np.abs(phi3 - phi0)) / np.max(np.abs(phi0)) < 1e-11
+    for a, b in zip(U3, U0):
+        assert np.max(np.abs(a - b)) / np.max(np.abs(b)) < 1e-11
+
+
+def test_anderson_converges_where_plain_gummel_does_not():
+    cp = pi.coupled_pair(m=16, n=32, scale=8.0)
+    assert not _step(cp, 0)[4]
+    U, phi, it, change, ok = _step(cp, 3)
+    assert ok and change <= 1e-12
+    g_phi = po.source_w(cp.phi, cp.w_phi)[1]
+    for c, prob in enumerate((cp.electrons, cp.holes)):   # a fixed point of the map
+        vr, vt = oc.face_drift(prob.r, prob.theta, phi, g_phi, cp.mobility[c])
+        again = _plain_step(replace(prob, v_rface=vr, v_tface=vt), prob.u0, cp.t[0], cp.t[1],
+                            cp.theta_w)
+        assert np.max(np.abs(again - U[c])) / np.max(np.abs(U[c])) < 1e-10
