@@ -632,14 +632,16 @@ def _pair_oracle_step(args_):
     t0 = time.perf_counter()
     _, _, iters, _, ok = oc.gummel_step(cp.phi, [cp.electrons, cp.holes],
                                         [cp.electrons.u0, cp.holes.u0], cp.t[0], cp.t[1],
-                                        cp.theta_w, w, cp.w_phi, cp.mobility, cp.slots, 1e-10, 60)
+                                        cp.theta_w, w, cp.w_phi, cp.mobility, cp.slots, 1e-10, 60,
+                                        depth=3)
     return 2 * cp.electrons.N, time.perf_counter() - t0, iters
 
 
 def run_pair(args):
-    """The electron-hole pair with a self-consistent potential (Gummel's iteration per
-    theta-step, stop at a potential change of 1e-10): the coupled-pair recipe on a 512 x 1024
-    mesh (or --mesh M N).  value = carrier updates (2 N per step) / device time."""
+    """The electron-hole pair with a self-consistent potential (Gummel's iteration with
+    Anderson depth 3 per theta-step, stop at a potential change of 1e-10): the coupled-pair
+    recipe on a 512 x 1024 mesh (or --mesh M N).  value = carrier updates (2 N per step) /
+    device time."""
     import torch
     import polar_inputs as pi
     import paper_2509_15879_gb300 as P
@@ -664,7 +666,7 @@ def run_pair(args):
     ho = driver.create(cp.holes, precision, stream=stream.cuda_stream)
     P.polar_set_state(ph, np.zeros(cp.phi.N), 0.0)
     g = P.polar_gummel_create(ph, el, ho, cp.mobility, cp.slots[0], cp.slots[1], tol=1e-10,
-                              max_iter=60)
+                              max_iter=60, depth=3)
     w = [1.0, 1.0]
     for k in range(W):
         P.polar_gummel_step(g, cp.t[k], cp.t[k + 1], cp.theta_w, w, w, cp.w_phi)
@@ -687,9 +689,9 @@ def run_pair(args):
             "scaling": "weak", "vs_baseline": None,
             "dtype": "f64" if precision == P.POLAR_FP64 else "f32+f64", "data": "synthetic",
             "config": {"workload": f"electron-hole pair with a Poisson potential, {m} x {n} "
-                                   f"stretched adaptive mesh, Gummel's iteration to a "
-                                   f"potential change of 1e-10 per theta-step; updates = "
-                                   f"both carriers' unknowns per step",
+                                   f"stretched adaptive mesh, Gummel's iteration "
+                                   f"(Anderson depth 3) to a potential change of 1e-10 per "
+                                   f"theta-step; updates = both carriers' unknowns per step",
                        "m": m, "n": n, "N": cp.electrons.N, "precision": args.precision},
             "potential_solves_per_step": float(np.mean(iters)), "clocks": clk}
     if pool is not None:

@@ -281,13 +281,18 @@ int polar_face_drift(polar_ctx* ctx, double mobility, const double* g, double* v
  * theta-step from their state at t[0] with that drift held over the step (one 2-instance
  * polar_batch; w[c] holds 2 x nsrc weights of carrier c at t[0] and t[1]); repeated
  * until max|phi_j - phi_{j-1}| / max|phi_j| <= tol (the absolute change when phi_j = 0),
- * at most max_iter potential solves.  The carriers then hold t[1]'s densities and phi
- * the potential of those densities.  The object's device buffers (3 N doubles from the
- * potential's allocator; each carrier's face D, reaction and drift faces from its own)
+ * at most max_iter potential solves.  With depth d > 0 the potential that sets the next
+ * drift is Anderson's extrapolation x = g - sum_a gamma_a (dX_a + dF_a) over the last d
+ * differences of the iterates x and residuals f = g - x (g the new potential), gamma the
+ * least-squares fit of f by dF (normal equations by Cholesky, the oldest difference
+ * dropped while a pivot is not above 1e-13 of the largest diagonal entry); it converges
+ * in fewer solves, and at couplings where plain Gummel does not.  The carriers then hold t[1]'s densities and phi
+ * the potential of those densities.  The object's device buffers ((5 + 2 d) N doubles from
+ * the potential's allocator; each carrier's face D, reaction and drift faces from its own)
  * are freed with those contexts; destroy the object before any of its contexts.  The
  * carriers' face D and reaction are those set when the object was created.
- * Errors: POLAR_EINVAL (mismatched meshes or scheme, bad slots, mobility, tol or
- * max_iter), POLAR_ESTATE (coefficients or states missing), POLAR_ENOCONV (max_iter
+ * Errors: POLAR_EINVAL (mismatched meshes or scheme, bad slots, mobility, tol, max_iter
+ * or depth), POLAR_ESTATE (coefficients or states missing), POLAR_ENOCONV (max_iter
  * reached: the carriers hold the last iterate), errors of the solves. */
 typedef struct {
   double mobility[2];      /* electrons, holes: v_c = -mobility[c] grad phi            */
@@ -295,7 +300,7 @@ typedef struct {
   int32_t src_holes;
   double tol;              /* on max|phi_j - phi_{j-1}| / max|phi_j|                   */
   int32_t max_iter;        /* potential solves per step                                */
-  int32_t reserved;
+  int32_t depth;           /* Anderson acceleration depth, 0 (plain Gummel) .. 5       */
 } polar_gummel_desc;
 typedef struct {
   int32_t iters;                /* potential solves of the step                        */

@@ -62,7 +62,7 @@ class polar_step_stats(C.Structure):
 class polar_gummel_desc(C.Structure):
     _fields_ = [("mobility", C.c_double * 2), ("src_electrons", C.c_int32),
                 ("src_holes", C.c_int32), ("tol", C.c_double), ("max_iter", C.c_int32),
-                ("reserved", C.c_int32)]
+                ("depth", C.c_int32)]
 
 
 class polar_gummel_stats(C.Structure):
@@ -465,9 +465,9 @@ class Gummel:
 
 
 def polar_gummel_create(phi: Ctx, electrons: Ctx, holes: Ctx, mobility, src_electrons,
-                        src_holes, tol=1e-10, max_iter=50) -> Gummel:
+                        src_holes, tol=1e-10, max_iter=50, depth=0) -> Gummel:
     d = polar_gummel_desc((C.c_double * 2)(*[float(x) for x in mobility]), int(src_electrons),
-                          int(src_holes), float(tol), int(max_iter), 0)
+                          int(src_holes), float(tol), int(max_iter), int(depth))
     h = C.c_void_p()
     _check(load().polar_gummel_create(phi.handle, electrons.handle, holes.handle, C.byref(d),
                                       C.byref(h)))

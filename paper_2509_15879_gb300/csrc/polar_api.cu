@@ -103,7 +103,15 @@ struct polar_gummel {
   double* b[2] = {nullptr, nullptr};
   double* vr[2] = {nullptr, nullptr};
   double* vt[2] = {nullptr, nullptr};
+  // Anderson acceleration: last iterate and residual, the current residual, and the
+  // difference columns (ring buffers of `depth` each), dot-product partials
+  double *x_last = nullptr, *f_last = nullptr, *f_cur = nullptr;
+  double* dX[kMaxAnderson] = {};
+  double* dF[kMaxAnderson] = {};
+  double* partials = nullptr;
+  std::vector<double> partials_host;
 };
+constexpr int kAABlocks = 304;
 struct polar_batch {
   std::vector<polar_ctx*> ctx;
   cudaStream_t st = nullptr;
@@ -2632,6 +2640,99 @@ int polar_face_drift(polar_ctx* c, double mobility, const double* g, double* v_r
   return POLAR_OK;
 }
 
+// Anderson step of the Gummel map (the potential's state g = G(x), x in phi_prev): the
+// new difference columns, gamma from the normal equations by Cholesky (the oldest column
+// dropped while a pivot is not above 1e-13 of the largest diagonal entry), then the
+// extrapolated potential written over the state.
+static int anderson_update(polar_gummel* G, int* cols, int& ncols, bool& have_last) {
+  polar_ctx* c = G->phi;
+  const Shape sh = c->sh0();
+  const size_t nv = c->nv();
+  const int depth = G->d.depth;
+  int slot = 0;
+  if (have_last) {
+    if (ncols < depth) {
+      slot = ncols;
+      cols[ncols++] = slot;
+    } else {
+      slot = cols[0];
+      for (int a = 0; a + 1 < ncols; ++a) cols[a] = cols[a + 1];
+      cols[ncols - 1] = slot;
+    }
+  }
+  LAUNCH(launch_aa_columns(sh, c->U, G->phi_prev, G->f_last, G->x_last, G->f_cur, G->dF[slot],
+                           G->dX[slot], have_last, c->st));
+  CUDA_TRY(cudaMemcpyAsync(G->x_last, G->phi_prev, nv * sizeof(double), cudaMemcpyDeviceToDevice,
+                           c->st));
+  std::swap(G->f_last, G->f_cur);  // f_last now holds this residual
+  have_last = true;
+  for (int first = 0; first < ncols; ++first) {
+    const int k = ncols - first;
+    AndersonCols dc{};
+    for (int a = 0; a < k; ++a) dc.v[a] = G->dF[cols[first + a]];
+    dc.v[k] = G->f_last;
+    for (int a = k + 1; a <= kMaxAnderson; ++a) dc.v[a] = G->f_last;
+    dc.count = k + 1;
+    const int nd = k * (k + 1) / 2 + k;
+    LAUNCH(launch_aa_dots(sh, dc, G->partials, kAABlocks, c->st));
+    G->partials_host.resize((size_t)kAABlocks * nd);
+    CUDA_TRY(cudaMemcpyAsync(G->partials_host.data(), G->partials,
+                             G->partials_host.size() * sizeof(double), cudaMemcpyDeviceToHost,
+                             c->st));
+    CUDA_TRY(cudaStreamSynchronize(c->st));
+    std::vector<double> dots(nd, 0.0);
+    for (int b = 0; b < kAABlocks; ++b)
+      for (int q = 0; q < nd; ++q) dots[q] += G->partials_host[(size_t)b * nd + q];
+    // Gram matrix (upper triangle row by row) and right-hand side, in the kernel's order
+    std::vector<double> A((size_t)k * k), rhs(k);
+    int q = 0;
+    for (int a = 0; a < k; ++a) {
+      for (int b = a; b < k; ++b) A[(size_t)a * k + b] = A[(size_t)b * k + a] = dots[q++];
+      rhs[a] = dots[q++];
+    }
+    double top = 0.0;
+    for (int a = 0; a < k; ++a) top = std::max(top, A[(size_t)a * k + a]);
+    std::vector<double> L((size_t)k * k, 0.0);
+    bool ok = true;
+    for (int i = 0; i < k && ok; ++i)
+      for (int j = 0; j <= i; ++j) {
+        double acc = A[(size_t)i * k + j];
+        for (int p = 0; p < j; ++p) acc -= L[(size_t)i * k + p] * L[(size_t)j * k + p];
+        if (i == j) {
+          if (!(acc > 1e-13 * top)) {
+            ok = false;
+            break;
+          }
+          L[(size_t)i * k + i] = std::sqrt(acc);
+        } else {
+          L[(size_t)i * k + j] = acc / L[(size_t)j * k + j];
+        }
+      }
+    if (!ok) continue;  // drop the oldest column
+    std::vector<double> y(k), gam(k);
+    for (int i = 0; i < k; ++i) {
+      double acc = rhs[i];
+      for (int p = 0; p < i; ++p) acc -= L[(size_t)i * k + p] * y[p];
+      y[i] = acc / L[(size_t)i * k + i];
+    }
+    for (int i = k - 1; i >= 0; --i) {
+      double acc = y[i];
+      for (int p = i + 1; p < k; ++p) acc -= L[(size_t)p * k + i] * gam[p];
+      gam[i] = acc / L[(size_t)i * k + i];
+    }
+    AndersonCols cx{}, cf{};
+    for (int a = 0; a < k; ++a) {
+      cx.v[a] = G->dX[cols[first + a]];
+      cf.v[a] = G->dF[cols[first + a]];
+    }
+    cx.count = cf.count = k;
+    LAUNCH(launch_aa_update(sh, cx, cf, gam.data(), c->U, c->st));
+    break;
+  }
+  CUDA_TRY(cudaStreamSynchronize(c->st));
+  return POLAR_OK;
+}
+
 int polar_gummel_create(polar_ctx* phi, polar_ctx* electrons, polar_ctx* holes,
                         const polar_gummel_desc* d, polar_gummel** out) {
   if (!phi || !electrons || !holes || !d || !out) return fail(POLAR_EINVAL, "null argument");
@@ -2651,8 +2752,8 @@ int polar_gummel_create(polar_ctx* phi, polar_ctx* electrons, polar_ctx* holes,
       d->src_holes >= phi->nsrc || d->src_electrons == d->src_holes)
     return fail(POLAR_EINVAL, "the carrier source slots must be two distinct sources of the potential");
   if (!std::isfinite(d->mobility[0]) || !std::isfinite(d->mobility[1]) || !(d->tol > 0) ||
-      d->max_iter < 1)
-    return fail(POLAR_EINVAL, "bad mobility, tol or max_iter");
+      d->max_iter < 1 || d->depth < 0 || d->depth > kMaxAnderson)
+    return fail(POLAR_EINVAL, "bad mobility, tol, max_iter or depth");
   CUDA_TRY(cudaSetDevice(phi->device));
   polar_gummel* G = new polar_gummel();
   G->phi = phi;
@@ -2665,6 +2766,16 @@ int polar_gummel_create(polar_ctx* phi, polar_ctx* electrons, polar_ctx* holes,
   if (rc == POLAR_OK) rc = dalloc(phi, &G->save[1], nv);
   if (rc == POLAR_OK) rc = dalloc(phi, &G->phi_prev, nv);
   if (rc == POLAR_OK) rc = dalloc(phi, &G->change, 2);
+  if (rc == POLAR_OK && d->depth > 0) {
+    rc = dalloc(phi, &G->x_last, nv);
+    if (rc == POLAR_OK) rc = dalloc(phi, &G->f_last, nv);
+    if (rc == POLAR_OK) rc = dalloc(phi, &G->f_cur, nv);
+    for (int a = 0; a < d->depth && rc == POLAR_OK; ++a) {
+      rc = dalloc(phi, &G->dX[a], nv);
+      if (rc == POLAR_OK) rc = dalloc(phi, &G->dF[a], nv);
+    }
+    if (rc == POLAR_OK) rc = dalloc(phi, &G->partials, (size_t)kAABlocks * 20);
+  }
   if (rc == POLAR_OK) rc = ensure_mesh_dev(phi);
   const size_t nf = (size_t)(phi->m + 1) * phi->n, nt = (size_t)phi->m * phi->n;
   for (int k = 0; k < 2 && rc == POLAR_OK; ++k) {
@@ -2734,6 +2845,9 @@ int polar_gummel_step(polar_gummel* G, const double* t, double theta, const doub
   double change = 0.0;
   int it = 0;
   bool converged = false;
+  int cols[kMaxAnderson];  // Anderson difference columns in use, oldest first
+  int ncols = 0;
+  bool have_last = false;
   for (it = 0; it < G->d.max_iter; ++it) {
     // the carrier densities as the potential's sources (split layout times volumes)
     for (int k = 0; k < 2; ++k) {
@@ -2755,6 +2869,7 @@ int polar_gummel_step(polar_gummel* G, const double* t, double theta, const doub
         ++it;
         break;
       }
+      if (G->d.depth > 0) TRY(anderson_update(G, cols, ncols, have_last));
     }
     CUDA_TRY(cudaMemcpyAsync(G->phi_prev, phi->U, nv * sizeof(double), cudaMemcpyDeviceToDevice,
                              phi->st));

@@ -594,6 +594,25 @@ struct CoarsenLevel {
 };
 int launch_coarsen(const CoarsenLevel& f, const CoarsenLevel& c, cudaStream_t st);
 
+// Anderson acceleration of a fixed-point iteration on level-0 vectors (split layout; only
+// the N unknowns are read or written).  kMaxAnderson columns at most.
+constexpr int kMaxAnderson = 5;
+struct AndersonCols {
+  const double* v[kMaxAnderson + 1];
+  int count;
+};
+// f = g - x; with `last`, also dF = f - f_last and dX = x - x_last
+int launch_aa_columns(const Shape& sh, const double* g, const double* x, const double* f_last,
+                      const double* x_last, double* f, double* dF, double* dX, bool last,
+                      cudaStream_t st);
+// per-block partial dot products of the columns c[0..k-1] with each other (a <= b, row
+// by row) and with c[k]: k (k + 1) / 2 + k values per block, `blocks` blocks
+int launch_aa_dots(const Shape& sh, const AndersonCols& c, double* partials, int blocks,
+                   cudaStream_t st);
+// x -= sum_a gamma_a (dX_a + dF_a), the columns in order
+int launch_aa_update(const Shape& sh, const AndersonCols& dX, const AndersonCols& dF,
+                     const double* gamma_host, double* x, cudaStream_t st);
+
 // out[0] = max_k |a_k - b_k|, out[1] = max_k |a_k| over n doubles (out zeroed first; NaN
 // counts as +inf)
 int launch_max_change(size_t n, const double* a, const double* b, double* out, cudaStream_t st);

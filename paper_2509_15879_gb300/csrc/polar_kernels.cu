@@ -1096,6 +1096,104 @@ int launch_max_change(size_t n, const double* a, const double* b, double* out, c
   return 1;
 }
 
+// ------------------------------------------------------------------ Anderson acceleration
+// split index of unknown q (0: the origin, 1 + j m + (i - 1): node (i, j))
+__device__ __forceinline__ size_t split_of(const Shape& sh, size_t q) {
+  if (q == 0) return 0;
+  const size_t jj = (q - 1) / sh.m;
+  return sh.at((int)(q - 1 - jj * sh.m) + 1, (int)jj);
+}
+
+__global__ void k_aa_columns(Shape sh, const double* g, const double* x, const double* f_last,
+                             const double* x_last, double* f, double* dF, double* dX, int last) {
+  const size_t N = (size_t)sh.m * sh.n + 1;
+  for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < N;
+       q += (size_t)gridDim.x * blockDim.x) {
+    const size_t p = split_of(sh, q);
+    const double fv = g[p] - x[p];
+    f[p] = fv;
+    if (last) {
+      dF[p] = fv - f_last[p];
+      dX[p] = x[p] - x_last[p];
+    }
+  }
+}
+int launch_aa_columns(const Shape& sh, const double* g, const double* x, const double* f_last,
+                      const double* x_last, double* f, double* dF, double* dX, bool last,
+                      cudaStream_t st) {
+  k_aa_columns<<<grid_for((size_t)sh.m * sh.n + 1, kVT), kVT, 0, st>>>(sh, g, x, f_last, x_last,
+                                                                       f, dF, dX, last ? 1 : 0);
+  return 1;
+}
+
+constexpr int kAAMaxDots = kMaxAnderson * (kMaxAnderson + 1) / 2 + kMaxAnderson;
+__global__ void __launch_bounds__(256) k_aa_dots(Shape sh, AndersonCols c, double* partials) {
+  const int k = c.count - 1, nd = k * (k + 1) / 2 + k;
+  double acc[kAAMaxDots];
+#pragma unroll
+  for (int d = 0; d < kAAMaxDots; ++d) acc[d] = 0.0;
+  const size_t N = (size_t)sh.m * sh.n + 1;
+  for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < N;
+       q += (size_t)gridDim.x * blockDim.x) {
+    const size_t p = split_of(sh, q);
+    double v[kMaxAnderson + 1];
+#pragma unroll
+    for (int a = 0; a <= kMaxAnderson; ++a) v[a] = a <= k ? c.v[a][p] : 0.0;
+    int d = 0;
+#pragma unroll
+    for (int a = 0; a < kMaxAnderson; ++a)
+#pragma unroll
+      for (int b = 0; b <= kMaxAnderson; ++b) {
+        // pairs (a, b) with a <= b < k, then (a, k): the columns against the right-hand side
+        const bool pair = a < k && ((b >= a && b < k) || b == kMaxAnderson);
+        if (pair) {
+          const double w = (b == kMaxAnderson) ? v[k] : v[b];
+          acc[d] = fma(v[a], w, acc[d]);
+          ++d;
+        }
+      }
+  }
+  __shared__ double red[8][kAAMaxDots];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int d = 0; d < nd; ++d) {
+    double s = acc[d];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (lane == 0) red[warp][d] = s;
+  }
+  __syncthreads();
+  if (threadIdx.x < nd) {
+    double s = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w][threadIdx.x];
+    partials[(size_t)blockIdx.x * nd + threadIdx.x] = s;
+  }
+}
+int launch_aa_dots(const Shape& sh, const AndersonCols& c, double* partials, int blocks,
+                   cudaStream_t st) {
+  k_aa_dots<<<blocks, 256, 0, st>>>(sh, c, partials);
+  return 1;
+}
+
+struct AAGamma {
+  double g[kMaxAnderson];
+};
+__global__ void k_aa_update(Shape sh, AndersonCols dX, AndersonCols dF, AAGamma gm, double* x) {
+  const size_t N = (size_t)sh.m * sh.n + 1;
+  for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < N;
+       q += (size_t)gridDim.x * blockDim.x) {
+    const size_t p = split_of(sh, q);
+    double v = x[p];
+    for (int a = 0; a < dX.count; ++a) v -= gm.g[a] * (dX.v[a][p] + dF.v[a][p]);
+    x[p] = v;
+  }
+}
+int launch_aa_update(const Shape& sh, const AndersonCols& dX, const AndersonCols& dF,
+                     const double* gamma_host, double* x, cudaStream_t st) {
+  AAGamma gm{};
+  for (int a = 0; a < dX.count; ++a) gm.g[a] = gamma_host[a];
+  k_aa_update<<<grid_for((size_t)sh.m * sh.n + 1, kVT), kVT, 0, st>>>(sh, dX, dF, gm, x);
+  return 1;
+}
+
 // ------------------------------------------------------------------ layout conversion
 // interface index q = 1 + j m + (i - 1) <-> split index sh.at(i, j); q = 0 is the origin
 __global__ void k_pack(Shape sh, const double* in, const double* scale, double* out) {
