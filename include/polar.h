@@ -347,9 +347,8 @@ int polar_apply_operator(polar_ctx* ctx, double alpha, double beta, const double
  * angles is staged there.  Every call shares that array, so calls that may overlap on the
  * GPU (different streams, or several host threads) race; serialise them.  Each call looks
  * up the array's address on the current device (the first call on a device is its set-up);
- * make that first call before any stream capture begins: a call while `stream` is being
- * captured reuses the address found by the device's last call, and returns POLAR_ESTATE if
- * there was none. */
+ * make that first call before any stream capture begins (a first call made during a
+ * capture returns POLAR_ESTATE). */
 int polar_apply_rows_noalloc(int32_t m, int32_t n, const double* R, const double* W,
                              const double* E, const double* S, const double* N,
                              const double* o, double alpha, double beta, const double* x,
