@@ -76,9 +76,9 @@ WORKLOADS = {
 # ncu dram bytes (read + write) per launch of the dominant kernel class, from the capture
 # summarised under profiles/, keyed by (workload, kernel class); absent until a capture of
 # the current kernel exists.  The 8192 x 16384 entry: the FP64 level-0 even-ring
-# post-smoothing captured on the same recipe at 2048 x 4096 (411.6 MB, equal to its
-# algorithmic bytes), scaled by the 16x level-0 points of the full mesh.
-NCU_TRAFFIC = {("c5", "ring_post_even@L0"): 411.6e6 * 16}
+# post-smoothing captured on the same recipe at 2048 x 4096 (392.2 MB read + 34.3 MB
+# written; algorithmic 403 MB), scaled by the 16x level-0 points of the full mesh.
+NCU_TRAFFIC = {("c5", "ring_post_even@L0"): 426.5e6 * 16}
 
 # FP64 arithmetic rate of the GB300s: 528 G FMA/s from a probe of independent FMA
 # chains on every SM (the nominal figure is 1.25 TFLOP/s)
