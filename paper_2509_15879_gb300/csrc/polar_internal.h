@@ -470,7 +470,6 @@ int launch_coarsest(const LevelView<T>& L, const T* b, T* x, Params p, const int
 // ----------------------------------------------------------------- batched launchers
 // Each launches `grid` blocks over the slots S[0, nslots) with per-slot arguments A (see
 // BSlot); the active instances are those with mask[inst] != 0.
-int persistent_grid(int nwork, int per_sm);
 template <typename T>
 int launch_stencil_b(int mode, const StArgs<T>* A, const BSlot* S, int nslots, const int* mask,
                      int grid, int TK, cudaStream_t st);

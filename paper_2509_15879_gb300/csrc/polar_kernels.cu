@@ -1235,18 +1235,6 @@ int launch_unpack(const Shape& sh, const double* in, const double* div, double* 
 
 
 // ------------------------------------------------------------------ batched launchers
-// Blocks of a persistent batched launch: per_sm blocks on each of the GPU's SMs, at most one
-// per work item.
-int persistent_grid(int nwork, int per_sm) {
-  static int sms = 0;
-  if (!sms) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0)
-      sms = 152;
-  }
-  return std::max(1, std::min(nwork, sms * per_sm));
-}
 template <typename T>
 int launch_stencil_b(int mode, const StArgs<T>* A, const BSlot* S, int nslots, const int* mask,
                      int grid, int TK, cudaStream_t st) {
