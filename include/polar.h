@@ -286,11 +286,12 @@ int polar_face_drift(polar_ctx* ctx, double mobility, const double* g, double* v
  * differences of the iterates x and residuals f = g - x (g the new potential), gamma the
  * least-squares fit of f by dF (normal equations by Cholesky, the oldest difference
  * dropped while a pivot is not above 1e-13 of the largest diagonal entry); it converges
- * in fewer solves, and at couplings where plain Gummel does not.  The carriers then hold t[1]'s densities and phi
- * the potential of those densities.  The object's device buffers ((5 + 2 d) N doubles from
- * the potential's allocator; each carrier's face D, reaction and drift faces from its own)
- * are freed with those contexts; destroy the object before any of its contexts.  The
- * carriers' face D and reaction are those set when the object was created.
+ * in fewer solves, and at couplings where plain Gummel does not.  The carriers then hold
+ * t[1]'s densities and phi the potential of those densities.  The object's device buffers
+ * (3 N doubles, plus (3 + 2 d) N with depth d > 0, from the potential's allocator; each
+ * carrier's face D, reaction and drift faces from its own) are freed with those contexts;
+ * destroy the object before any of its contexts.  The carriers' face D and reaction are
+ * those set when the object was created.
  * Errors: POLAR_EINVAL (mismatched meshes or scheme, bad slots, mobility, tol, max_iter
  * or depth), POLAR_ESTATE (coefficients or states missing), POLAR_ENOCONV (max_iter
  * reached: the carriers hold the last iterate), errors of the solves. */
