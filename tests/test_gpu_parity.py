@@ -266,3 +266,23 @@ def test_c2_recipe_whole_schedule(c2_recipe_schedule, precision, tol):
         print(f"PARITY C2 recipe 64x128 consecutive, level {k0 + 100}, precision {precision}: "
               f"{d:.2e} of max_(l<=k)|U^l| (max|U^k| = {np.max(np.abs(Uref)):.2e}, bar {tol:g})")
         assert d < tol, (k0 + 100, d)
+
+
+def test_timing_reports_bytes_and_flops():
+    # the per-kernel timing carries each class's algorithmic bytes and arithmetic; the
+    # rates it implies stay below what the device can do (HBM copy rate, FP64 pipe)
+    prob = _small_continuity(40, 72, K=2)
+    ctx = driver.create(prob, P.POLAR_FP64)
+    driver.advance(ctx, prob, 0, 1)
+    P.polar_timing_enable(ctx, True)
+    driver.advance(ctx, prob, 1, 2)
+    q = P.polar_timing_query(ctx)
+    P.polar_timing_enable(ctx, False)
+    pts = prob.m * prob.n
+    for name in ("ring_pre_odd@L0", "ring_post_even@L0", "stencil_dot", "resid64"):
+        d = q[name]
+        assert d["launches"] > 0 and d["bytes"] > 0 and d["flops"] > 0
+        per_launch = d["flops"] / d["launches"]
+        assert pts < per_launch < 40 * pts        # a few to a few tens of flops per point
+        assert d["flops"] / (d["ms"] * 1e-3) < 1.3e12   # under GB300's FP64 rate
+    assert q["correct"]["flops"] == 0.0             # classes without a model report 0
