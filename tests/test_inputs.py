@@ -121,3 +121,18 @@ def test_chunked_field_evaluation_matches_whole_arrays():
     got = _chunked(lambda a, b: F.vel(a, b), x, y, nout=3, chunk=100)
     for g_, w_ in zip(got, (vx, vy, dv)):
         assert np.allclose(g_, w_, rtol=1e-13, atol=1e-13 * np.max(np.abs(w_)))
+
+
+def test_coupled_pair_is_seeded_and_consistent():
+    a, b = pi.coupled_pair(m=12, n=24), pi.coupled_pair(m=12, n=24)
+    for pa, pb in ((a.phi, b.phi), (a.electrons, b.electrons), (a.holes, b.holes)):
+        assert np.array_equal(pa.d_rface, pb.d_rface) and np.array_equal(pa.u0, pb.u0)
+        assert pa.m == 12 and pa.n == 24 and np.array_equal(pa.r, a.phi.r)
+        assert np.array_equal(pa.theta, a.phi.theta)
+    c = pi.coupled_pair(m=12, n=24, seed=7)
+    assert not np.array_equal(c.electrons.d_rface, a.electrons.d_rface)
+    # the potential's source weights put the densities in with opposite signs and the
+    # carriers' drift signs are opposite
+    assert a.w_phi[a.slots[0]] == -a.w_phi[a.slots[1]]
+    assert a.mobility[0] * a.mobility[1] < 0
+    assert np.all(a.electrons.u0 > 0) and np.all(a.holes.u0 > 0)
